@@ -1,0 +1,358 @@
+"""Throughput of the LLG right-hand side inside adaptive RK45 on one GB300.
+
+A step is one Dormand-Prince attempt over the whole workload: 7 right-hand
+sides (RK prologue, zero-padded FFT demag with the fused tensor product,
+exchange/DMI/anisotropy/Zeeman epilogue, LL torque), the FP64 error-norm
+reduction, the step controller and the projection onto |m| = 1.  The metric
+counts cell-updates: cells x right-hand sides / second.
+
+Default workload: 512 x 512 x 4 thin film with interfacial DMI and
+perpendicular anisotropy, ~200 reversed disks (FP32 path; the FP64 path is
+measured on the same workload and reported beside it).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                  [--workload film|film_relax_32|cube|neb|batch]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "LLG RHS cell-updates/s, FP32/batched vs FP64 plain, % HBM roofline, 1 GB300"
+UNIT = "cell-updates/s"
+L2_BYTES = 129e6
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ workloads
+def workload(name):
+    if name == "film":
+        return synth.skyrmion_film(precision="f32")
+    if name == "film_relax_32":
+        return synth.film_relax_32()
+    if name == "cube":
+        return synth.bulk_cube()
+    if name == "neb":
+        return synth.neb_chain()
+    if name == "batch":
+        return synth.uneven_batch()
+    raise SystemExit(f"unknown workload {name}")
+
+
+def cells(w):
+    return sum(s.mesh.ncells for s in w.sims)
+
+
+def pad(n, min2=False):
+    if n <= 1:
+        return 2 if min2 else 1
+    p = 1
+    while p < 2 * n - 1:
+        p *= 2
+    return p
+
+
+def kernel_bytes(w, e):
+    """Compulsory bytes per attempt of each kernel kind ('Roofline')."""
+    out = {k: 0.0 for k in ("x_forward", "y_forward", "z_fused", "y_inverse", "y_fused",
+                            "x_inverse_epilogue", "project")}
+    for s in w.sims:
+        n = s.mesh.ncells
+        nx, ny, nz = s.mesh.nx, s.mesh.ny, s.mesh.nz
+        Px, Py, Pz = pad(nx, True), pad(ny), pad(nz)
+        Kx = Px // 2 + 1
+        c = 2 * e                                    # one complex value
+        spec_rows = 3 * nz * ny * Kx * c             # x-transform rows (ny of Py)
+        spec_full = 3 * nz * Py * Kx * c             # all Py rows
+        ncomp = 6 if Pz > 1 else 4
+        tens = ncomp * (Pz // 2 + 1) * (Py // 2 + 1) * Kx * e
+        demag = s.mat.demag
+        for st in range(1, 8):
+            out["x_forward"] += 3 * e * n * st + (3 * e * n if st > 1 else 0) + (3 * e * n if st == 7 else 0)
+            if demag:
+                out["x_forward"] += spec_rows
+                if Pz > 1:
+                    if Py > 1:
+                        out["y_forward"] += spec_rows + spec_full
+                        out["y_inverse"] += spec_full + spec_rows
+                    out["z_fused"] += 2 * spec_full + tens
+                elif Py > 1:
+                    out["y_fused"] += 2 * spec_rows + tens
+            out["x_inverse_epilogue"] += (spec_rows if demag else 0) + 6 * e * n + (3 * e * n if st == 7 else 0)
+        out["project"] += 6 * e * n
+    return out
+
+
+def step_bytes_survey(w, e):
+    """The whole-step algorithmic figure: 22.5 e + T bytes per cell-update (T = tensor bytes / cell)."""
+    tot = 0.0
+    for s in w.sims:
+        nx, ny, nz = s.mesh.nx, s.mesh.ny, s.mesh.nz
+        Px, Py, Pz = pad(nx, True), pad(ny), pad(nz)
+        Kx = Px // 2 + 1
+        ncomp = 6 if Pz > 1 else 4
+        T = ncomp * e * (Kx * (Py // 2 + 1) * (Pz // 2 + 1)) / s.mesh.ncells if s.mat.demag else 0.0
+        tot += (22.5 * e + T) * s.mesh.ncells * 7
+    return tot
+
+
+# ------------------------------------------------------------------ clocks
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-i", str(self.index), "-lms", "100"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.p:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+
+    def summary(self):
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(", ") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for i, nme in enumerate(names):
+                if len(r) > 5 + i and r[5 + i].strip().lower() == "active":
+                    reasons.add(nme)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ oracle timing
+def oracle_rate(w, budget_s, max_evals, min_evals=1):
+    """FP64 oracle right-hand sides of the workload's first simulation on the host cores."""
+    from oracle import demag as D
+    from oracle import fields as F
+    s = w.sims[0]
+    Nt = D.mesh_tensor(s.mesh) if s.mat.demag else None
+    Ms = F.ms_array(s.mesh, s.mat)
+    t0 = time.perf_counter()
+    F.rhs(s.mesh, s.mat, s.m0, Ms, Nt, "fft")
+    one = time.perf_counter() - t0
+    n = int(max(min_evals, min(max_evals, budget_s // max(one, 1e-9))))
+    t0 = time.perf_counter()
+    for _ in range(n):
+        F.rhs(s.mesh, s.mat, s.m0, Ms, Nt, "fft")
+    dt = time.perf_counter() - t0
+    return s.mesh.ncells * n / dt, n, dt, s.mesh
+
+
+# ------------------------------------------------------------------ main
+def run_reference(args, rank, world):
+    w = workload(args.workload)
+    line = {"impl": "reference", "metric": METRIC, "unit": UNIT, "n_gpus": world, "higher_is_better": True,
+            "data": "synthetic", "dtype": "f64",
+            "config": {"workload": w.name, "cells": cells(w), "path": "FP64 numpy oracle, host cores"}}
+    if rank != 0:
+        return None
+    budget = min(180.0, 3.0 * max(1, args.steps + args.warmup))
+    value, n, dt, mesh = oracle_rate(w, budget, max_evals=args.steps, min_evals=1)
+    line.update({"value": value, "steps": n, "warmup": 1, "ms_per_step": 1e3 * dt / n, "scaling": "weak",
+                 "vs_baseline": None,
+                 "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                  "sample": f"{n} right-hand sides of the {mesh.nx}x{mesh.ny}x{mesh.nz} mesh "
+                                            f"(FFT demag, numpy, one thread)"},
+                 "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}})
+    return line
+
+
+def timed_attempts(ctx, torch, stream, k):
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    start.record(stream)
+    ctx.rk45_attempts(k)
+    end.record(stream)
+    end.synchronize()
+    return start.elapsed_time(end)
+
+
+def setup_ctx(mm, w, precision, stream, rtol):
+    ctx = mm.Context(precision, stream=stream.cuda_stream)
+    for s in w.sims:
+        ctx.add_sim(s.mesh, s.mat, s.Ms_cells)
+    ctx.precompute()
+    ctx.set_m(np.concatenate([s.m0.ravel() for s in w.sims]))
+    if w.neb:
+        ctx.neb_setup(0, len(w.sims), w.neb["k_spring"])
+    ctx.reset_time()
+    ctx.rk45_setup(rtol, t_end=0.0, max_dmdt=0.0)
+    return ctx
+
+
+def run_gpu(args, rank, world, dist):
+    import torch
+    from paper_2406_16064_gb300 import mm
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream()
+    w = workload(args.workload)
+    prec = args.precision or ("f64" if args.workload == "film_relax_32" else "f32")
+    w.precision = prec
+    e = 8 if prec == "f64" else 4
+    ncell = cells(w)
+    ctx = setup_ctx(mm, w, prec, stream, w.rtol)
+    ctx.rk45_attempts(args.warmup)
+    torch.cuda.synchronize()
+    n0 = ctx.launches()
+    if dist:
+        dist.barrier()
+    with Clocks(dev) as clk:
+        ms = timed_attempts(ctx, torch, stream, args.steps)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    launches = ctx.launches() - n0
+    clocks = clk.summary()
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = world * ncell * 7 * args.steps / (ms_max / 1e3)
+    # per-kernel durations inside the same step (events on the launching stream)
+    prof = ctx.profile_attempts(max(1, min(5, args.steps)))
+    kb = kernel_bytes(w, e)
+    hbm, peak_kind = peaks()
+    rows = {}
+    for k, (tms, cnt) in prof.items():
+        if cnt:
+            rows[k] = {"ms_per_attempt": tms / max(1, min(5, args.steps)), "launches": cnt,
+                       "achieved_gbs": (kb.get(k, 0.0) * max(1, min(5, args.steps))) / (tms / 1e3) / 1e9
+                       if k in kb and tms > 0 else None}
+    dom = max((k for k in rows if k in kb), key=lambda k: rows[k]["ms_per_attempt"])
+    reps = max(1, min(5, args.steps))
+    launches_dom = prof[dom][1] / reps
+    avg_launch_ms = prof[dom][0] / prof[dom][1]
+    bytes_per_launch = kb[dom] / launches_dom
+    achieved = bytes_per_launch / (avg_launch_ms / 1e3) / 1e9
+    step_ms = ms_max / args.steps
+    step_bytes = step_bytes_survey(w, e)
+    # end to end through the C ABI with host buffers: H2D of m, one attempt, D2H of m
+    ke = max(3, min(50, args.steps // 20))
+    mhost = ctx.get_m(-1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(ke):
+        ctx.set_m(mhost)
+        ctx.rk45_attempts(1)
+        mhost = ctx.get_m(-1)
+    e2e_s = time.perf_counter() - t0
+    e2e_value = world * ncell * 7 * ke / e2e_s
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": prec, "data": "synthetic",
+        "config": {"workload": w.name, "cells": ncell, "rhs_per_step": 7, "rtol": w.rtol,
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "l2": f"inputs larger than L2: working set ~{int(step_bytes / 7 / 1e6)} MB per RHS "
+                         f"(state, 7 stage vectors, spectrum, tensor) vs 129 MB L2"},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "peak_kind": f"of {peak_kind}",
+                     "bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_launch_ms, "traffic": None,
+                     "step_algorithmic_gbs": step_bytes / (step_ms / 1e3) / 1e9,
+                     "step_frac": step_bytes / (step_ms / 1e3) / 1e9 / hbm},
+        "kernels": rows,
+        "clocks": clocks,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 3 * ncell * e,
+                "d2h_bytes_per_step": 3 * ncell * e, "steps": ke},
+        "gpu_launches": launches,
+    }
+    ctx.close()
+    # the FP64 plain path on the same workload, fewer steps
+    if not args.no_f64 and prec == "f32":
+        w64 = workload(args.workload)
+        w64.precision = "f64"
+        ctx64 = setup_ctx(mm, w64, "f64", stream, 1e-6)
+        ctx64.rk45_attempts(max(1, args.warmup // 4))
+        k64 = max(3, min(args.steps, 100))
+        ms64 = timed_attempts(ctx64, torch, stream, k64)
+        line["f64"] = {"value": world * ncell * 7 * k64 / (ms64 / 1e3), "ms_per_step": ms64 / k64, "steps": k64}
+        ctx64.close()
+    if rank == 0 and not args.no_cpu:
+        v, n, dt, mesh = oracle_rate(w, 12.0, max_evals=8)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"{n} FP64 right-hand sides of the {mesh.nx}x{mesh.ny}x{mesh.nz} "
+                                          f"mesh (numpy oracle, FFT demag, one thread; tensor setup excluded)"}
+    return line
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="gb300")
+    ap.add_argument("--workload", default="film")
+    ap.add_argument("--precision", default=None)
+    ap.add_argument("--no-f64", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = None
+    if args.impl == "reference":
+        line = run_reference(args, rank, world)
+    else:
+        if world > 1:
+            import torch
+            import torch.distributed as dist
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+            dist.init_process_group("nccl")
+        line = run_gpu(args, rank, world, dist)
+        if dist:
+            dist.destroy_process_group()
+    if rank == 0 and line is not None:
+        print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

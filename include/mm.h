@@ -1,0 +1,191 @@
+/*
+ * mm.h -- C ABI of the GB300 finite-difference LLG solver core (libmm).
+ *
+ * What is computed (arXiv 2406.16064, MicroMagnetic.jl):
+ *   the Landau-Lifshitz-Gilbert right-hand side on a regular cell mesh,
+ *   dm/dt = -g~ m x H - alpha g~ m x (m x H), g~ = gamma/(1+alpha^2)
+ *   (Sec. "LLG equation", LL form), with the effective field (Eq. 1) the sum of
+ *     exchange             Sec. "Exchange energy", Eq. 5 (6-neighbour stencil)
+ *     interfacial DMI      Sec. "Dzyaloshinskii-Moriya Energy", Eq. 14
+ *     uniaxial / cubic     Sec. "Anisotropy"
+ *     Zeeman               Sec. "Zeeman energy"
+ *     demagnetising field  Sec. "Magnetostatic energy", Eqs. 6-8: the discrete
+ *                          convolution with the Newell tensor, evaluated by
+ *                          zero-padded FFTs;
+ *   integrated with adaptive Dormand-Prince RK45 and projection onto |m| = 1
+ *   after every accepted step (Sec. "LLG equation"), and the nudged elastic
+ *   band of Sec. "Miscellaneous".
+ *
+ * Conventions
+ *   Units are SI: lengths m, fields A/m, Ms A/m, A J/m, D J/m^2, K J/m^3,
+ *   gamma m/(A s), time s, energy J.  mu0 = 4e-7*pi.
+ *   A magnetisation state of one simulation is structure-of-arrays
+ *   m[c][z][y][x] (c = x,y,z; x fastest): 3*nx*ny*nz numbers.  A batch state
+ *   is the concatenation of its simulations' blocks in the order they were
+ *   added (mm_batch_layout gives the offsets).  Device buffers have the
+ *   context's precision (double for MM_F64, float for MM_F32); host buffers
+ *   are always double.
+ *   Boundaries are free: a neighbour outside the mesh or with Ms = 0 is
+ *   dropped from the exchange and DMI sums; cells with Ms = 0 have no field
+ *   and no torque.
+ *
+ * Ownership and errors
+ *   The library owns every device buffer it allocates; the *_dev arguments
+ *   are caller-owned device pointers (for example a torch tensor's
+ *   data_ptr()), contiguous, read or written on the context stream.  Host
+ *   pointers are read or written before the call returns.
+ *   Every call returns MM_OK (0) or a negative status; mm_last_error gives a
+ *   message.  No call falls back to the CPU; without a usable GPU mm_create
+ *   fails with MM_ECUDA.
+ */
+#ifndef MM_H
+#define MM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    MM_OK = 0,
+    MM_EINVAL = -1,     /* bad argument or call order */
+    MM_ENOMEM = -2,     /* device allocation failed */
+    MM_ECUDA = -3,      /* CUDA runtime error */
+    MM_ENAN = -4,       /* non-finite error norm in a step */
+    MM_ESTEP = -5,      /* step size underflow */
+    MM_ETIMEOUT = -6,   /* a bounded device wait ran out */
+    MM_EBOUNDS = -7     /* a checked kernel saw an out-of-range index */
+};
+
+enum { MM_F64 = 0, MM_F32 = 1 };          /* context precision */
+enum { MM_HOST = 0, MM_DEVICE = 1 };      /* where a buffer lives */
+enum { MM_DMI_NONE = 0, MM_DMI_INTERFACIAL = 1 };
+
+typedef struct mm_ctx mm_ctx;             /* opaque */
+
+/* Regular mesh of nx*ny*nz cells of size dx*dy*dz (FDMesh, Sec. "Design"). */
+typedef struct { int nx, ny, nz; double dx, dy, dz; } mm_mesh;
+
+/* Per-simulation material.  Kc is the cubic constant of the paper's form
+ * E = Kc (mx^4 + my^4 + mz^4) (Sec. "Anisotropy"); u is normalised by the
+ * library; precession = 0 drops the -g~ m x H term (relaxation / NEB);
+ * demag = 0 switches the demagnetising field off. */
+typedef struct {
+    double Ms, A, D;
+    int dmi_kind;
+    double Ku, u[3], Kc;
+    double H[3];
+    double alpha, gamma;
+    int precession;
+    int demag;
+} mm_material;
+
+/* Per-simulation integration status (mm_get_status). */
+typedef struct {
+    double t, h, err, max_dmdt;
+    long long n_accepted, n_rejected;
+    int status;           /* 0 running, 1 reached t_end, 2 relaxed, <0 error code */
+    int pad;
+} mm_status;
+
+/* Create a context on CUDA device `device` with precision MM_F64 or MM_F32.
+ * cuda_stream is a cudaStream_t (NULL = the library creates its own). */
+int mm_create(mm_ctx **out, int device, int precision, void *cuda_stream);
+int mm_destroy(mm_ctx *ctx);
+const char *mm_last_error(const mm_ctx *ctx);
+
+/* Add a simulation (mesh + material + optional per-cell Ms, host double
+ * array of nx*ny*nz values, NULL for uniform Ms = mat->Ms; Ms = 0 marks
+ * cells outside the shape, Listing 1).  Must precede mm_precompute_demag.
+ * Limits: each padded FFT length (next power of two >= 2n-1) <= 8192. */
+int mm_add_sim(mm_ctx *ctx, const mm_mesh *mesh, const mm_material *mat,
+               const double *Ms_cells, int *sim_id);
+
+/* Offsets (in elements) of each simulation's [3][N] block inside a batch
+ * state buffer, and the total length; offsets has room for n_sims entries. */
+int mm_batch_layout(const mm_ctx *ctx, long long *offsets, long long *total);
+int mm_num_sims(const mm_ctx *ctx);
+
+/* Applied field of one simulation (field sweeps, Listing 2), A/m. */
+int mm_set_field(mm_ctx *ctx, int sim_id, const double H[3]);
+
+/* Finalise the batch: allocate device state, compute the Newell tensor in
+ * FP64 for every distinct (mesh, cell) geometry (Eq. 7, Newell 1993; closed
+ * form near, tent-averaged dipole quadrature far) and its spectrum, and
+ * store -N^/(Px Py Pz) in the context precision.  Simulations with the same
+ * geometry share one spectrum. */
+int mm_precompute_demag(mm_ctx *ctx);
+
+/* Real-space tensor of one simulation's geometry, FP64, for offsets
+ * |i| < nx etc: out_host has 6*(2nz-1)*(2ny-1)*(2nx-1) doubles laid out
+ * [c][k+nz-1][j+ny-1][i+nx-1], c in (xx, yy, zz, xy, xz, yz). */
+int mm_newell_tensor(mm_ctx *ctx, int sim_id, double *out_host);
+
+/* Integration state m (sim_id = -1: the whole batch in batch layout). */
+int mm_set_m(mm_ctx *ctx, int sim_id, const void *m, int where);
+int mm_get_m(mm_ctx *ctx, int sim_id, void *m, int where);
+
+/* One right-hand-side evaluation (Eqs. 1-14 + LL form) of caller-owned
+ * device buffers: m_dev in, dmdt_dev out, heff_dev (nullable) out, all in
+ * the context precision, [3][N] per simulation (sim_id = -1: whole batch
+ * layout).  Asynchronous on the context stream. */
+int mm_rhs_eval(mm_ctx *ctx, int sim_id, const void *m_dev, void *dmdt_dev, void *heff_dev);
+
+/* The same evaluation with host double buffers (copies inside the call). */
+int mm_rhs_eval_host(mm_ctx *ctx, int sim_id, const double *m_host, double *dmdt_host,
+                     double *heff_host);
+
+/* Adaptive Dormand-Prince RK45 (Sec. "LLG equation").  mm_rk45_attempts
+ * issues n_attempts attempted steps for every running simulation without
+ * synchronising (7 right-hand sides each, the error-norm reduction, the
+ * controller and the projection, captured once as a CUDA graph).
+ * mm_rk45_step repeats attempts until every running simulation accepted one
+ * step.  rtol is the error tolerance of the step controller (max-norm of the
+ * embedded error, absolute = relative as |m| = 1). */
+int mm_rk45_setup(mm_ctx *ctx, double rtol, double t_end, double max_dmdt);
+int mm_rk45_attempts(mm_ctx *ctx, int n_attempts);
+int mm_rk45_step(mm_ctx *ctx, int *n_accepted, int *n_rejected);
+
+/* Integrate every simulation until t >= t_end (t_end > 0) or until
+ * max_i |dm/dt|_i < max_dmdt rad/s (max_dmdt > 0), at most max_steps
+ * attempts; sync_every attempts are issued between status checks. */
+int mm_relax(mm_ctx *ctx, double rtol, double t_end, double max_dmdt, long long max_steps,
+             int sync_every, long long *attempts_done);
+
+int mm_get_status(mm_ctx *ctx, int sim_id, mm_status *out);
+int mm_reset_time(mm_ctx *ctx);
+
+/* Energies of one simulation at its current m, J:
+ * E[0..6] = exchange, dmi, uniaxial, cubic, zeeman, demag, total. */
+int mm_energy(mm_ctx *ctx, int sim_id, double E[7]);
+
+/* Nudged elastic band (Sec. "Miscellaneous"; geodesic NEB of Bessarab et
+ * al. 2015 for the details the paper leaves out).  Makes simulations
+ * [first_sim, first_sim + n_images) one chain: their end images are fixed,
+ * the free images move along -alpha g~ m x (m x F) with F the effective
+ * field minus its tangent part plus the spring force k_spring (A/m per
+ * radian) along the tangent; the chain shares one step size. */
+int mm_neb_setup(mm_ctx *ctx, int first_sim, int n_images, double k_spring);
+/* n_steps attempted RK45 steps of every chain; energies_out (nullable,
+ * host) receives the energy of every simulation afterwards. */
+int mm_neb_relax(mm_ctx *ctx, double rtol, long long n_steps, double *energies_out);
+
+/* Profiling aid: runs `reps` RK45 attempts with direct launches (no graph)
+ * and a CUDA event recorded on the context stream after every kernel.
+ * ms[k] / counts[k] receive the summed duration and the launch count of each
+ * kernel kind k: 0 x-forward pass (with the RK prologue), 1 y forward,
+ * 2 z fused, 3 y inverse, 4 y fused (films), 5 x-inverse + field/torque
+ * epilogue, 6 step control, 7 projection, 8 NEB; arrays of 9 entries. */
+int mm_profile_attempts(mm_ctx *ctx, int reps, double *ms, long long *counts);
+
+/* Debugging aid: bounded-wait check.  Runs a kernel that waits on a device
+ * flag nobody sets, for at most `spins` polls, and returns MM_ETIMEOUT. */
+int mm_debug_bounded_wait(mm_ctx *ctx, long long spins);
+
+/* Number of kernels this context launched (graph launches count their
+ * kernel nodes). */
+long long mm_kernel_launches(const mm_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MM_H */

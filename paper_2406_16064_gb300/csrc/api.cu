@@ -1,0 +1,951 @@
+// C ABI of libmm (declared in include/mm.h): contexts, the batch layout,
+// work lists, the FP64 tensor precompute, right-hand-side evaluation, graph-
+// captured Dormand-Prince attempts, relaxation, energies and NEB chains.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "engine.cuh"
+#include "mm.h"
+
+using namespace mm;
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+char g_last_error[512] = "";
+
+int ilog2(int v) {
+    int l = 0;
+    while ((1 << l) < v) ++l;
+    return l;
+}
+
+// padded FFT length: the smallest power of two >= 2n - 1 (1 for n == 1 unless min2)
+int pad_len(int n, bool min2) {
+    if (n <= 1) return min2 ? 2 : 1;
+    int p = 1;
+    while (p < 2 * n - 1) p <<= 1;
+    return p;
+}
+
+int pow2floor(int v) {
+    int p = 1;
+    while (p * 2 <= v) p *= 2;
+    return p;
+}
+
+struct SimHost {
+    mm_mesh mesh;
+    mm_material mat;
+    std::vector<double> Ms;
+    SimDesc d;
+    int geom = -1;
+};
+
+struct Geom {
+    int nx, ny, nz;
+    double dx, dy, dz;
+    bool demag = false;
+    long long tens_off = -1;    // in the stored tensor (context precision)
+    long long oct_off = -1;     // in the FP64 octant table
+};
+
+}  // namespace
+
+struct mm_ctx {
+    int device = 0;
+    int precision = MM_F64;
+    size_t esz = 8;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::string err;
+    std::vector<SimHost> sims;
+    std::vector<Geom> geoms;
+    bool finalized = false;
+    long long total_elems = 0, spec_elems = 0, ms_elems = 0, tens_elems = 0, oct_elems = 0;
+    void *m = nullptr, *ybuf = nullptr, *k[7] = {}, *errp = nullptr, *spec = nullptr, *Msd = nullptr,
+         *tens = nullptr, *twd = nullptr, *twf = nullptr;
+    void *sc_in = nullptr, *sc_out = nullptr, *sc_h = nullptr, *heff = nullptr, *tau = nullptr;
+    void** kvec_dev = nullptr;
+    double* oct = nullptr;
+    SimDesc* desc_d = nullptr;
+    SimState* state_d = nullptr;
+    WorkItem *xi = nullptr, *y13i = nullptr, *zi = nullptr, *y2i = nullptr;
+    std::vector<WorkItem> xv, y13v, zv, y2v;
+    std::vector<int> xb, xc, y13b, y13c, zb, zc, y2b, y2c;
+    size_t smem_x = 0, smem_y13 = 0, smem_z = 0, smem_y2 = 0;
+    int *flag_d = nullptr, *status_d = nullptr;
+    unsigned long long* diag_d = nullptr;
+    cudaGraphExec_t rk_exec = nullptr;
+    bool rk_exec_neb = false;
+    long long graph_kernels = 0;
+    long long launches = 0;
+    bool neb = false;
+    double tensor_imag_ratio = 0.0;
+};
+
+namespace {
+
+int fail(mm_ctx* C, int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (C) C->err = buf;
+    snprintf(g_last_error, sizeof(g_last_error), "%s", buf);
+    return code;
+}
+
+#define CK(x)                                                                                       \
+    do {                                                                                            \
+        cudaError_t e_ = (x);                                                                       \
+        if (e_ != cudaSuccess) return fail(C, MM_ECUDA, "%s: %s", #x, cudaGetErrorString(e_));     \
+    } while (0)
+
+int dalloc(mm_ctx* C, void** p, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(C, MM_ENOMEM, "cudaMalloc(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
+    }
+    return MM_OK;
+}
+
+Launch make_launch(mm_ctx* C, int sim) {
+    Launch L;
+    L.stream = C->stream;
+    L.desc = C->desc_d;
+    L.state = C->state_d;
+    L.nsims = (int)C->sims.size();
+    auto set = [&](ItemSet& is, WorkItem* dev, const std::vector<int>& b, const std::vector<int>& c,
+                   const std::vector<WorkItem>& all) {
+        if (sim < 0) { is.dev = dev; is.count = (int)all.size(); }
+        else { is.dev = dev + b[sim]; is.count = c[sim]; }
+    };
+    set(L.x, C->xi, C->xb, C->xc, C->xv);
+    set(L.y13, C->y13i, C->y13b, C->y13c, C->y13v);
+    set(L.z, C->zi, C->zb, C->zc, C->zv);
+    set(L.y2, C->y2i, C->y2b, C->y2c, C->y2v);
+    L.smem_x = C->smem_x;
+    L.smem_y13 = C->smem_y13;
+    L.smem_z = C->smem_z;
+    L.smem_y2 = C->smem_y2;
+    L.tensor = C->tens;
+    L.Ms = C->Msd;
+    L.tw = C->precision == MM_F32 ? C->twf : C->twd;
+    L.spec = C->spec;
+    L.launches = &C->launches;
+    return L;
+}
+
+int check_ready(mm_ctx* C) {
+    if (!C) return MM_EINVAL;
+    if (!C->finalized) return fail(C, MM_EINVAL, "call mm_precompute_demag first");
+    return MM_OK;
+}
+
+// Every global index a work item can touch, checked on the host before any launch.
+int validate_items(mm_ctx* C) {
+    const size_t vsz = 2 * C->esz;
+    for (const WorkItem& w : C->xv) {
+        const SimDesc& d = C->sims[w.sim].d;
+        const int rows = d.ny * d.nz;
+        if (w.a < 0 || w.b < 1 || w.a + w.b > rows) return fail(C, MM_EBOUNDS, "x item rows out of range");
+        const long long last_cell = (long long)(w.a + w.b) * d.nx - 1;
+        if (d.off + 2LL * d.ncells + last_cell >= C->total_elems) return fail(C, MM_EBOUNDS, "x item state");
+        if (3ULL * w.b * d.Kx * vsz > C->smem_x) return fail(C, MM_EBOUNDS, "x item smem");
+        if (d.flags & F_DEMAG) {
+            const int row = w.a + w.b - 1, z = row / d.ny, y = row % d.ny;
+            const long long si = d.spec_off + (((2LL * d.nz + z) * d.Py + y) * d.Kx + d.Kx - 1);
+            if (si >= C->spec_elems) return fail(C, MM_EBOUNDS, "x item spectrum");
+        }
+        if (d.ms_off >= 0 && d.ms_off + d.ncells > C->ms_elems) return fail(C, MM_EBOUNDS, "Ms array");
+    }
+    for (const WorkItem& w : C->y13v) {
+        const SimDesc& d = C->sims[w.sim].d;
+        if (w.a < 0 || w.a >= d.nz || w.b < 0 || w.b >= d.Kx || w.c < 0 || w.c > 2)
+            return fail(C, MM_EBOUNDS, "y item range");
+        const long long si = d.spec_off + (((2LL * d.nz + d.nz - 1) * d.Py + d.Py - 1) * d.Kx + d.Kx - 1);
+        if (si >= C->spec_elems) return fail(C, MM_EBOUNDS, "y item spectrum");
+        if ((size_t)d.Py * d.Ty * vsz > C->smem_y13) return fail(C, MM_EBOUNDS, "y item smem");
+    }
+    for (const WorkItem& w : C->y2v) {
+        const SimDesc& d = C->sims[w.sim].d;
+        if (w.a != 0 || d.nz != 1 || w.b < 0 || w.b >= d.Kx) return fail(C, MM_EBOUNDS, "y2 item range");
+        const long long si = d.spec_off + (((2LL * d.nz + 0) * d.Py + d.Py - 1) * d.Kx + d.Kx - 1);
+        if (si >= C->spec_elems) return fail(C, MM_EBOUNDS, "y2 item spectrum");
+        if (3ULL * d.Py * d.Ty * vsz > C->smem_y2) return fail(C, MM_EBOUNDS, "y2 item smem");
+    }
+    for (const WorkItem& w : C->zv) {
+        const SimDesc& d = C->sims[w.sim].d;
+        if (w.a < 0 || w.a >= d.Py || w.b < 0 || w.b >= d.Kx) return fail(C, MM_EBOUNDS, "z item range");
+        const long long si = d.spec_off + (((2LL * d.nz + d.nz - 1) * d.Py + w.a) * d.Kx + d.Kx - 1);
+        if (si >= C->spec_elems) return fail(C, MM_EBOUNDS, "z item spectrum");
+        if (3ULL * d.Pz * d.Tz * vsz > C->smem_z) return fail(C, MM_EBOUNDS, "z item smem");
+    }
+    for (const SimHost& s : C->sims) {
+        const SimDesc& d = s.d;
+        if (d.flags & F_DEMAG) {
+            const long long plane = (long long)d.Pzh * d.Pyh * d.Kx;
+            if (d.tens_off + d.ncomp * plane > C->tens_elems) return fail(C, MM_EBOUNDS, "tensor block");
+        }
+        if (d.off + 3LL * d.ncells > C->total_elems) return fail(C, MM_EBOUNDS, "state block");
+    }
+    const size_t cap = 227 * 1024 - 4096;
+    if (C->smem_x > cap || C->smem_y13 > cap + 4096 || C->smem_y2 > cap + 4096 || C->smem_z > cap + 4096)
+        return fail(C, MM_EINVAL, "a padded FFT length needs more shared memory than one CTA has");
+    return MM_OK;
+}
+
+int upload_descs(mm_ctx* C) {
+    std::vector<SimDesc> h(C->sims.size());
+    for (size_t i = 0; i < C->sims.size(); ++i) h[i] = C->sims[i].d;
+    CK(cudaMemcpyAsync(C->desc_d, h.data(), h.size() * sizeof(SimDesc), cudaMemcpyHostToDevice, C->stream));
+    CK(cudaStreamSynchronize(C->stream));
+    return MM_OK;
+}
+
+int read_states(mm_ctx* C, std::vector<SimState>& st) {
+    st.resize(C->sims.size());
+    CK(cudaMemcpyAsync(st.data(), C->state_d, st.size() * sizeof(SimState), cudaMemcpyDeviceToHost, C->stream));
+    CK(cudaStreamSynchronize(C->stream));
+    return MM_OK;
+}
+
+int write_states(mm_ctx* C, const std::vector<SimState>& st) {
+    CK(cudaMemcpyAsync(C->state_d, st.data(), st.size() * sizeof(SimState), cudaMemcpyHostToDevice, C->stream));
+    CK(cudaStreamSynchronize(C->stream));
+    return MM_OK;
+}
+
+// FP64 octant table and stored spectrum of one geometry
+int precompute_geometry(mm_ctx* C, Geom& g, const SimDesc& d) {
+    launch_newell_octant(C->stream, g.nx, g.ny, g.nz, g.dx, g.dy, g.dz, C->oct + g.oct_off);
+    C->launches += 1;
+    CK(cudaGetLastError());
+    if (!g.demag) return MM_OK;
+    void* buf = nullptr;
+    const size_t bytes = (size_t)d.Px * d.Py * d.Pz * 16;
+    int rc = dalloc(C, &buf, bytes);
+    if (rc) return rc;
+    const double scale = 1.0 / ((double)d.Px * d.Py * d.Pz);
+    // the spectrum of an even/odd real tensor is real: compare the largest imaginary
+    // part of any component with the largest real part of all of them
+    CK(cudaMemsetAsync(C->diag_d, 0, 2 * sizeof(unsigned long long), C->stream));
+    for (int c = 0; c < d.ncomp; ++c) {
+        launch_newell_place(C->stream, C->oct + g.oct_off, c, g.nx, g.ny, g.nz, d.Px, d.Py, d.Pz, buf);
+        for (int ax = 0; ax < 3; ++ax) launch_fft_axis_f64(C->stream, buf, d.Px, d.Py, d.Pz, ax, C->twd);
+        char* out = (char*)C->tens + (size_t)g.tens_off * C->esz;
+        launch_newell_extract(C->stream, buf, c, d.Px, d.Py, d.Kx, d.Pyh, d.Pzh, scale, out,
+                              C->precision == MM_F32, C->diag_d, C->diag_d + 1);
+        C->launches += 5;
+        CK(cudaGetLastError());
+    }
+    unsigned long long hb[2];
+    CK(cudaMemcpyAsync(hb, C->diag_d, sizeof(hb), cudaMemcpyDeviceToHost, C->stream));
+    CK(cudaStreamSynchronize(C->stream));
+    double im, re;
+    memcpy(&im, &hb[0], 8);
+    memcpy(&re, &hb[1], 8);
+    const double worst = re > 0 ? im / re : 0.0;
+    cudaFree(buf);
+    C->tensor_imag_ratio = std::max(C->tensor_imag_ratio, worst);
+    if (!(worst < 1e-9)) return fail(C, MM_ECUDA, "tensor spectrum not real (|Im|/|Re| = %g)", worst);
+    return MM_OK;
+}
+
+template <typename T>
+void to_prec(const double* src, T* dst, size_t n) {
+    for (size_t i = 0; i < n; ++i) dst[i] = (T)src[i];
+}
+
+int ensure_scratch(mm_ctx* C) {
+    if (C->sc_in) return MM_OK;
+    const size_t b = (size_t)C->total_elems * C->esz;
+    int rc;
+    if ((rc = dalloc(C, &C->sc_in, b))) return rc;
+    if ((rc = dalloc(C, &C->sc_out, b))) return rc;
+    if ((rc = dalloc(C, &C->sc_h, b))) return rc;
+    return MM_OK;
+}
+
+int build_graph(mm_ctx* C) {
+    if (C->rk_exec && C->rk_exec_neb == C->neb) return MM_OK;
+    if (C->rk_exec) { cudaGraphExecDestroy(C->rk_exec); C->rk_exec = nullptr; }
+    Launch L = make_launch(C, -1);
+    RkBuffers B;
+    B.m = C->m;
+    B.ybuf = C->ybuf;
+    B.kvec_dev = C->kvec_dev;
+    for (int j = 0; j < 7; ++j) B.kvec[j] = C->k[j];
+    B.errp = C->errp;
+    B.heff = C->heff;
+    B.tau = C->tau;
+    const long long before = C->launches;
+    cudaGraph_t g;
+    CK(cudaStreamBeginCapture(C->stream, cudaStreamCaptureModeThreadLocal));
+    if (C->precision == MM_F32) {
+        if (C->neb) engine_neb_attempt<float>(L, B); else engine_attempt<float>(L, B);
+    } else {
+        if (C->neb) engine_neb_attempt<double>(L, B); else engine_attempt<double>(L, B);
+    }
+    cudaError_t e = cudaStreamEndCapture(C->stream, &g);
+    if (e != cudaSuccess) return fail(C, MM_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&C->rk_exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(C, MM_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    C->graph_kernels = C->launches - before;
+    C->launches = before;
+    C->rk_exec_neb = C->neb;
+    return MM_OK;
+}
+
+int launch_attempts(mm_ctx* C, long long n) {
+    int rc = build_graph(C);
+    if (rc) return rc;
+    for (long long i = 0; i < n; ++i) {
+        CK(cudaGraphLaunch(C->rk_exec, C->stream));
+        C->launches += C->graph_kernels;
+    }
+    return MM_OK;
+}
+
+int first_error(mm_ctx* C, const std::vector<SimState>& st) {
+    for (size_t i = 0; i < st.size(); ++i) {
+        if (st[i].status < 0) {
+            const int s = st[i].status;
+            return fail(C, s, "simulation %zu: %s", i,
+                        s == MM_ENAN ? "non-finite error norm" : (s == MM_ESTEP ? "step size underflow" : "error"));
+        }
+    }
+    return MM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mm_last_error(const mm_ctx* C) { return C ? C->err.c_str() : g_last_error; }
+
+int mm_create(mm_ctx** out, int device, int precision, void* cuda_stream) {
+    if (!out) return fail(nullptr, MM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (precision != MM_F64 && precision != MM_F32) return fail(nullptr, MM_EINVAL, "precision must be MM_F64 or MM_F32");
+    int n = 0;
+    cudaError_t e = cudaGetDeviceCount(&n);
+    if (e != cudaSuccess || n == 0) {
+        cudaGetLastError();
+        return fail(nullptr, MM_ECUDA, "no CUDA device: %s", cudaGetErrorString(e));
+    }
+    if (device < 0 || device >= n) return fail(nullptr, MM_EINVAL, "device %d out of range", device);
+    mm_ctx* C = new mm_ctx;
+    C->device = device;
+    C->precision = precision;
+    C->esz = precision == MM_F32 ? 4 : 8;
+    e = cudaSetDevice(device);
+    if (e != cudaSuccess) { delete C; return fail(nullptr, MM_ECUDA, "cudaSetDevice: %s", cudaGetErrorString(e)); }
+    if (cuda_stream) C->stream = (cudaStream_t)cuda_stream;
+    else {
+        e = cudaStreamCreateWithFlags(&C->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) { delete C; return fail(nullptr, MM_ECUDA, "stream: %s", cudaGetErrorString(e)); }
+        C->own_stream = true;
+    }
+    *out = C;
+    return MM_OK;
+}
+
+int mm_destroy(mm_ctx* C) {
+    if (!C) return MM_EINVAL;
+    cudaSetDevice(C->device);
+    if (C->stream) cudaStreamSynchronize(C->stream);
+    if (C->rk_exec) cudaGraphExecDestroy(C->rk_exec);
+    void* ptrs[] = {C->m, C->ybuf, C->errp, C->spec, C->Msd, C->tens, C->twd, C->twf, C->sc_in, C->sc_out,
+                    C->sc_h, C->heff, C->tau, C->kvec_dev, C->oct, C->desc_d, C->state_d, C->xi, C->y13i,
+                    C->zi, C->y2i, C->flag_d, C->status_d, C->diag_d};
+    for (void* p : ptrs) if (p) cudaFree(p);
+    for (int j = 0; j < 7; ++j) if (C->k[j]) cudaFree(C->k[j]);
+    if (C->own_stream) cudaStreamDestroy(C->stream);
+    delete C;
+    return MM_OK;
+}
+
+int mm_add_sim(mm_ctx* C, const mm_mesh* mesh, const mm_material* mat, const double* Ms_cells, int* sim_id) {
+    if (!C || !mesh || !mat) return fail(C, MM_EINVAL, "NULL argument");
+    if (C->finalized) return fail(C, MM_EINVAL, "mm_add_sim after mm_precompute_demag");
+    if (mesh->nx < 1 || mesh->ny < 1 || mesh->nz < 1) return fail(C, MM_EINVAL, "mesh dims must be >= 1");
+    if (!(mesh->dx > 0 && mesh->dy > 0 && mesh->dz > 0)) return fail(C, MM_EINVAL, "cell sizes must be > 0");
+    const long long ncells = (long long)mesh->nx * mesh->ny * mesh->nz;
+    if (ncells > (1LL << 30)) return fail(C, MM_EINVAL, "mesh too large");
+    if (!(mat->Ms >= 0) || !(mat->alpha >= 0) || !(mat->gamma > 0))
+        return fail(C, MM_EINVAL, "Ms, alpha must be >= 0 and gamma > 0");
+    SimHost s;
+    s.mesh = *mesh;
+    s.mat = *mat;
+    SimDesc& d = s.d;
+    memset(&d, 0, sizeof(d));
+    d.nx = mesh->nx; d.ny = mesh->ny; d.nz = mesh->nz;
+    d.ncells = (int)ncells;
+    d.Px = pad_len(d.nx, true);
+    d.Py = pad_len(d.ny, false);
+    d.Pz = pad_len(d.nz, false);
+    const int lim_yz = C->precision == MM_F32 ? 8192 : 4096;
+    if (d.Px > 8192 || d.Py > lim_yz || d.Pz > lim_yz)
+        return fail(C, MM_EINVAL, "padded FFT length too large (max 8192 along x, %d along y/z)", lim_yz);
+    d.lPx = ilog2(d.Px); d.lPy = ilog2(d.Py); d.lPz = ilog2(d.Pz);
+    d.Kx = d.Px / 2 + 1;
+    d.Pyh = d.Py / 2 + 1;
+    d.Pzh = d.Pz / 2 + 1;
+    d.ncomp = d.Pz > 1 ? 6 : 4;
+    double un = std::sqrt(mat->u[0] * mat->u[0] + mat->u[1] * mat->u[1] + mat->u[2] * mat->u[2]);
+    if (mat->Ku != 0.0 && !(un > 0)) return fail(C, MM_EINVAL, "anisotropy axis is zero");
+    for (int i = 0; i < 3; ++i) d.u[i] = un > 0 ? mat->u[i] / un : 0.0;
+    d.Ms = mat->Ms; d.A = mat->A; d.D = mat->D; d.Ku = mat->Ku; d.Kc = mat->Kc;
+    for (int i = 0; i < 3; ++i) d.H[i] = mat->H[i];
+    d.alpha = mat->alpha; d.gamma = mat->gamma;
+    d.dx = mesh->dx; d.dy = mesh->dy; d.dz = mesh->dz;
+    d.flags = (mat->demag ? F_DEMAG : 0) | (mat->dmi_kind == MM_DMI_INTERFACIAL ? F_DMI : 0) |
+              (mat->precession ? F_PREC : 0);
+    if (mat->dmi_kind != MM_DMI_NONE && mat->dmi_kind != MM_DMI_INTERFACIAL)
+        return fail(C, MM_EINVAL, "unsupported DMI kind");
+    d.group_begin = d.group_end = -1;
+    d.neb_index = -1;
+    d.ms_off = -1;
+    if (Ms_cells) {
+        s.Ms.assign(Ms_cells, Ms_cells + ncells);
+        for (double v : s.Ms) if (!(v >= 0)) return fail(C, MM_EINVAL, "per-cell Ms must be >= 0");
+        d.flags |= F_MSARR;
+    }
+    C->sims.push_back(std::move(s));
+    if (sim_id) *sim_id = (int)C->sims.size() - 1;
+    return MM_OK;
+}
+
+int mm_num_sims(const mm_ctx* C) { return C ? (int)C->sims.size() : MM_EINVAL; }
+
+int mm_batch_layout(const mm_ctx* C, long long* offsets, long long* total) {
+    if (!C) return MM_EINVAL;
+    long long off = 0;
+    for (size_t i = 0; i < C->sims.size(); ++i) {
+        if (offsets) offsets[i] = off;
+        off += 3LL * C->sims[i].d.ncells;
+    }
+    if (total) *total = off;
+    return MM_OK;
+}
+
+int mm_set_field(mm_ctx* C, int sim, const double H[3]) {
+    if (!C || !H) return MM_EINVAL;
+    if (sim < 0 || sim >= (int)C->sims.size()) return fail(C, MM_EINVAL, "bad sim id");
+    for (int i = 0; i < 3; ++i) {
+        C->sims[sim].mat.H[i] = H[i];
+        C->sims[sim].d.H[i] = H[i];
+    }
+    if (C->finalized) {
+        CK(cudaMemcpyAsync(&C->desc_d[sim].H[0], H, 3 * sizeof(double), cudaMemcpyHostToDevice, C->stream));
+        CK(cudaStreamSynchronize(C->stream));
+    }
+    return MM_OK;
+}
+
+int mm_precompute_demag(mm_ctx* C) {
+    if (!C) return MM_EINVAL;
+    if (C->finalized) return fail(C, MM_EINVAL, "already finalised");
+    if (C->sims.empty()) return fail(C, MM_EINVAL, "no simulations");
+    CK(cudaSetDevice(C->device));
+    const bool f32 = C->precision == MM_F32;
+    const int EB = f32 ? 4096 : 2048;          // complex elements per component per CTA
+    // geometries
+    std::map<std::tuple<int, int, int, double, double, double>, int> gmap;
+    for (SimHost& s : C->sims) {
+        auto key = std::make_tuple(s.mesh.nx, s.mesh.ny, s.mesh.nz, s.mesh.dx, s.mesh.dy, s.mesh.dz);
+        auto it = gmap.find(key);
+        if (it == gmap.end()) {
+            Geom g;
+            g.nx = s.mesh.nx; g.ny = s.mesh.ny; g.nz = s.mesh.nz;
+            g.dx = s.mesh.dx; g.dy = s.mesh.dy; g.dz = s.mesh.dz;
+            gmap[key] = (int)C->geoms.size();
+            C->geoms.push_back(g);
+            it = gmap.find(key);
+        }
+        s.geom = it->second;
+        if (s.d.flags & F_DEMAG) C->geoms[s.geom].demag = true;
+    }
+    // tensor and octant offsets
+    for (size_t gi = 0; gi < C->geoms.size(); ++gi) {
+        Geom& g = C->geoms[gi];
+        g.oct_off = C->oct_elems;
+        C->oct_elems += 6LL * g.nx * g.ny * g.nz;
+        if (g.demag) {
+            for (SimHost& s : C->sims)
+                if (s.geom == (int)gi) {
+                    g.tens_off = C->tens_elems;
+                    C->tens_elems += (long long)s.d.ncomp * s.d.Pzh * s.d.Pyh * s.d.Kx;
+                    break;
+                }
+        }
+    }
+    // per-simulation layout, tiles and work items
+    for (size_t i = 0; i < C->sims.size(); ++i) {
+        SimHost& s = C->sims[i];
+        SimDesc& d = s.d;
+        d.off = C->total_elems;
+        C->total_elems += 3LL * d.ncells;
+        d.tens_off = C->geoms[s.geom].tens_off;
+        if (d.flags & F_MSARR) { d.ms_off = C->ms_elems; C->ms_elems += d.ncells; }
+        const bool demag = (d.flags & F_DEMAG) != 0;
+        if (demag) { d.spec_off = C->spec_elems; C->spec_elems += 3LL * d.nz * d.Py * d.Kx; }
+        else d.spec_off = 0;
+        const int rows = d.ny * d.nz;
+        d.Rx = std::max(1, std::min(rows, EB / d.Kx));
+        const int kcap = std::min(32, 1 << ilog2(d.Kx));
+        if (d.Pz > 1) d.Ty = std::min(kcap, pow2floor(std::max(1, 3 * EB / d.Py)));
+        else d.Ty = std::min(kcap, pow2floor(std::max(1, EB / d.Py)));
+        d.Tz = std::min(kcap, pow2floor(std::max(1, EB / d.Pz)));
+        const int sid = (int)i;
+        C->xb.push_back((int)C->xv.size());
+        for (int r0 = 0; r0 < rows; r0 += d.Rx) C->xv.push_back({sid, r0, std::min(d.Rx, rows - r0), 0});
+        C->xc.push_back((int)C->xv.size() - C->xb.back());
+        C->y13b.push_back((int)C->y13v.size());
+        C->zb.push_back((int)C->zv.size());
+        C->y2b.push_back((int)C->y2v.size());
+        if (demag) {
+            if (d.Pz > 1) {
+                if (d.Py > 1)
+                    for (int z = 0; z < d.nz; ++z)
+                        for (int k0 = 0; k0 < d.Kx; k0 += d.Ty)
+                            for (int c = 0; c < 3; ++c) C->y13v.push_back({sid, z, k0, c});
+                for (int ky = 0; ky < d.Py; ++ky)
+                    for (int k0 = 0; k0 < d.Kx; k0 += d.Tz) C->zv.push_back({sid, ky, k0, 0});
+            } else if (d.Py > 1) {
+                for (int k0 = 0; k0 < d.Kx; k0 += d.Ty) C->y2v.push_back({sid, 0, k0, -1});
+            }
+        }
+        C->y13c.push_back((int)C->y13v.size() - C->y13b.back());
+        C->zc.push_back((int)C->zv.size() - C->zb.back());
+        C->y2c.push_back((int)C->y2v.size() - C->y2b.back());
+        const size_t vsz = 2 * C->esz;
+        C->smem_x = std::max(C->smem_x, 3 * (size_t)d.Rx * d.Kx * vsz);
+        if (demag && d.Pz > 1 && d.Py > 1) C->smem_y13 = std::max(C->smem_y13, (size_t)d.Py * d.Ty * vsz);
+        if (demag && d.Pz > 1) C->smem_z = std::max(C->smem_z, 3 * (size_t)d.Pz * d.Tz * vsz);
+        if (demag && d.Pz == 1 && d.Py > 1) C->smem_y2 = std::max(C->smem_y2, 3 * (size_t)d.Py * d.Ty * vsz);
+    }
+    int rc = validate_items(C);
+    if (rc) return rc;
+    // device memory
+    const size_t sb = (size_t)C->total_elems * C->esz;
+    if ((rc = dalloc(C, &C->m, sb))) return rc;
+    if ((rc = dalloc(C, &C->ybuf, sb))) return rc;
+    for (int j = 0; j < 7; ++j) if ((rc = dalloc(C, &C->k[j], sb))) return rc;
+    if ((rc = dalloc(C, &C->errp, sb))) return rc;
+    if ((rc = dalloc(C, &C->spec, (size_t)C->spec_elems * 2 * C->esz))) return rc;
+    if ((rc = dalloc(C, &C->Msd, (size_t)C->ms_elems * C->esz))) return rc;
+    if ((rc = dalloc(C, &C->tens, (size_t)C->tens_elems * C->esz))) return rc;
+    if ((rc = dalloc(C, (void**)&C->oct, (size_t)C->oct_elems * 8))) return rc;
+    if ((rc = dalloc(C, &C->twd, (size_t)MM_LMAX * 16))) return rc;
+    if ((rc = dalloc(C, &C->twf, (size_t)MM_LMAX * 8))) return rc;
+    if ((rc = dalloc(C, (void**)&C->kvec_dev, 7 * sizeof(void*)))) return rc;
+    if ((rc = dalloc(C, (void**)&C->desc_d, C->sims.size() * sizeof(SimDesc)))) return rc;
+    if ((rc = dalloc(C, (void**)&C->state_d, C->sims.size() * sizeof(SimState)))) return rc;
+    if ((rc = dalloc(C, (void**)&C->flag_d, 16))) return rc;
+    if ((rc = dalloc(C, (void**)&C->status_d, 16))) return rc;
+    if ((rc = dalloc(C, (void**)&C->diag_d, 16))) return rc;
+    auto up_items = [&](WorkItem** dst, const std::vector<WorkItem>& v) -> int {
+        int r = dalloc(C, (void**)dst, std::max<size_t>(1, v.size()) * sizeof(WorkItem));
+        if (r) return r;
+        if (!v.empty())
+            CK(cudaMemcpyAsync(*dst, v.data(), v.size() * sizeof(WorkItem), cudaMemcpyHostToDevice, C->stream));
+        return MM_OK;
+    };
+    if ((rc = up_items(&C->xi, C->xv))) return rc;
+    if ((rc = up_items(&C->y13i, C->y13v))) return rc;
+    if ((rc = up_items(&C->zi, C->zv))) return rc;
+    if ((rc = up_items(&C->y2i, C->y2v))) return rc;
+    CK(cudaMemcpyAsync(C->kvec_dev, C->k, 7 * sizeof(void*), cudaMemcpyHostToDevice, C->stream));
+    CK(cudaMemsetAsync(C->spec, 0, (size_t)C->spec_elems * 2 * C->esz, C->stream));
+    CK(cudaMemsetAsync(C->m, 0, sb, C->stream));
+    CK(cudaMemsetAsync(C->ybuf, 0, sb, C->stream));
+    CK(cudaMemsetAsync(C->errp, 0, sb, C->stream));
+    for (int j = 0; j < 7; ++j) CK(cudaMemsetAsync(C->k[j], 0, sb, C->stream));
+    // per-cell Ms
+    if (C->ms_elems) {
+        std::vector<double> all(C->ms_elems);
+        for (const SimHost& s : C->sims)
+            if (s.d.ms_off >= 0) std::copy(s.Ms.begin(), s.Ms.end(), all.begin() + s.d.ms_off);
+        if (f32) {
+            std::vector<float> fl(all.size());
+            to_prec(all.data(), fl.data(), all.size());
+            CK(cudaMemcpy(C->Msd, fl.data(), fl.size() * 4, cudaMemcpyHostToDevice));
+        } else {
+            CK(cudaMemcpy(C->Msd, all.data(), all.size() * 8, cudaMemcpyHostToDevice));
+        }
+    }
+    engine_set_attributes();
+    launch_twiddles(C->stream, C->twd, C->twf);
+    upload_gauss_legendre();
+    C->launches += 1;
+    CK(cudaGetLastError());
+    for (Geom& g : C->geoms) {
+        const SimDesc* d = nullptr;
+        for (const SimHost& s : C->sims) if (s.geom == (int)(&g - &C->geoms[0])) { d = &s.d; break; }
+        if ((rc = precompute_geometry(C, g, *d))) return rc;
+    }
+    if ((rc = upload_descs(C))) return rc;
+    std::vector<SimState> st(C->sims.size());
+    memset(st.data(), 0, st.size() * sizeof(SimState));
+    for (auto& x : st) x.rtol = 1e-6;
+    if ((rc = write_states(C, st))) return rc;
+    CK(cudaStreamSynchronize(C->stream));
+    C->finalized = true;
+    return MM_OK;
+}
+
+int mm_newell_tensor(mm_ctx* C, int sim, double* out) {
+    int rc = check_ready(C);
+    if (rc) return rc;
+    if (sim < 0 || sim >= (int)C->sims.size() || !out) return fail(C, MM_EINVAL, "bad arguments");
+    const Geom& g = C->geoms[C->sims[sim].geom];
+    const long long n = (long long)g.nx * g.ny * g.nz;
+    std::vector<double> oct(6 * n);
+    CK(cudaMemcpyAsync(oct.data(), C->oct + g.oct_off, oct.size() * 8, cudaMemcpyDeviceToHost, C->stream));
+    CK(cudaStreamSynchronize(C->stream));
+    const int X = 2 * g.nx - 1, Y = 2 * g.ny - 1, Z = 2 * g.nz - 1;
+    static const int odd[6] = {0, 0, 0, 3, 5, 6};
+    for (int c = 0; c < 6; ++c)
+        for (int k = -(g.nz - 1); k < g.nz; ++k)
+            for (int j = -(g.ny - 1); j < g.ny; ++j)
+                for (int i = -(g.nx - 1); i < g.nx; ++i) {
+                    double sgn = 1.0;
+                    if ((odd[c] & 1) && i < 0) sgn = -sgn;
+                    if ((odd[c] & 2) && j < 0) sgn = -sgn;
+                    if ((odd[c] & 4) && k < 0) sgn = -sgn;
+                    const long long src = c * n + ((long long)std::abs(k) * g.ny + std::abs(j)) * g.nx + std::abs(i);
+                    out[(((long long)c * Z + k + g.nz - 1) * Y + j + g.ny - 1) * X + i + g.nx - 1] = sgn * oct[src];
+                }
+    return MM_OK;
+}
+
+int mm_set_m(mm_ctx* C, int sim, const void* m, int where) {
+    int rc = check_ready(C);
+    if (rc) return rc;
+    if (!m || sim < -1 || sim >= (int)C->sims.size()) return fail(C, MM_EINVAL, "bad arguments");
+    const long long off = sim < 0 ? 0 : C->sims[sim].d.off;
+    const long long n = sim < 0 ? C->total_elems : 3LL * C->sims[sim].d.ncells;
+    char* dst = (char*)C->m + off * C->esz;
+    if (where == MM_DEVICE) {
+        CK(cudaMemcpyAsync(dst, m, n * C->esz, cudaMemcpyDeviceToDevice, C->stream));
+    } else if (C->precision == MM_F32) {
+        std::vector<float> f(n);
+        to_prec((const double*)m, f.data(), n);
+        CK(cudaMemcpyAsync(dst, f.data(), n * 4, cudaMemcpyHostToDevice, C->stream));
+    } else {
+        CK(cudaMemcpyAsync(dst, m, n * 8, cudaMemcpyHostToDevice, C->stream));
+    }
+    CK(cudaStreamSynchronize(C->stream));
+    return MM_OK;
+}
+
+int mm_get_m(mm_ctx* C, int sim, void* m, int where) {
+    int rc = check_ready(C);
+    if (rc) return rc;
+    if (!m || sim < -1 || sim >= (int)C->sims.size()) return fail(C, MM_EINVAL, "bad arguments");
+    const long long off = sim < 0 ? 0 : C->sims[sim].d.off;
+    const long long n = sim < 0 ? C->total_elems : 3LL * C->sims[sim].d.ncells;
+    const char* src = (const char*)C->m + off * C->esz;
+    if (where == MM_DEVICE) {
+        CK(cudaMemcpyAsync(m, src, n * C->esz, cudaMemcpyDeviceToDevice, C->stream));
+    } else if (C->precision == MM_F32) {
+        std::vector<float> f(n);
+        CK(cudaMemcpyAsync(f.data(), src, n * 4, cudaMemcpyDeviceToHost, C->stream));
+        CK(cudaStreamSynchronize(C->stream));
+        for (long long i = 0; i < n; ++i) ((double*)m)[i] = f[i];
+    } else {
+        CK(cudaMemcpyAsync(m, src, n * 8, cudaMemcpyDeviceToHost, C->stream));
+    }
+    CK(cudaStreamSynchronize(C->stream));
+    return MM_OK;
+}
+
+int mm_rhs_eval(mm_ctx* C, int sim, const void* m_dev, void* dmdt_dev, void* heff_dev) {
+    int rc = check_ready(C);
+    if (rc) return rc;
+    if (!m_dev || !dmdt_dev || sim < -1 || sim >= (int)C->sims.size()) return fail(C, MM_EINVAL, "bad arguments");
+    Launch L = make_launch(C, sim);
+    const long long adj = sim < 0 ? 0 : C->sims[sim].d.off;
+    if (C->precision == MM_F32)
+        engine_rhs<float>(L, 0, (const float*)m_dev, (float*)dmdt_dev, (float*)heff_dev, adj);
+    else
+        engine_rhs<double>(L, 0, (const double*)m_dev, (double*)dmdt_dev, (double*)heff_dev, adj);
+    CK(cudaGetLastError());
+    return MM_OK;
+}
+
+int mm_rhs_eval_host(mm_ctx* C, int sim, const double* m, double* dmdt, double* heff) {
+    int rc = check_ready(C);
+    if (rc) return rc;
+    if (!m || !dmdt || sim < -1 || sim >= (int)C->sims.size()) return fail(C, MM_EINVAL, "bad arguments");
+    if ((rc = ensure_scratch(C))) return rc;
+    const long long n = sim < 0 ? C->total_elems : 3LL * C->sims[sim].d.ncells;
+    if (C->precision == MM_F32) {
+        std::vector<float> f(n);
+        to_prec(m, f.data(), n);
+        CK(cudaMemcpyAsync(C->sc_in, f.data(), n * 4, cudaMemcpyHostToDevice, C->stream));
+        if ((rc = mm_rhs_eval(C, sim, C->sc_in, C->sc_out, heff ? C->sc_h : nullptr))) return rc;
+        CK(cudaMemcpyAsync(f.data(), C->sc_out, n * 4, cudaMemcpyDeviceToHost, C->stream));
+        CK(cudaStreamSynchronize(C->stream));
+        for (long long i = 0; i < n; ++i) dmdt[i] = f[i];
+        if (heff) {
+            CK(cudaMemcpyAsync(f.data(), C->sc_h, n * 4, cudaMemcpyDeviceToHost, C->stream));
+            CK(cudaStreamSynchronize(C->stream));
+            for (long long i = 0; i < n; ++i) heff[i] = f[i];
+        }
+    } else {
+        CK(cudaMemcpyAsync(C->sc_in, m, n * 8, cudaMemcpyHostToDevice, C->stream));
+        if ((rc = mm_rhs_eval(C, sim, C->sc_in, C->sc_out, heff ? C->sc_h : nullptr))) return rc;
+        CK(cudaMemcpyAsync(dmdt, C->sc_out, n * 8, cudaMemcpyDeviceToHost, C->stream));
+        if (heff) CK(cudaMemcpyAsync(heff, C->sc_h, n * 8, cudaMemcpyDeviceToHost, C->stream));
+        CK(cudaStreamSynchronize(C->stream));
+    }
+    return MM_OK;
+}
+
+int mm_rk45_setup(mm_ctx* C, double rtol, double t_end, double max_dmdt) {
+    int rc = check_ready(C);
+    if (rc) return rc;
+    if (!(rtol > 0)) return fail(C, MM_EINVAL, "rtol must be > 0");
+    std::vector<SimState> st;
+    if ((rc = read_states(C, st))) return rc;
+    for (auto& s : st) {
+        s.rtol = rtol;
+        s.t_end = t_end;
+        s.max_dmdt = max_dmdt;
+        if (s.status >= 0) s.status = 0;
+    }
+    return write_states(C, st);
+}
+
+int mm_reset_time(mm_ctx* C) {
+    int rc = check_ready(C);
+    if (rc) return rc;
+    std::vector<SimState> st;
+    if ((rc = read_states(C, st))) return rc;
+    for (auto& s : st) {
+        s.t = 0.0; s.h = 0.0; s.n_acc = 0; s.n_rej = 0; s.status = 0; s.accepted = 0;
+        s.err_bits = 0; s.maxk_bits = 0;
+    }
+    return write_states(C, st);
+}
+
+int mm_rk45_attempts(mm_ctx* C, int n) {
+    int rc = check_ready(C);
+    if (rc) return rc;
+    if (n < 0) return fail(C, MM_EINVAL, "n < 0");
+    return launch_attempts(C, n);
+}
+
+int mm_rk45_step(mm_ctx* C, int* n_acc, int* n_rej) {
+    int rc = check_ready(C);
+    if (rc) return rc;
+    std::vector<SimState> st;
+    if ((rc = read_states(C, st))) return rc;
+    std::vector<long long> acc0(st.size()), rej0(st.size());
+    for (size_t i = 0; i < st.size(); ++i) { acc0[i] = st[i].n_acc; rej0[i] = st[i].n_rej; }
+    for (int it = 0; it < 1000; ++it) {
+        bool any = false;
+        for (auto& s : st) any |= s.status == 0;
+        if (!any) break;
+        if ((rc = launch_attempts(C, 1))) return rc;
+        if ((rc = read_states(C, st))) return rc;
+        if ((rc = first_error(C, st))) return rc;
+        bool changed = false;
+        for (auto& s : st)
+            if (s.status == 0 && s.accepted) { s.status = 3; changed = true; }   // pause until all accepted
+        if (changed && (rc = write_states(C, st))) return rc;
+    }
+    long long a = 0, r = 0;
+    for (size_t i = 0; i < st.size(); ++i) {
+        if (st[i].status == 3) st[i].status = 0;
+        a += st[i].n_acc - acc0[i];
+        r += st[i].n_rej - rej0[i];
+    }
+    if ((rc = write_states(C, st))) return rc;
+    if (n_acc) *n_acc = (int)a;
+    if (n_rej) *n_rej = (int)r;
+    return MM_OK;
+}
+
+int mm_relax(mm_ctx* C, double rtol, double t_end, double max_dmdt, long long max_steps, int sync_every,
+             long long* done) {
+    int rc = check_ready(C);
+    if (rc) return rc;
+    if ((rc = mm_rk45_setup(C, rtol, t_end, max_dmdt))) return rc;
+    if (sync_every < 1) sync_every = 1;
+    long long att = 0;
+    std::vector<SimState> st;
+    while (att < max_steps) {
+        const long long n = std::min<long long>(sync_every, max_steps - att);
+        if ((rc = launch_attempts(C, n))) return rc;
+        att += n;
+        if ((rc = read_states(C, st))) return rc;
+        if ((rc = first_error(C, st))) return rc;
+        bool live = false;
+        for (auto& s : st) live |= s.status == 0;
+        if (!live) break;
+    }
+    if (done) *done = att;
+    return MM_OK;
+}
+
+int mm_get_status(mm_ctx* C, int sim, mm_status* out) {
+    int rc = check_ready(C);
+    if (rc) return rc;
+    if (!out || sim < 0 || sim >= (int)C->sims.size()) return fail(C, MM_EINVAL, "bad arguments");
+    SimState s;
+    CK(cudaMemcpyAsync(&s, C->state_d + sim, sizeof(s), cudaMemcpyDeviceToHost, C->stream));
+    CK(cudaStreamSynchronize(C->stream));
+    out->t = s.t; out->h = s.h; out->err = s.err; out->max_dmdt = s.maxk;
+    out->n_accepted = s.n_acc; out->n_rejected = s.n_rej;
+    out->status = s.status; out->pad = 0;
+    return MM_OK;
+}
+
+int mm_energy(mm_ctx* C, int sim, double E[7]) {
+    int rc = check_ready(C);
+    if (rc) return rc;
+    if (!E || sim < -1 || sim >= (int)C->sims.size()) return fail(C, MM_EINVAL, "bad arguments");
+    CK(cudaMemset2DAsync(&C->state_d[0].E[0], sizeof(SimState), 0, 8 * sizeof(double), C->sims.size(), C->stream));
+    Launch L = make_launch(C, sim);
+    if (C->precision == MM_F32)
+        engine_rhs<float>(L, MODE_ENERGY, (const float*)C->m, nullptr, nullptr, 0);
+    else
+        engine_rhs<double>(L, MODE_ENERGY, (const double*)C->m, nullptr, nullptr, 0);
+    CK(cudaGetLastError());
+    std::vector<SimState> st;
+    if ((rc = read_states(C, st))) return rc;
+    const int s = sim < 0 ? 0 : sim;
+    double tot = 0;
+    for (int i = 0; i < 6; ++i) { E[i] = st[s].E[i]; tot += E[i]; }
+    E[6] = tot;
+    return MM_OK;
+}
+
+int mm_neb_setup(mm_ctx* C, int first, int n, double k_spring) {
+    int rc = check_ready(C);
+    if (rc) return rc;
+    if (n < 3 || first < 0 || first + n > (int)C->sims.size()) return fail(C, MM_EINVAL, "bad chain range");
+    const SimDesc& d0 = C->sims[first].d;
+    for (int i = first; i < first + n; ++i) {
+        const SimDesc& d = C->sims[i].d;
+        if (d.nx != d0.nx || d.ny != d0.ny || d.nz != d0.nz || d.group_begin >= 0)
+            return fail(C, MM_EINVAL, "chain images must share one mesh and belong to no other chain");
+    }
+    for (int i = first; i < first + n; ++i) {
+        SimDesc& d = C->sims[i].d;
+        d.group_begin = first;
+        d.group_end = first + n;
+        d.neb_index = i - first;
+        d.k_spring = k_spring;
+    }
+    for (const SimHost& s : C->sims)
+        if (s.d.group_begin < 0) return fail(C, MM_EINVAL, "every simulation of a NEB context must be in a chain");
+    if (!C->heff) {
+        const size_t sb = (size_t)C->total_elems * C->esz;
+        if ((rc = dalloc(C, &C->heff, sb))) return rc;
+        if ((rc = dalloc(C, &C->tau, sb))) return rc;
+        CK(cudaMemset(C->heff, 0, sb));
+        CK(cudaMemset(C->tau, 0, sb));
+    }
+    C->neb = true;
+    return upload_descs(C);
+}
+
+int mm_neb_relax(mm_ctx* C, double rtol, long long n_steps, double* energies) {
+    int rc = check_ready(C);
+    if (rc) return rc;
+    if (!C->neb) return fail(C, MM_EINVAL, "call mm_neb_setup first");
+    if ((rc = mm_rk45_setup(C, rtol, 0.0, 0.0))) return rc;
+    if ((rc = launch_attempts(C, n_steps))) return rc;
+    std::vector<SimState> st;
+    if ((rc = read_states(C, st))) return rc;
+    if ((rc = first_error(C, st))) return rc;
+    if (energies) {
+        CK(cudaMemset2DAsync(&C->state_d[0].E[0], sizeof(SimState), 0, 8 * sizeof(double), C->sims.size(),
+                             C->stream));
+        Launch L = make_launch(C, -1);
+        if (C->precision == MM_F32)
+            engine_rhs<float>(L, MODE_ENERGY, (const float*)C->m, nullptr, nullptr, 0);
+        else
+            engine_rhs<double>(L, MODE_ENERGY, (const double*)C->m, nullptr, nullptr, 0);
+        CK(cudaGetLastError());
+        if ((rc = read_states(C, st))) return rc;
+        for (size_t i = 0; i < st.size(); ++i) {
+            double t = 0;
+            for (int j = 0; j < 6; ++j) t += st[i].E[j];
+            energies[i] = t;
+        }
+    }
+    return MM_OK;
+}
+
+int mm_profile_attempts(mm_ctx* C, int reps, double* ms, long long* counts) {
+    int rc = check_ready(C);
+    if (rc) return rc;
+    if (reps < 1 || !ms || !counts) return fail(C, MM_EINVAL, "bad arguments");
+    if (C->neb) return fail(C, MM_EINVAL, "profiling covers plain RK45 contexts");
+    ProfileHook H;
+    H.stream = C->stream;
+    H.cap = 64 * reps + 2;
+    std::vector<cudaEvent_t> ev(H.cap);
+    std::vector<int> kinds(H.cap, -1);
+    for (auto& e : ev) CK(cudaEventCreate(&e));
+    H.ev = ev.data();
+    H.kinds = kinds.data();
+    Launch L = make_launch(C, -1);
+    L.hook = &H;
+    RkBuffers B;
+    B.m = C->m; B.ybuf = C->ybuf; B.kvec_dev = C->kvec_dev; B.errp = C->errp;
+    for (int j = 0; j < 7; ++j) B.kvec[j] = C->k[j];
+    H.mark(-1);
+    for (int r = 0; r < reps; ++r) {
+        if (C->precision == MM_F32) engine_attempt<float>(L, B); else engine_attempt<double>(L, B);
+    }
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(C->stream));
+    for (int k = 0; k < KIND_COUNT; ++k) { ms[k] = 0.0; counts[k] = 0; }
+    for (int i = 1; i < H.used; ++i) {
+        float t = 0.f;
+        CK(cudaEventElapsedTime(&t, ev[i - 1], ev[i]));
+        if (kinds[i] >= 0 && kinds[i] < KIND_COUNT) { ms[kinds[i]] += t; counts[kinds[i]] += 1; }
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
+    return MM_OK;
+}
+
+int mm_debug_bounded_wait(mm_ctx* C, long long spins) {
+    int rc = check_ready(C);
+    if (rc) return rc;
+    CK(cudaMemsetAsync(C->flag_d, 0, 16, C->stream));
+    CK(cudaMemsetAsync(C->status_d, 0, 16, C->stream));
+    engine_bounded_wait(C->stream, C->flag_d, spins, C->status_d);
+    C->launches += 1;
+    CK(cudaGetLastError());
+    int st = 0;
+    CK(cudaMemcpyAsync(&st, C->status_d, sizeof(int), cudaMemcpyDeviceToHost, C->stream));
+    CK(cudaStreamSynchronize(C->stream));
+    if (st == MM_ETIMEOUT) return fail(C, MM_ETIMEOUT, "bounded device wait ran out after %lld polls", spins);
+    return MM_OK;
+}
+
+long long mm_kernel_launches(const mm_ctx* C) { return C ? C->launches : 0; }
+
+}  // extern "C"

@@ -1,0 +1,256 @@
+// Step control, projection and NEB kernels.
+//
+//  k_after_stage1  per simulation: max|dm/dt| of stage 1, relaxation stop
+//                  test (max|dm/dt| < max_dmdt), initial step
+//                  h0 = min(1e-12 s, 0.01 / max|dm/dt|).
+//  k_controller    per simulation: accept when err = max|h sum e_j k_j| / rtol
+//                  <= 1, h <- h clamp(0.9 err^-1/5, 0.2, 5), clip to t_end
+//                  (adaptive Dormand-Prince, Sec. "LLG equation").  NEB chain
+//                  members share err (max over the chain) and so h.
+//  k_project       m <- y5 / |y5| for accepted simulations (the projection onto
+//                  |m| = 1 after every successful step), norm in FP64.
+//  k_neb_tangent / k_neb_force
+//                  geodesic NEB (Sec. "Miscellaneous"): energy-weighted upwind
+//                  tangent projected onto the tangent planes, geodesic image
+//                  distances, force H - (H.tau) tau + k (L+ - L-) tau and the
+//                  precession-free LL torque -alpha g~ m x (m x F).
+#pragma once
+#include "passes.cuh"
+
+namespace mm {
+
+__device__ __forceinline__ unsigned long long group_max(const SimDesc* desc, const SimState* st, int s,
+                                                        bool err) {
+    unsigned long long b = err ? st[s].err_bits : st[s].maxk_bits;
+    const int gb = desc[s].group_begin, ge = desc[s].group_end;
+    if (gb >= 0) {
+        for (int i = gb; i < ge; ++i) {
+            const unsigned long long v = err ? st[i].err_bits : st[i].maxk_bits;
+            b = v > b ? v : b;
+        }
+    }
+    return b;
+}
+
+static __global__ void k_after_stage1(const SimDesc* desc, SimState* st, int nsims) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nsims) return;
+    SimState& S = st[s];
+    if (S.status != 0) return;
+    const double mk = bits_to_double(group_max(desc, st, s, false));
+    S.maxk = mk;
+    S.err_bits = 0ull;
+    if (!(mk == mk) || isinf(mk)) { S.status = -4; return; }
+    if (S.max_dmdt > 0.0 && mk < S.max_dmdt) { S.status = 2; return; }
+    if (S.h <= 0.0) {
+        double h = mk > 0.0 ? fmin(1e-12, 0.01 / mk) : 1e-12;
+        if (S.t_end > 0.0) h = fmin(h, S.t_end - S.t);
+        S.h = h;
+    }
+}
+
+static __global__ void k_controller(const SimDesc* desc, SimState* st, int nsims) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nsims) return;
+    SimState& S = st[s];
+    S.maxk_bits = 0ull;
+    if (S.status != 0) { S.accepted = 0; return; }
+    const double err = bits_to_double(group_max(desc, st, s, true)) / S.rtol;
+    S.err = err;
+    if (!(err == err) || isinf(err)) { S.status = -4; S.accepted = 0; return; }
+    const int acc = err <= 1.0;
+    double h = S.h;
+    if (acc) { S.t += h; S.n_acc += 1; } else { S.n_rej += 1; }
+    S.accepted = acc;
+    const double f = err == 0.0 ? 5.0 : fmin(5.0, fmax(0.2, 0.9 * pow(err, -0.2)));
+    h *= f;
+    if (S.t_end > 0.0) {
+        h = fmin(h, S.t_end - S.t);
+        if (S.t_end - S.t <= 1e-12 * S.t_end) S.status = 1;
+    }
+    S.h = h;
+    if (S.status == 0 && !(h > 1e-24)) S.status = -5;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(MM_THREADS) k_project(const SimDesc* __restrict__ desc, const SimState* st,
+                                                        const WorkItem* __restrict__ items, T* m, const T* y) {
+    const WorkItem w = items[blockIdx.x];
+    const SimState& S = st[w.sim];
+    if (!S.accepted) return;                       // rejected, or not running
+    const SimDesc& d = desc[w.sim];
+    if (d.group_begin >= 0 && (d.neb_index == 0 || d.neb_index == d.group_end - d.group_begin - 1))
+        return;                                    // NEB end images stay bit-fixed
+    const int N = d.ncells;
+    const long long c0 = (long long)w.a * d.nx;
+    const int cnt = w.b * d.nx;
+    for (int id = threadIdx.x; id < cnt; id += blockDim.x) {
+        const long long o = d.off + c0 + id;
+        const double a = y[o], b = y[o + N], c = y[o + 2 * (long long)N];
+        const double n = sqrt(a * a + b * b + c * c);
+        if (n > 0.0) {
+            const double inv = 1.0 / n;
+            m[o] = (T)(a * inv); m[o + N] = (T)(b * inv); m[o + 2 * (long long)N] = (T)(c * inv);
+        } else {
+            m[o] = (T)a; m[o + N] = (T)b; m[o + 2 * (long long)N] = (T)c;
+        }
+    }
+}
+
+// ------------------------------------------------------------------- NEB
+template <typename T>
+struct NebParams {
+    const SimDesc* __restrict__ desc;
+    SimState* state;
+    const WorkItem* __restrict__ items;
+    const T* ys;          // stage state of every image
+    const T* heff;        // effective field of every image
+    T* tau;               // raw projected tangent
+    T* kout;              // k_s
+    const T* errp;
+    const T* __restrict__ Ms;
+    int stage;
+    double e7;
+};
+
+static __global__ void k_neb_reset(SimState* st, int nsims) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nsims) return;
+    for (int i = 0; i < 8; ++i) st[s].E[i] = 0.0;
+    for (int i = 0; i < 4; ++i) st[s].neb[i] = 0.0;
+}
+
+__device__ __forceinline__ double total_energy(const SimState& S) {
+    return S.E[0] + S.E[1] + S.E[2] + S.E[3] + S.E[4] + S.E[5];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(MM_THREADS) k_neb_tangent(NebParams<T> p) {
+    __shared__ double red[MM_THREADS / 32];
+    const WorkItem w = p.items[blockIdx.x];
+    SimState* st = p.state;
+    if (st[w.sim].status != 0) return;
+    const SimDesc& d = p.desc[w.sim];
+    const int i = d.neb_index, n = d.group_end - d.group_begin;
+    const int N = d.ncells;
+    const bool free_img = i > 0 && i < n - 1;
+    const bool has_next = i < n - 1;
+    double wp = 0.0, wm = 0.0;                   // tau = wp * tau+ + wm * tau-
+    if (free_img) {
+        const double Ep = total_energy(st[w.sim + 1]), E0 = total_energy(st[w.sim]),
+                     Em = total_energy(st[w.sim - 1]);
+        if (Ep > E0 && E0 > Em) { wp = 1.0; wm = 0.0; }
+        else if (Ep < E0 && E0 < Em) { wp = 0.0; wm = 1.0; }
+        else {
+            const double dmax = fmax(fabs(Ep - E0), fabs(Em - E0));
+            const double dmin = fmin(fabs(Ep - E0), fabs(Em - E0));
+            if (Ep > Em) { wp = dmax; wm = dmin; } else { wp = dmin; wm = dmax; }
+        }
+    }
+    const long long off = d.off;
+    const long long offn = has_next ? p.desc[w.sim + 1].off : off;
+    const long long offp = free_img ? p.desc[w.sim - 1].off : off;
+    double t2 = 0.0, ht = 0.0, th2 = 0.0;
+    const long long c0 = (long long)w.a * d.nx;
+    const int cnt = w.b * d.nx;
+    for (int id = threadIdx.x; id < cnt; id += blockDim.x) {
+        const long long cell = c0 + id;
+        double m[3], mn[3], mp[3];
+        for (int c = 0; c < 3; ++c) {
+            m[c] = p.ys[off + c * (long long)N + cell];
+            mn[c] = p.ys[offn + c * (long long)N + cell];
+            mp[c] = p.ys[offp + c * (long long)N + cell];
+        }
+        if (has_next) {
+            const double cx = m[1] * mn[2] - m[2] * mn[1], cy = m[2] * mn[0] - m[0] * mn[2],
+                         cz = m[0] * mn[1] - m[1] * mn[0];
+            const double th = atan2(sqrt(cx * cx + cy * cy + cz * cz), m[0] * mn[0] + m[1] * mn[1] + m[2] * mn[2]);
+            th2 += th * th;
+        }
+        if (free_img) {
+            double t[3];
+            for (int c = 0; c < 3; ++c) t[c] = wp * (mn[c] - m[c]) + wm * (m[c] - mp[c]);
+            const double tm = t[0] * m[0] + t[1] * m[1] + t[2] * m[2];
+            for (int c = 0; c < 3; ++c) t[c] -= tm * m[c];
+            for (int c = 0; c < 3; ++c) {
+                p.tau[off + c * (long long)N + cell] = (T)t[c];
+                t2 += t[c] * t[c];
+                ht += (double)p.heff[off + c * (long long)N + cell] * t[c];
+            }
+        }
+    }
+    const double s0 = block_sum(t2, red);
+    if (threadIdx.x == 0) atomicAdd(&st[w.sim].neb[0], s0);
+    const double s1 = block_sum(ht, red);
+    if (threadIdx.x == 0) atomicAdd(&st[w.sim].neb[1], s1);
+    const double s2 = block_sum(th2, red);
+    if (threadIdx.x == 0) atomicAdd(&st[w.sim].neb[2], s2);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(MM_THREADS) k_neb_force(NebParams<T> p) {
+    __shared__ unsigned long long red[MM_THREADS / 32];
+    const WorkItem w = p.items[blockIdx.x];
+    SimState* st = p.state;
+    if (st[w.sim].status != 0) return;
+    const SimDesc& d = p.desc[w.sim];
+    const int i = d.neb_index, n = d.group_end - d.group_begin;
+    const int N = d.ncells;
+    const bool free_img = i > 0 && i < n - 1;
+    const bool msarr = (d.flags & F_MSARR) != 0;
+    const double agt = d.alpha * d.gamma / (1.0 + d.alpha * d.alpha);
+    double inv_t = 0.0, Ht = 0.0, spring = 0.0;
+    if (free_img) {
+        const double t2 = st[w.sim].neb[0];
+        inv_t = t2 > 0.0 ? 1.0 / sqrt(t2) : 0.0;
+        Ht = st[w.sim].neb[1] * inv_t;
+        spring = d.k_spring * (sqrt(st[w.sim].neb[2]) - sqrt(st[w.sim - 1].neb[2]));
+    }
+    const double hstep = st[w.sim].h;
+    const long long off = d.off;
+    const long long c0 = (long long)w.a * d.nx;
+    const int cnt = w.b * d.nx;
+    unsigned long long vmax = 0ull;
+    for (int id = threadIdx.x; id < cnt; id += blockDim.x) {
+        const long long cell = c0 + id;
+        const bool mag = !msarr || p.Ms[d.ms_off + cell] > (T)0;
+        double k[3] = {0.0, 0.0, 0.0};
+        if (free_img && mag) {
+            double m[3], F[3];
+            for (int c = 0; c < 3; ++c) {
+                m[c] = p.ys[off + c * (long long)N + cell];
+                const double tc = (double)p.tau[off + c * (long long)N + cell] * inv_t;
+                F[c] = (double)p.heff[off + c * (long long)N + cell] - Ht * tc + spring * tc;
+            }
+            const double c0x = m[1] * F[2] - m[2] * F[1], c0y = m[2] * F[0] - m[0] * F[2],
+                         c0z = m[0] * F[1] - m[1] * F[0];
+            k[0] = -agt * (m[1] * c0z - m[2] * c0y);
+            k[1] = -agt * (m[2] * c0x - m[0] * c0z);
+            k[2] = -agt * (m[0] * c0y - m[1] * c0x);
+        }
+        for (int c = 0; c < 3; ++c) p.kout[off + c * (long long)N + cell] = (T)k[c];
+        if (p.stage == 1) {
+            const double v = sqrt(k[0] * k[0] + k[1] * k[1] + k[2] * k[2]);
+            vmax = umax64(vmax, (unsigned long long)__double_as_longlong(v));
+        } else if (p.stage == 7) {
+            for (int c = 0; c < 3; ++c) {
+                const double v = fabs(hstep * ((double)p.errp[off + c * (long long)N + cell] + p.e7 * (double)(T)k[c]));
+                vmax = umax64(vmax, (unsigned long long)__double_as_longlong(v));
+            }
+        }
+    }
+    if (p.stage == 1 || p.stage == 7) {
+        const unsigned long long r = block_max_u64(vmax, red);
+        if (threadIdx.x == 0) atomicMax(p.stage == 1 ? &st[w.sim].maxk_bits : &st[w.sim].err_bits, r);
+    }
+}
+
+// A wait on a device flag that nothing sets, bounded by `spins` polls;
+// reports MM_ETIMEOUT through *status instead of hanging.
+static __global__ void k_bounded_wait(volatile int* flag, long long spins, int* status) {
+    long long i = 0;
+    while (*flag == 0 && i < spins) ++i;
+    *status = (*flag == 0) ? -6 : 0;
+}
+
+}  // namespace mm

@@ -1,0 +1,180 @@
+// Kernel sequencing of the right-hand side and of one RK45 attempt.
+#pragma once
+#include <cstring>
+
+#include "control.cuh"
+#include "engine.cuh"
+
+namespace mm {
+
+// Dormand & Prince (1980) RK5(4)7M: a_{s,j} for stages 2..7 and the error
+// weights e_j = b_j - bhat_j.
+static const double kDP_A[7][6] = {
+    {0, 0, 0, 0, 0, 0},
+    {1.0 / 5, 0, 0, 0, 0, 0},
+    {3.0 / 40, 9.0 / 40, 0, 0, 0, 0},
+    {44.0 / 45, -56.0 / 15, 32.0 / 9, 0, 0, 0},
+    {19372.0 / 6561, -25360.0 / 2187, 64448.0 / 6561, -212.0 / 729, 0, 0},
+    {9017.0 / 3168, -355.0 / 33, 46732.0 / 5247, 49.0 / 176, -5103.0 / 18656, 0},
+    {35.0 / 384, 0, 500.0 / 1113, 125.0 / 192, -2187.0 / 6784, 11.0 / 84},
+};
+static const double kDP_E[7] = {71.0 / 57600, 0, -71.0 / 16695, 71.0 / 1920, -17253.0 / 339200, 22.0 / 525,
+                                -1.0 / 40};
+
+template <typename T>
+static PassParams<T> base_params(const Launch& L) {
+    PassParams<T> p;
+    memset(&p, 0, sizeof(p));
+    p.desc = L.desc;
+    p.state = L.state;
+    p.spec = reinterpret_cast<V2<T>*>(L.spec);
+    p.tensor = reinterpret_cast<const T*>(L.tensor);
+    p.Ms = reinterpret_cast<const T*>(L.Ms);
+    p.tw = reinterpret_cast<const V2<T>*>(L.tw);
+    for (int j = 0; j < 7; ++j) p.e[j] = kDP_E[j];
+    return p;
+}
+
+template <typename T>
+static void issue_passes(const Launch& L, PassParams<T> p, const T* ys, bool include_xinv = true) {
+    if (L.x.count == 0) return;
+    cudaStream_t s = L.stream;
+    ProfileHook* hk = L.hook;
+    p.items = L.x.dev;
+    k_xfwd<T><<<L.x.count, MM_THREADS, L.smem_x, s>>>(p);
+    if (hk) hk->mark(KIND_XFWD);
+    long long n = 1;
+    if (L.y13.count) {
+        p.items = L.y13.dev;
+        k_ycol<T, 0><<<L.y13.count, MM_THREADS, L.smem_y13, s>>>(p);
+        if (hk) hk->mark(KIND_YFWD);
+        ++n;
+    }
+    if (L.z.count) {
+        p.items = L.z.dev;
+        k_zcol<T><<<L.z.count, MM_THREADS, L.smem_z, s>>>(p);
+        if (hk) hk->mark(KIND_ZCOL);
+        ++n;
+    }
+    if (L.y13.count) {
+        p.items = L.y13.dev;
+        k_ycol<T, 1><<<L.y13.count, MM_THREADS, L.smem_y13, s>>>(p);
+        if (hk) hk->mark(KIND_YINV);
+        ++n;
+    }
+    if (L.y2.count) {
+        p.items = L.y2.dev;
+        k_ycol<T, 2><<<L.y2.count, MM_THREADS, L.smem_y2, s>>>(p);
+        if (hk) hk->mark(KIND_YFUSED);
+        ++n;
+    }
+    if (include_xinv) {
+        p.items = L.x.dev;
+        k_xinv<T><<<L.x.count, MM_THREADS, L.smem_x, s>>>(p, ys);
+        if (hk) hk->mark(KIND_XINV);
+        ++n;
+    }
+    if (L.launches) *L.launches += n;
+}
+
+template <typename T>
+void engine_rhs(const Launch& L, int mode, const T* m, T* dmdt, T* heff, long long off_adjust) {
+    PassParams<T> p = base_params<T>(L);
+    p.mode = mode;
+    p.m = m;
+    p.kout = dmdt;
+    p.heff = heff;
+    p.off_adjust = off_adjust;
+    issue_passes<T>(L, p, m);
+}
+
+static inline int blocks_for(int n) { return (n + 127) / 128; }
+
+template <typename T>
+void engine_attempt(const Launch& L, const RkBuffers& B) {
+    cudaStream_t s = L.stream;
+    for (int st = 1; st <= 7; ++st) {
+        PassParams<T> p = base_params<T>(L);
+        p.mode = MODE_RK;
+        p.stage = st;
+        p.nk = st - 1;
+        p.write_y = st > 1;
+        for (int j = 0; j < 6; ++j) p.a[j] = kDP_A[st - 1][j];
+        p.m = reinterpret_cast<const T*>(B.m);
+        p.ybuf = reinterpret_cast<T*>(B.ybuf);
+        p.kvec = reinterpret_cast<T* const*>(B.kvec_dev);
+        p.kout = reinterpret_cast<T*>(B.kvec[st - 1]);
+        p.errp = reinterpret_cast<T*>(B.errp);
+        const T* ys = st == 1 ? reinterpret_cast<const T*>(B.m) : reinterpret_cast<const T*>(B.ybuf);
+        issue_passes<T>(L, p, ys);
+        if (st == 1) {
+            k_after_stage1<<<blocks_for(L.nsims), 128, 0, s>>>(L.desc, L.state, L.nsims);
+            if (L.hook) L.hook->mark(KIND_CONTROL);
+            if (L.launches) *L.launches += 1;
+        }
+    }
+    k_controller<<<blocks_for(L.nsims), 128, 0, s>>>(L.desc, L.state, L.nsims);
+    if (L.hook) L.hook->mark(KIND_CONTROL);
+    k_project<T><<<L.x.count, MM_THREADS, 0, s>>>(L.desc, L.state, L.x.dev, reinterpret_cast<T*>(B.m),
+                                                  reinterpret_cast<const T*>(B.ybuf));
+    if (L.hook) L.hook->mark(KIND_PROJECT);
+    if (L.launches) *L.launches += 2;
+}
+
+template <typename T>
+void engine_neb_attempt(const Launch& L, const RkBuffers& B) {
+    cudaStream_t s = L.stream;
+    for (int st = 1; st <= 7; ++st) {
+        k_neb_reset<<<blocks_for(L.nsims), 128, 0, s>>>(L.state, L.nsims);
+        PassParams<T> p = base_params<T>(L);
+        p.mode = MODE_NEB;
+        p.stage = st;
+        p.nk = st - 1;
+        p.write_y = st > 1;
+        for (int j = 0; j < 6; ++j) p.a[j] = kDP_A[st - 1][j];
+        p.m = reinterpret_cast<const T*>(B.m);
+        p.ybuf = reinterpret_cast<T*>(B.ybuf);
+        p.kvec = reinterpret_cast<T* const*>(B.kvec_dev);
+        p.kout = nullptr;
+        p.heff = reinterpret_cast<T*>(B.heff);
+        p.errp = reinterpret_cast<T*>(B.errp);
+        const T* ys = st == 1 ? reinterpret_cast<const T*>(B.m) : reinterpret_cast<const T*>(B.ybuf);
+        issue_passes<T>(L, p, ys);
+        NebParams<T> q;
+        q.desc = L.desc;
+        q.state = L.state;
+        q.items = L.x.dev;
+        q.ys = ys;
+        q.heff = reinterpret_cast<const T*>(B.heff);
+        q.tau = reinterpret_cast<T*>(B.tau);
+        q.kout = reinterpret_cast<T*>(B.kvec[st - 1]);
+        q.errp = reinterpret_cast<const T*>(B.errp);
+        q.Ms = reinterpret_cast<const T*>(L.Ms);
+        q.stage = st;
+        q.e7 = kDP_E[6];
+        k_neb_tangent<T><<<L.x.count, MM_THREADS, 0, s>>>(q);
+        k_neb_force<T><<<L.x.count, MM_THREADS, 0, s>>>(q);
+        if (L.launches) *L.launches += 3;
+        if (st == 1) {
+            k_after_stage1<<<blocks_for(L.nsims), 128, 0, s>>>(L.desc, L.state, L.nsims);
+            if (L.launches) *L.launches += 1;
+        }
+    }
+    k_controller<<<blocks_for(L.nsims), 128, 0, s>>>(L.desc, L.state, L.nsims);
+    k_project<T><<<L.x.count, MM_THREADS, 0, s>>>(L.desc, L.state, L.x.dev, reinterpret_cast<T*>(B.m),
+                                                  reinterpret_cast<const T*>(B.ybuf));
+    if (L.launches) *L.launches += 2;
+}
+
+template <typename T>
+static void set_attrs() {
+    const int mx = 227 * 1024;
+    cudaFuncSetAttribute(k_xfwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_xinv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx - 4096);
+    cudaFuncSetAttribute(k_ycol<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_ycol<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_ycol<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_zcol<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+}
+
+}  // namespace mm

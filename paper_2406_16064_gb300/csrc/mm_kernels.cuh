@@ -1,0 +1,216 @@
+// Internal device-side definitions of libmm: simulation descriptors, kernel
+// parameters, complex helpers and the in-place shared-memory FFT.
+//
+// Layouts (all simulations of a batch live in one set of buffers):
+//   state  [3][nz][ny][nx] per simulation at element offset SimDesc::off
+//   spectrum [3][nz][Py][Kx] complex per simulation at SimDesc::spec_off;
+//          rows y < ny hold the x-transform, all Py rows the xy-transform
+//   tensor [ncomp][Pz/2+1][Py/2+1][Kx] real per geometry at SimDesc::tens_off,
+//          ncomp = 6 (xx yy zz xy xz yz) or 4 when Pz == 1 (xz = yz = 0),
+//          holding -N^(k)/(Px Py Pz); other bins follow from the parities
+//          of the Newell tensor (diagonal even, xy odd in kx and ky, xz odd
+//          in kx and kz, yz odd in ky and kz).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define MM_LOG2_LMAX 13
+#define MM_LMAX (1 << MM_LOG2_LMAX)
+#define MM_THREADS 256
+
+#ifndef MM_CHECKED
+#define MM_CHECKED 0
+#endif
+
+enum { F_DEMAG = 1, F_DMI = 2, F_PREC = 4, F_MSARR = 8 };
+
+struct SimDesc {
+    int nx, ny, nz, ncells;
+    int Px, Py, Pz;
+    int lPx, lPy, lPz;       // log2 of the padded sizes
+    int Kx;                  // Px/2 + 1
+    int Pyh, Pzh;            // tensor bins along y and z
+    int ncomp;               // 4 or 6
+    int flags;
+    int Rx;                  // rows per CTA in the x passes
+    int Ty;                  // kx columns per CTA in the y passes
+    int Tz;                  // kx columns per CTA in the z pass
+    int group_begin, group_end;   // NEB chain members [begin, end), -1 if none
+    int neb_index;                // image index in its chain
+    int pad0;
+    long long off;           // element offset of the [3][N] state block
+    long long spec_off;      // complex offset of the spectrum block
+    long long ms_off;        // offset into the per-cell Ms array, -1 if uniform
+    long long tens_off;      // element offset of the tensor block
+    double Ms, A, D, Ku, u[3], Kc, H[3], alpha, gamma;
+    double dx, dy, dz;
+    double k_spring;
+};
+
+struct SimState {
+    double t, h, t_end, rtol, max_dmdt;
+    double err, maxk;
+    unsigned long long err_bits;     // max of |h sum e_j k_j| as ordered bits (NaN wins)
+    unsigned long long maxk_bits;    // max |dm/dt| over cells at stage 1
+    long long n_acc, n_rej;
+    int status, accepted, pad1, pad2;
+    double E[8];                     // energy accumulators (ex, dmi, uni, cub, zee, demag)
+    double neb[4];                   // NEB reductions: |tau|^2, H.tau, distance to next image
+};
+
+struct WorkItem { int sim, a, b, c; };
+
+template <typename T> struct alignas(2 * sizeof(T)) V2 { T x, y; };
+
+template <typename T> __device__ __forceinline__ V2<T> mk(T x, T y) { V2<T> r; r.x = x; r.y = y; return r; }
+template <typename T> __device__ __forceinline__ V2<T> operator+(V2<T> a, V2<T> b) { return mk<T>(a.x + b.x, a.y + b.y); }
+template <typename T> __device__ __forceinline__ V2<T> operator-(V2<T> a, V2<T> b) { return mk<T>(a.x - b.x, a.y - b.y); }
+template <typename T> __device__ __forceinline__ V2<T> cmul(V2<T> a, V2<T> b) {
+    return mk<T>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename T> __device__ __forceinline__ V2<T> cconj(V2<T> a) { return mk<T>(a.x, -a.y); }
+template <typename T> __device__ __forceinline__ V2<T> cscale(V2<T> a, T s) { return mk<T>(a.x * s, a.y * s); }
+// multiply by -i (forward) or +i (inverse)
+template <typename T, bool INV> __device__ __forceinline__ V2<T> mul_mi(V2<T> a) {
+    return INV ? mk<T>(-a.y, a.x) : mk<T>(a.y, -a.x);
+}
+
+__device__ __forceinline__ int bitrev(int v, int bits) {
+    return bits == 0 ? 0 : (int)(__brev((unsigned)v) >> (32 - bits));
+}
+
+// twiddle W_M^k = exp(-+2 pi i k / M), M = 2^logM, from the table of exp(-2 pi i j / LMAX)
+template <typename T, bool INV>
+__device__ __forceinline__ V2<T> twid(const V2<T>* __restrict__ tw, int k, int logM) {
+    V2<T> w = tw[k << (MM_LOG2_LMAX - logM)];
+    if (INV) w.y = -w.y;
+    return w;
+}
+
+// Map a linear butterfly index to (sequence, group).  Sequences stored with
+// unit element stride are walked group-fastest; interleaved sequences
+// (element stride > 1) sequence-fastest, so a warp touches adjacent words.
+__device__ __forceinline__ void split_id(int id, int ngroups, int nseq, int estride, int& seq, int& g) {
+    if (estride == 1) { seq = id / ngroups; g = id - seq * ngroups; }
+    else { g = id / nseq; seq = id - g * nseq; }
+}
+
+// In-place decimation-in-time FFT of nseq sequences of length 2^logL held in
+// shared memory in BIT-REVERSED order; leaves them in natural order.
+// Radix-2 stages are fused in pairs (radix-4 butterflies), one leading
+// radix-2 stage when logL is odd.  Unnormalised.  Ends with __syncthreads().
+template <typename T, bool INV>
+__device__ void fft_dit(V2<T>* buf, int logL, int nseq, int sstride, int estride,
+                        const V2<T>* __restrict__ tw) {
+    const int L = 1 << logL;
+    int lg = 0;
+    if (logL & 1) {
+        const int ng = L >> 1, tot = ng * nseq;
+        for (int id = threadIdx.x; id < tot; id += blockDim.x) {
+            int seq, g; split_id(id, ng, nseq, estride, seq, g);
+            V2<T>* p = buf + seq * sstride;
+            const int j0 = (2 * g) * estride, j1 = j0 + estride;
+            V2<T> a = p[j0], b = p[j1];
+            p[j0] = a + b; p[j1] = a - b;
+        }
+        __syncthreads();
+        lg = 1;
+    }
+    while (lg < logL) {
+        const int s = 1 << lg;
+        const int ng = L >> 2, tot = ng * nseq;
+        for (int id = threadIdx.x; id < tot; id += blockDim.x) {
+            int seq, g; split_id(id, ng, nseq, estride, seq, g);
+            V2<T>* p = buf + seq * sstride;
+            const int r = g & (s - 1);
+            const int j0 = (((g >> lg) << (lg + 2)) + r);
+            const V2<T> w1 = twid<T, INV>(tw, r, lg + 1);
+            const V2<T> w2 = twid<T, INV>(tw, r, lg + 2);
+            const V2<T> w3 = mul_mi<T, INV>(w2);
+            V2<T> a0 = p[j0 * estride], a1 = cmul(p[(j0 + s) * estride], w1);
+            V2<T> a2 = p[(j0 + 2 * s) * estride], a3 = cmul(p[(j0 + 3 * s) * estride], w1);
+            V2<T> b0 = a0 + a1, b1 = a0 - a1, b2 = a2 + a3, b3 = a2 - a3;
+            V2<T> c2 = cmul(b2, w2), c3 = cmul(b3, w3);
+            p[j0 * estride] = b0 + c2;
+            p[(j0 + 2 * s) * estride] = b0 - c2;
+            p[(j0 + s) * estride] = b1 + c3;
+            p[(j0 + 3 * s) * estride] = b1 - c3;
+        }
+        __syncthreads();
+        lg += 2;
+    }
+}
+
+// In-place decimation-in-frequency FFT: natural order in, BIT-REVERSED order
+// out.  Pairs of radix-2 stages fused, a trailing radix-2 stage when logL is
+// odd.  Unnormalised.  Ends with __syncthreads().
+template <typename T, bool INV>
+__device__ void fft_dif(V2<T>* buf, int logL, int nseq, int sstride, int estride,
+                        const V2<T>* __restrict__ tw) {
+    const int L = 1 << logL;
+    int lS = logL - 1;                 // current span S = 2^lS
+    while (lS >= 1) {
+        const int S = 1 << lS, h = S >> 1;
+        const int ng = L >> 2, tot = ng * nseq;
+        for (int id = threadIdx.x; id < tot; id += blockDim.x) {
+            int seq, g; split_id(id, ng, nseq, estride, seq, g);
+            V2<T>* p = buf + seq * sstride;
+            const int r = g & (h - 1);
+            const int j0 = ((g >> (lS - 1)) << (lS + 1)) + r;
+            const V2<T> w1 = twid<T, INV>(tw, r, lS + 1);        // W_{2S}^r
+            const V2<T> w1b = mul_mi<T, INV>(w1);                 // W_{2S}^{r+S/2}
+            const V2<T> w2 = twid<T, INV>(tw, r, lS);             // W_S^r
+            V2<T> a0 = p[j0 * estride], a1 = p[(j0 + h) * estride];
+            V2<T> a2 = p[(j0 + S) * estride], a3 = p[(j0 + S + h) * estride];
+            V2<T> b0 = a0 + a2, b2 = cmul(a0 - a2, w1);
+            V2<T> b1 = a1 + a3, b3 = cmul(a1 - a3, w1b);
+            p[j0 * estride] = b0 + b1;
+            p[(j0 + h) * estride] = cmul(b0 - b1, w2);
+            p[(j0 + S) * estride] = b2 + b3;
+            p[(j0 + S + h) * estride] = cmul(b2 - b3, w2);
+        }
+        __syncthreads();
+        lS -= 2;
+    }
+    if (lS == 0) {
+        const int ng = L >> 1, tot = ng * nseq;
+        for (int id = threadIdx.x; id < tot; id += blockDim.x) {
+            int seq, g; split_id(id, ng, nseq, estride, seq, g);
+            V2<T>* p = buf + seq * sstride;
+            const int j0 = (2 * g) * estride, j1 = j0 + estride;
+            V2<T> a = p[j0], b = p[j1];
+            p[j0] = a + b; p[j1] = a - b;
+        }
+        __syncthreads();
+    }
+}
+
+// Parameters of every pass kernel (passed by value).
+enum { MODE_RHS = 0, MODE_RK = 1, MODE_ENERGY = 2, MODE_NEB = 3 };
+
+template <typename T>
+struct PassParams {
+    const SimDesc* __restrict__ desc;
+    SimState* state;
+    const WorkItem* __restrict__ items;
+    int mode;
+    int stage;              // 1..7 in MODE_RK
+    int nk;                 // number of k vectors combined by the RK prologue
+    int write_y;            // prologue writes the stage state
+    double a[7];            // RK coefficients a_{s,j}
+    double e[7];            // error coefficients (stage 7)
+    const T* m;             // y_n (MODE_RK) or the evaluated state (other modes)
+    T* ybuf;                // stage state
+    T* const* kvec;         // k_1..k_7 (device array of 7 pointers)
+    T* kout;                // k_s / dm/dt output
+    T* heff;                // optional H_eff output
+    T* errp;                // partial error vector (stage 7)
+    long long off_adjust;   // subtracted from SimDesc::off for caller buffers of one simulation
+    V2<T>* spec;
+    const T* __restrict__ tensor;
+    const T* __restrict__ Ms;
+    const V2<T>* __restrict__ tw;
+    int* errflag;           // set by checked builds on an out-of-range index
+};
+
+__device__ __forceinline__ double bits_to_double(unsigned long long b) { return __longlong_as_double((long long)b); }

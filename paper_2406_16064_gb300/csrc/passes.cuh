@@ -1,0 +1,515 @@
+// Pass kernels of one LLG right-hand-side evaluation over a batch of
+// simulations (one launch per pass covers every simulation of the batch,
+// one CTA per work item):
+//
+//   k_xfwd   RK stage prologue y_s = y_n + h sum_j a_sj k_j (Dormand-Prince,
+//            Sec. "LLG equation"), M = Ms y_s, zero-padded real-to-complex
+//            FFT along x (half-length complex FFT + split), for the ny*nz
+//            non-zero rows only.
+//   k_ycol   column FFTs along y over tiles of kx columns: forward (only the
+//            ny non-zero input rows are read), inverse (only ny output rows
+//            written), or -- for films (Pz = 1) -- forward, tensor product,
+//            inverse in one kernel.
+//   k_zcol   forward FFT along z, tensor product H^ = -N^ M^ (Eq. 8 in
+//            Fourier space), inverse FFT along z; nz of Pz planes in/out.
+//   k_xinv   complex-to-real inverse FFT along x (only the nx outputs), then
+//            per cell: exchange (Eq. 5), interfacial DMI (Eq. 14), uniaxial
+//            and cubic anisotropy, Zeeman, the LL torque (LL form of the
+//            LLG equation), optional H_eff, the stage-1 max|dm/dt| and the
+//            stage-7 embedded error norm (FP64 ordered-bit max reductions),
+//            or the energies (FP64 sums) in energy mode.
+#pragma once
+#include "mm_kernels.cuh"
+
+namespace mm {
+
+static constexpr double kMu0 = 4e-7 * 3.14159265358979323846;
+
+template <typename T>
+__device__ __forceinline__ long long spec_index(const SimDesc& d, int c, int z, int y, int kx) {
+    return d.spec_off + ((((long long)c * d.nz + z) * d.Py + y) * d.Kx + kx);
+}
+
+// H = T M with T the stored (negated, scaled) tensor at bin (kx, ky, kz)
+template <typename T>
+__device__ __forceinline__ void tensor_apply(const SimDesc& d, const T* __restrict__ tens, int kx, int ky,
+                                             int kz, V2<T>& Mx, V2<T>& My, V2<T>& Mz) {
+    int kyh = ky, kzh = kz;
+    T sy = (T)1, sz = (T)1;
+    if (ky > (d.Py >> 1)) { kyh = d.Py - ky; sy = (T)-1; }
+    if (kz > (d.Pz >> 1)) { kzh = d.Pz - kz; sz = (T)-1; }
+    const long long plane = (long long)d.Pzh * d.Pyh * d.Kx;
+    const long long i0 = d.tens_off + ((long long)kzh * d.Pyh + kyh) * d.Kx + kx;
+    const T xx = tens[i0], yy = tens[i0 + plane], zz = tens[i0 + 2 * plane];
+    const T xy = sy * tens[i0 + 3 * plane];
+    T xz = (T)0, yz = (T)0;
+    if (d.ncomp == 6) { xz = sz * tens[i0 + 4 * plane]; yz = sy * sz * tens[i0 + 5 * plane]; }
+    const V2<T> a = Mx, b = My, c = Mz;
+    Mx = mk<T>(xx * a.x + xy * b.x + xz * c.x, xx * a.y + xy * b.y + xz * c.y);
+    My = mk<T>(xy * a.x + yy * b.x + yz * c.x, xy * a.y + yy * b.y + yz * c.y);
+    Mz = mk<T>(xz * a.x + yz * b.x + zz * c.x, xz * a.y + yz * b.y + zz * c.y);
+}
+
+template <typename T>
+__device__ __forceinline__ bool sim_inactive(const PassParams<T>& p, int sim) {
+    return (p.mode == MODE_RK || p.mode == MODE_NEB) && p.state[sim].status != 0;
+}
+
+// ---------------------------------------------------------------- x forward
+template <typename T>
+__global__ void __launch_bounds__(MM_THREADS) k_xfwd(PassParams<T> p) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    V2<T>* sm = reinterpret_cast<V2<T>*>(smraw);
+    const WorkItem w = p.items[blockIdx.x];
+    if (sim_inactive(p, w.sim)) return;
+    const SimDesc& d = p.desc[w.sim];
+    const int nx = d.nx, ny = d.ny, N = d.ncells;
+    const int lLh = d.lPx - 1, Lh = 1 << lLh;
+    const int row0 = w.a, nrows = w.b;
+    const long long base = d.off - p.off_adjust;
+    const bool demag = (d.flags & F_DEMAG) != 0;
+    const bool msarr = (d.flags & F_MSARR) != 0;
+    const T hstep = (T)((p.mode == MODE_RK || p.mode == MODE_NEB) ? p.state[w.sim].h : 0.0);
+    const int tot = nrows << lLh;
+    for (int id = threadIdx.x; id < tot; id += blockDim.x) {
+        const int r = id >> lLh, n = id & (Lh - 1);
+        const long long row = row0 + r;
+        V2<T> val[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) val[c] = mk<T>((T)0, (T)0);
+#pragma unroll
+        for (int h2 = 0; h2 < 2; ++h2) {
+            const int x = 2 * n + h2;
+            if (x < nx) {
+                const long long cell = row * nx + x;
+                T yv[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) yv[c] = p.m[base + (long long)c * N + cell];
+                if (p.nk > 0) {
+                    T acc[3] = {(T)0, (T)0, (T)0};
+                    for (int j = 0; j < p.nk; ++j) {
+                        if (p.a[j] != 0.0) {
+                            const T aj = (T)p.a[j];
+                            const T* kj = p.kvec[j];
+#pragma unroll
+                            for (int c = 0; c < 3; ++c) acc[c] += aj * kj[base + (long long)c * N + cell];
+                        }
+                    }
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) yv[c] += hstep * acc[c];
+                    if (p.write_y) {
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) p.ybuf[base + (long long)c * N + cell] = yv[c];
+                    }
+                    if (p.stage == 7) {
+                        T ev[3] = {(T)0, (T)0, (T)0};
+                        for (int j = 0; j < 6; ++j) {
+                            if (p.e[j] != 0.0) {
+                                const T ej = (T)p.e[j];
+                                const T* kj = p.kvec[j];
+#pragma unroll
+                                for (int c = 0; c < 3; ++c) ev[c] += ej * kj[base + (long long)c * N + cell];
+                            }
+                        }
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) p.errp[base + (long long)c * N + cell] = ev[c];
+                    }
+                }
+                if (demag) {
+                    const T ms = msarr ? p.Ms[d.ms_off + cell] : (T)d.Ms;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        if (h2 == 0) val[c].x = ms * yv[c]; else val[c].y = ms * yv[c];
+                    }
+                }
+            }
+        }
+        if (demag) {
+            const int pos = bitrev(n, lLh);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) sm[((c * nrows + r) << lLh) + pos] = val[c];
+        }
+    }
+    if (!demag) return;
+    __syncthreads();
+    fft_dit<T, false>(sm, lLh, 3 * nrows, Lh, 1, p.tw);
+    const int Kx = d.Kx;
+    const int tot2 = 3 * nrows * Kx;
+    for (int id = threadIdx.x; id < tot2; id += blockDim.x) {
+        const int q = id / Kx, k = id - q * Kx;
+        const int c = q / nrows, r = q - c * nrows;
+        const V2<T>* s = sm + (q << lLh);
+        const V2<T> Zk = s[k & (Lh - 1)];
+        const V2<T> Zm = cconj(s[(Lh - k) & (Lh - 1)]);
+        const V2<T> E = cscale(Zk + Zm, (T)0.5);
+        const V2<T> Dd = Zk - Zm;
+        const V2<T> O = mk<T>(Dd.y * (T)0.5, -Dd.x * (T)0.5);
+        const V2<T> X = E + cmul(twid<T, false>(p.tw, k, d.lPx), O);
+        const int row = row0 + r;
+        const int z = row / ny, y = row - z * ny;
+        p.spec[spec_index<T>(d, c, z, y, k)] = X;
+    }
+}
+
+// ---------------------------------------------------------------- y columns
+// YMODE 0: forward (one component), 1: inverse (one component),
+//       2: forward + tensor product + inverse (three components, Pz == 1)
+template <typename T, int YMODE>
+__global__ void __launch_bounds__(MM_THREADS) k_ycol(PassParams<T> p) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    V2<T>* sm = reinterpret_cast<V2<T>*>(smraw);
+    const WorkItem w = p.items[blockIdx.x];
+    if (sim_inactive(p, w.sim)) return;
+    const SimDesc& d = p.desc[w.sim];
+    const int L = d.Py, lL = d.lPy, TT = d.Ty, ny = d.ny;
+    const int z = w.a, kx0 = w.b;
+    const int ncols = min(TT, d.Kx - kx0);
+    constexpr int NC = (YMODE == 2) ? 3 : 1;
+    const int c0 = (YMODE == 2) ? 0 : w.c;
+    const int es = NC * TT;                     // element stride: layout [y][cc][col]
+    const int tot = L * es;
+    for (int id = threadIdx.x; id < tot; id += blockDim.x) {
+        const int col = id % TT;
+        const int rest = id / TT;
+        const int cc = rest % NC;
+        const int y = rest / NC;
+        V2<T> v = mk<T>((T)0, (T)0);
+        int pos;
+        if (YMODE == 1) {
+            pos = y;
+            if (col < ncols) v = p.spec[spec_index<T>(d, c0 + cc, z, y, kx0 + col)];
+        } else {
+            pos = bitrev(y, lL);
+            if (col < ncols && y < ny) v = p.spec[spec_index<T>(d, c0 + cc, z, y, kx0 + col)];
+        }
+        sm[pos * es + cc * TT + col] = v;
+    }
+    __syncthreads();
+    if (YMODE == 0) {
+        fft_dit<T, false>(sm, lL, es, 1, es, p.tw);
+        for (int id = threadIdx.x; id < tot; id += blockDim.x) {
+            const int col = id % TT;
+            const int y = id / TT;
+            if (col < ncols) p.spec[spec_index<T>(d, c0, z, y, kx0 + col)] = sm[y * es + col];
+        }
+        return;
+    }
+    if (YMODE == 2) {
+        fft_dit<T, false>(sm, lL, es, 1, es, p.tw);
+        for (int id = threadIdx.x; id < L * TT; id += blockDim.x) {
+            const int col = id % TT;
+            const int y = id / TT;
+            if (col < ncols) {
+                V2<T>* q = sm + y * es + col;
+                V2<T> a = q[0], b = q[TT], c = q[2 * TT];
+                tensor_apply<T>(d, p.tensor, kx0 + col, y, 0, a, b, c);
+                q[0] = a; q[TT] = b; q[2 * TT] = c;
+            }
+        }
+        __syncthreads();
+    }
+    fft_dif<T, true>(sm, lL, es, 1, es, p.tw);
+    const int tot3 = ny * es;
+    for (int id = threadIdx.x; id < tot3; id += blockDim.x) {
+        const int col = id % TT;
+        const int rest = id / TT;
+        const int cc = rest % NC;
+        const int y = rest / NC;
+        if (col < ncols)
+            p.spec[spec_index<T>(d, c0 + cc, z, y, kx0 + col)] = sm[bitrev(y, lL) * es + cc * TT + col];
+    }
+}
+
+// ---------------------------------------------------------------- z columns
+template <typename T>
+__global__ void __launch_bounds__(MM_THREADS) k_zcol(PassParams<T> p) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    V2<T>* sm = reinterpret_cast<V2<T>*>(smraw);
+    const WorkItem w = p.items[blockIdx.x];
+    if (sim_inactive(p, w.sim)) return;
+    const SimDesc& d = p.desc[w.sim];
+    const int L = d.Pz, lL = d.lPz, TT = d.Tz, nz = d.nz;
+    const int ky = w.a, kx0 = w.b;
+    const int ncols = min(TT, d.Kx - kx0);
+    const int es = 3 * TT;                      // layout [z][c][col]
+    const int tot = L * es;
+    for (int id = threadIdx.x; id < tot; id += blockDim.x) {
+        const int col = id % TT;
+        const int rest = id / TT;
+        const int c = rest % 3;
+        const int z = rest / 3;
+        V2<T> v = mk<T>((T)0, (T)0);
+        if (col < ncols && z < nz) v = p.spec[spec_index<T>(d, c, z, ky, kx0 + col)];
+        sm[bitrev(z, lL) * es + c * TT + col] = v;
+    }
+    __syncthreads();
+    fft_dit<T, false>(sm, lL, es, 1, es, p.tw);
+    for (int id = threadIdx.x; id < L * TT; id += blockDim.x) {
+        const int col = id % TT;
+        const int z = id / TT;
+        if (col < ncols) {
+            V2<T>* q = sm + z * es + col;
+            V2<T> a = q[0], b = q[TT], c = q[2 * TT];
+            tensor_apply<T>(d, p.tensor, kx0 + col, ky, z, a, b, c);
+            q[0] = a; q[TT] = b; q[2 * TT] = c;
+        }
+    }
+    __syncthreads();
+    fft_dif<T, true>(sm, lL, es, 1, es, p.tw);
+    const int tot3 = nz * es;
+    for (int id = threadIdx.x; id < tot3; id += blockDim.x) {
+        const int col = id % TT;
+        const int rest = id / TT;
+        const int c = rest % 3;
+        const int z = rest / 3;
+        if (col < ncols) p.spec[spec_index<T>(d, c, z, ky, kx0 + col)] = sm[bitrev(z, lL) * es + c * TT + col];
+    }
+}
+
+// ------------------------------------------------------- x inverse + fields
+__device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsigned long long b) {
+    return a > b ? a : b;
+}
+
+__device__ __forceinline__ unsigned long long block_max_u64(unsigned long long v, unsigned long long* red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = umax64(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    unsigned long long r = 0;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r = umax64(r, red[i]);
+    }
+    return r;
+}
+
+__device__ __forceinline__ double block_sum(double v, double* red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r += red[i];
+    }
+    return r;
+}
+
+template <typename T>
+__device__ __forceinline__ T nb_ms(const PassParams<T>& p, const SimDesc& d, bool msarr, long long cell) {
+    return msarr ? p.Ms[d.ms_off + cell] : (T)1;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(MM_THREADS) k_xinv(PassParams<T> p, const T* __restrict__ ys) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    V2<T>* sm = reinterpret_cast<V2<T>*>(smraw);
+    __shared__ unsigned long long red_u[MM_THREADS / 32];
+    __shared__ double red_d[MM_THREADS / 32];
+    const WorkItem w = p.items[blockIdx.x];
+    if (sim_inactive(p, w.sim)) return;
+    const SimDesc& d = p.desc[w.sim];
+    const int nx = d.nx, ny = d.ny, nz = d.nz, N = d.ncells;
+    const int lLh = d.lPx - 1, Lh = 1 << lLh, Kx = d.Kx;
+    const int row0 = w.a, nrows = w.b;
+    const long long base = d.off - p.off_adjust;
+    const bool demag = (d.flags & F_DEMAG) != 0;
+    const bool msarr = (d.flags & F_MSARR) != 0;
+    if (demag) {
+        const int tot = 3 * nrows * Kx;
+        for (int id = threadIdx.x; id < tot; id += blockDim.x) {
+            const int q = id / Kx, k = id - q * Kx;
+            const int c = q / nrows, r = q - c * nrows;
+            const int row = row0 + r;
+            const int z = row / ny, y = row - z * ny;
+            sm[q * Kx + k] = p.spec[spec_index<T>(d, c, z, y, k)];
+        }
+        __syncthreads();
+        if (d.Py == 1 && d.Pz == 1) {            // x is the only transformed axis
+            for (int id = threadIdx.x; id < nrows * Kx; id += blockDim.x) {
+                const int r = id / Kx, k = id - r * Kx;
+                V2<T> a = sm[(0 * nrows + r) * Kx + k], b = sm[(1 * nrows + r) * Kx + k], c = sm[(2 * nrows + r) * Kx + k];
+                tensor_apply<T>(d, p.tensor, k, 0, 0, a, b, c);
+                sm[(0 * nrows + r) * Kx + k] = a; sm[(1 * nrows + r) * Kx + k] = b; sm[(2 * nrows + r) * Kx + k] = c;
+            }
+            __syncthreads();
+        }
+        // Hermitian split: Z_k = (X_k + X*_{Lh-k}) + i W^{-k} (X_k - X*_{Lh-k}), k < Lh
+        const int hk = (Lh >> 1) + 1;
+        const int tot2 = 3 * nrows * hk;
+        for (int id = threadIdx.x; id < tot2; id += blockDim.x) {
+            const int q = id / hk, k = id - q * hk;
+            V2<T>* s = sm + q * Kx;
+            if (k == 0) {
+                const V2<T> X0 = s[0], XL = cconj(s[Lh]);
+                const V2<T> e = X0 + XL, o = X0 - XL;
+                s[0] = mk<T>(e.x - o.y, e.y + o.x);
+            } else {
+                const int k2 = Lh - k;
+                const V2<T> Xa = s[k], Xb = s[k2];
+                const V2<T> ea = Xa + cconj(Xb);
+                const V2<T> ta = cmul(twid<T, true>(p.tw, k, d.lPx), Xa - cconj(Xb));
+                s[k] = mk<T>(ea.x - ta.y, ea.y + ta.x);
+                if (k2 != k) {
+                    const V2<T> eb = Xb + cconj(Xa);
+                    const V2<T> tb = cmul(twid<T, true>(p.tw, k2, d.lPx), Xb - cconj(Xa));
+                    s[k2] = mk<T>(eb.x - tb.y, eb.y + tb.x);
+                }
+            }
+        }
+        __syncthreads();
+        fft_dif<T, true>(sm, lLh, 3 * nrows, Kx, 1, p.tw);
+    }
+
+    // per-cell local fields and torque
+    const T mu0 = (T)kMu0;
+    const T Dxx = (T)d.dx, Dyy = (T)d.dy, Dzz = (T)d.dz;
+    const T cA = (T)(2.0 * d.A), cD = (T)d.D, cK = (T)(2.0 * d.Ku), cC = (T)(4.0 * d.Kc);
+    const T ux = (T)d.u[0], uy = (T)d.u[1], uz = (T)d.u[2];
+    const T Hx0 = (T)d.H[0], Hy0 = (T)d.H[1], Hz0 = (T)d.H[2];
+    const T gt = (T)(d.gamma / (1.0 + d.alpha * d.alpha));
+    const T agt = (T)(d.alpha * d.gamma / (1.0 + d.alpha * d.alpha));
+    const bool prec = (d.flags & F_PREC) != 0;
+    const bool dmi = (d.flags & F_DMI) != 0 && d.D != 0.0;
+    const bool do_ex = d.A != 0.0, do_uni = d.Ku != 0.0, do_cub = d.Kc != 0.0;
+    const bool energy = (p.mode == MODE_ENERGY || p.mode == MODE_NEB);
+    const bool write_k = (p.mode != MODE_ENERGY && p.mode != MODE_NEB);
+    const double V = d.dx * d.dy * d.dz;
+    const double hstep = (p.mode == MODE_RK) ? p.state[w.sim].h : 0.0;
+    unsigned long long vmax = 0ull;
+    double esum[6] = {0, 0, 0, 0, 0, 0};
+    const int tot = nrows * nx;
+    for (int id = threadIdx.x; id < tot; id += blockDim.x) {
+        const int r = id / nx, x = id - r * nx;
+        const int row = row0 + r;
+        const int z = row / ny, y = row - z * ny;
+        const long long cell = (long long)row * nx + x;
+        const T* mc = ys + base + cell;
+        const T m0 = mc[0], m1 = mc[N], m2 = mc[2 * (long long)N];
+        const T ms = msarr ? p.Ms[d.ms_off + cell] : (T)d.Ms;
+        T H0 = 0, H1 = 0, H2 = 0, k0 = 0, k1 = 0, k2 = 0;
+        if (ms > (T)0) {
+            const T inv = (T)1 / (mu0 * ms);
+            T hd0 = 0, hd1 = 0, hd2 = 0;
+            if (demag) {
+                const int pos = bitrev(x >> 1, lLh);
+                const V2<T> v0 = sm[(0 * nrows + r) * Kx + pos];
+                const V2<T> v1 = sm[(1 * nrows + r) * Kx + pos];
+                const V2<T> v2 = sm[(2 * nrows + r) * Kx + pos];
+                hd0 = (x & 1) ? v0.y : v0.x;
+                hd1 = (x & 1) ? v1.y : v1.x;
+                hd2 = (x & 1) ? v2.y : v2.x;
+            }
+            // exchange (Eq. 5) and interfacial DMI (Eq. 14), free boundaries
+            T ex0 = 0, ex1 = 0, ex2 = 0, dm0 = 0, dm1 = 0, dm2 = 0;
+            if (do_ex || dmi) {
+                const long long sx = 1, sy = nx, sz = (long long)nx * ny;
+#pragma unroll
+                for (int nb = 0; nb < 6; ++nb) {
+                    const int axis = nb >> 1;
+                    const int dir = (nb & 1) ? 1 : -1;
+                    bool ok;
+                    long long st;
+                    T Dl;
+                    if (axis == 0) { ok = dir < 0 ? x > 0 : x < nx - 1; st = sx; Dl = Dxx; }
+                    else if (axis == 1) { ok = dir < 0 ? y > 0 : y < ny - 1; st = sy; Dl = Dyy; }
+                    else { ok = dir < 0 ? z > 0 : z < nz - 1; st = sz; Dl = Dzz; }
+                    if (!ok) continue;
+                    const long long o = dir * st;
+                    if (msarr && !(nb_ms(p, d, msarr, cell + o) > (T)0)) continue;
+                    const T j0 = mc[o], j1 = mc[N + o], j2 = mc[2 * (long long)N + o];
+                    if (do_ex) {
+                        const T f = (T)1 / (Dl * Dl);
+                        ex0 += f * (j0 - m0); ex1 += f * (j1 - m1); ex2 += f * (j2 - m2);
+                    }
+                    if (dmi && axis < 2) {
+                        // sum_j e_ij x m_j / Delta: -x:-e_y, +x:+e_y, -y:+e_x, +y:-e_x
+                        const T f = (T)1 / Dl;
+                        if (axis == 0) {          // e_y x m = (mz, 0, -mx)
+                            const T s = (T)dir;
+                            dm0 += s * f * j2; dm2 -= s * f * j0;
+                        } else {                  // e_x x m = (0, -mz, my)
+                            const T s = (T)(-dir);
+                            dm1 -= s * f * j2; dm2 += s * f * j1;
+                        }
+                    }
+                }
+                ex0 *= cA * inv; ex1 *= cA * inv; ex2 *= cA * inv;
+                dm0 *= -cD * inv; dm1 *= -cD * inv; dm2 *= -cD * inv;
+            }
+            T un0 = 0, un1 = 0, un2 = 0, cu0 = 0, cu1 = 0, cu2 = 0;
+            if (do_uni) {
+                const T mu = m0 * ux + m1 * uy + m2 * uz;
+                const T f = cK * inv * mu;
+                un0 = f * ux; un1 = f * uy; un2 = f * uz;
+            }
+            if (do_cub) {
+                const T f = -cC * inv;
+                cu0 = f * m0 * m0 * m0; cu1 = f * m1 * m1 * m1; cu2 = f * m2 * m2 * m2;
+            }
+            H0 = hd0 + ex0 + dm0 + un0 + cu0 + Hx0;
+            H1 = hd1 + ex1 + dm1 + un1 + cu1 + Hy0;
+            H2 = hd2 + ex2 + dm2 + un2 + cu2 + Hz0;
+            if (energy) {
+                const double msV = (double)ms * V;
+                esum[0] += -0.5 * kMu0 * msV * ((double)m0 * ex0 + (double)m1 * ex1 + (double)m2 * ex2);
+                esum[1] += -0.5 * kMu0 * msV * ((double)m0 * dm0 + (double)m1 * dm1 + (double)m2 * dm2);
+                if (do_uni) {
+                    const double mu = (double)m0 * d.u[0] + (double)m1 * d.u[1] + (double)m2 * d.u[2];
+                    esum[2] += -d.Ku * V * mu * mu;
+                }
+                if (do_cub) {
+                    const double a0 = m0, a1 = m1, a2 = m2;
+                    esum[3] += d.Kc * V * (a0 * a0 * a0 * a0 + a1 * a1 * a1 * a1 + a2 * a2 * a2 * a2);
+                }
+                esum[4] += -kMu0 * msV * ((double)m0 * d.H[0] + (double)m1 * d.H[1] + (double)m2 * d.H[2]);
+                esum[5] += -0.5 * kMu0 * msV * ((double)m0 * hd0 + (double)m1 * hd1 + (double)m2 * hd2);
+            }
+            // LL form: dm/dt = -g~ m x H - alpha g~ m x (m x H)
+            const T c0 = m1 * H2 - m2 * H1, c1 = m2 * H0 - m0 * H2, c2 = m0 * H1 - m1 * H0;
+            const T dd0 = m1 * c2 - m2 * c1, dd1 = m2 * c0 - m0 * c2, dd2 = m0 * c1 - m1 * c0;
+            k0 = -agt * dd0; k1 = -agt * dd1; k2 = -agt * dd2;
+            if (prec) { k0 -= gt * c0; k1 -= gt * c1; k2 -= gt * c2; }
+        }
+        const long long o = base + cell;
+        if (write_k) {
+            p.kout[o] = k0; p.kout[o + N] = k1; p.kout[o + 2 * (long long)N] = k2;
+        }
+        if (p.heff) {
+            p.heff[o] = H0; p.heff[o + N] = H1; p.heff[o + 2 * (long long)N] = H2;
+        }
+        if (p.mode == MODE_RK && p.stage == 1) {
+            const double v = sqrt((double)k0 * k0 + (double)k1 * k1 + (double)k2 * k2);
+            vmax = umax64(vmax, (unsigned long long)__double_as_longlong(v));
+        } else if (p.mode == MODE_RK && p.stage == 7) {
+            const double e7 = p.e[6];
+            const T* ep = p.errp + o;
+            const double v0 = fabs(hstep * ((double)ep[0] + e7 * k0));
+            const double v1 = fabs(hstep * ((double)ep[N] + e7 * k1));
+            const double v2 = fabs(hstep * ((double)ep[2 * (long long)N] + e7 * k2));
+            vmax = umax64(vmax, (unsigned long long)__double_as_longlong(v0));
+            vmax = umax64(vmax, (unsigned long long)__double_as_longlong(v1));
+            vmax = umax64(vmax, (unsigned long long)__double_as_longlong(v2));
+        }
+    }
+    if (p.mode == MODE_RK && (p.stage == 1 || p.stage == 7)) {
+        const unsigned long long r = block_max_u64(vmax, red_u);
+        if (threadIdx.x == 0) {
+            unsigned long long* dst = p.stage == 1 ? &p.state[w.sim].maxk_bits : &p.state[w.sim].err_bits;
+            atomicMax(dst, r);
+        }
+    }
+    if (energy) {
+#pragma unroll
+        for (int t = 0; t < 6; ++t) {
+            const double s = block_sum(esum[t], red_d);
+            if (threadIdx.x == 0) atomicAdd(&p.state[w.sim].E[t], s);
+        }
+    }
+}
+
+}  // namespace mm
