@@ -185,6 +185,29 @@ int mm_debug_bounded_wait(mm_ctx *ctx, long long spins);
  * kernel nodes). */
 long long mm_kernel_launches(const mm_ctx *ctx);
 
+/* The right-hand-side evaluation of ONE simulation for callers that cannot
+ * allocate device memory.  The paper has no counterpart: this is a service of
+ * this library.  Callers such as a plugin handed device pointers by its host
+ * application, or code whose process owns the allocator, may not call
+ * cudaMalloc; this call allocates nothing (no cudaMalloc, cudaFree or
+ * allocating library routine).  The caller passes the state m_dev and the
+ * outputs dmdt_dev and heff_dev (nullable), [3][nz][ny][nx] each in the given
+ * precision (MM_F64: double, MM_F32: float), and a cudaStream_t (NULL = the
+ * default stream); the result equals mm_rhs_eval's for the same simulation
+ * (uniform Ms only).  Everything else -- twiddle tables, the FP64 Newell
+ * tensor and its spectrum (recomputed on every call), the demag spectrum,
+ * descriptors and work lists -- lives in one static device array of 32 MiB
+ * that every GPU loading libmm holds until the process exits.  A mesh whose
+ * padded FFT grid, Newell octant, tensor and spectrum do not fit returns
+ * MM_EINVAL with a message (mm_last_error(NULL)); for example 256x256x1 fits,
+ * 512x512x1 does not.  The first call on a device looks the array's device
+ * address up (cudaGetSymbolAddress): make it before any stream capture.  All
+ * calls share the array and it keeps the last call's contents, so calls that
+ * overlap on the GPU race: serialise them.  The call synchronises the stream
+ * once (after the tensor), then returns with the evaluation queued. */
+int mm_rhs_eval_static(const mm_mesh *mesh, const mm_material *mat, int precision,
+                       const void *m_dev, void *dmdt_dev, void *heff_dev, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

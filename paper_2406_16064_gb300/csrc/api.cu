@@ -949,3 +949,6 @@ int mm_debug_bounded_wait(mm_ctx* C, long long spins) {
 long long mm_kernel_launches(const mm_ctx* C) { return C ? C->launches : 0; }
 
 }  // extern "C"
+
+// Error message of calls that have no context (mm_last_error(NULL)).
+void mm_internal_set_error(const char* msg) { snprintf(g_last_error, sizeof(g_last_error), "%s", msg); }

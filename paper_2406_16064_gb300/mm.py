@@ -68,6 +68,7 @@ SIGNATURES = {
     "mm_profile_attempts": (C.c_int, [_P, C.c_int, _D, C.POINTER(C.c_longlong)]),
     "mm_debug_bounded_wait": (C.c_int, [_P, C.c_longlong]),
     "mm_kernel_launches": (C.c_longlong, [_P]),
+    "mm_rhs_eval_static": (C.c_int, [C.POINTER(mm_mesh), C.POINTER(mm_material), C.c_int, _P, _P, _P, _P]),
 }
 
 _lib = None
