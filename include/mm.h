@@ -174,7 +174,8 @@ int mm_neb_relax(mm_ctx *ctx, double rtol, long long n_steps, double *energies_o
  * ms[k] / counts[k] receive the summed duration and the launch count of each
  * kernel kind k: 0 x-forward pass (with the RK prologue), 1 y forward,
  * 2 z fused, 3 y inverse, 4 y fused (films), 5 x-inverse + field/torque
- * epilogue, 6 step control, 7 projection, 8 NEB; arrays of 9 entries. */
+ * epilogue, 6 step control, 7 projection, 8 NEB, 9 cluster-fused y/z pass;
+ * arrays of 10 entries. */
 int mm_profile_attempts(mm_ctx *ctx, int reps, double *ms, long long *counts);
 
 /* Debugging aid: bounded-wait check.  Runs a kernel that waits on a device

@@ -15,6 +15,7 @@
 
 #include "engine.cuh"
 #include "mm.h"
+#include "plan.h"
 
 using namespace mm;
 
@@ -22,26 +23,6 @@ namespace {
 
 constexpr double kPi = 3.14159265358979323846;
 char g_last_error[512] = "";
-
-int ilog2(int v) {
-    int l = 0;
-    while ((1 << l) < v) ++l;
-    return l;
-}
-
-// padded FFT length: the smallest power of two >= 2n - 1 (1 for n == 1 unless min2)
-int pad_len(int n, bool min2) {
-    if (n <= 1) return min2 ? 2 : 1;
-    int p = 1;
-    while (p < 2 * n - 1) p <<= 1;
-    return p;
-}
-
-int pow2floor(int v) {
-    int p = 1;
-    while (p * 2 <= v) p *= 2;
-    return p;
-}
 
 struct SimHost {
     mm_mesh mesh;
@@ -80,9 +61,10 @@ struct mm_ctx {
     SimDesc* desc_d = nullptr;
     SimState* state_d = nullptr;
     WorkItem *xi = nullptr, *y13i = nullptr, *zi = nullptr, *y2i = nullptr;
-    std::vector<WorkItem> xv, y13v, zv, y2v;
-    std::vector<int> xb, xc, y13b, y13c, zb, zc, y2b, y2c;
-    size_t smem_x = 0, smem_y13 = 0, smem_z = 0, smem_y2 = 0;
+    WorkItem* yzci[kMaxClusterPlanes + 1] = {};
+    PlanItems plan;
+    // per simulation: first item and item count in each list (the yzc list is the one of its nz)
+    std::vector<int> xb, xc, y13b, y13c, zb, zc, y2b, y2c, yzcb, yzcc;
     int *flag_d = nullptr, *status_d = nullptr;
     unsigned long long* diag_d = nullptr;
     cudaGraphExec_t rk_exec = nullptr;
@@ -133,14 +115,20 @@ Launch make_launch(mm_ctx* C, int sim) {
         if (sim < 0) { is.dev = dev; is.count = (int)all.size(); }
         else { is.dev = dev + b[sim]; is.count = c[sim]; }
     };
-    set(L.x, C->xi, C->xb, C->xc, C->xv);
-    set(L.y13, C->y13i, C->y13b, C->y13c, C->y13v);
-    set(L.z, C->zi, C->zb, C->zc, C->zv);
-    set(L.y2, C->y2i, C->y2b, C->y2c, C->y2v);
-    L.smem_x = C->smem_x;
-    L.smem_y13 = C->smem_y13;
-    L.smem_z = C->smem_z;
-    L.smem_y2 = C->smem_y2;
+    const PlanItems& P = C->plan;
+    set(L.x, C->xi, C->xb, C->xc, P.x);
+    set(L.y13, C->y13i, C->y13b, C->y13c, P.y13);
+    set(L.z, C->zi, C->zb, C->zc, P.z);
+    set(L.y2, C->y2i, C->y2b, C->y2c, P.y2);
+    for (int nz = 2; nz <= kMaxClusterPlanes; ++nz) {
+        if (sim < 0) L.yzc[nz] = {C->yzci[nz], (int)P.yzc[nz].size()};
+        else if (C->sims[sim].d.nz == nz) L.yzc[nz] = {C->yzci[nz] + C->yzcb[sim], C->yzcc[sim]};
+    }
+    L.smem_x = P.smem_x;
+    L.smem_y13 = P.smem_y13;
+    L.smem_z = P.smem_z;
+    L.smem_y2 = P.smem_y2;
+    L.smem_yzc = P.smem_yzc;
     L.tensor = C->tens;
     L.Ms = C->Msd;
     L.tw = C->precision == MM_F32 ? C->twf : C->twd;
@@ -156,54 +144,56 @@ int check_ready(mm_ctx* C) {
 }
 
 // Every global index a work item can touch, checked on the host before any launch.
+// Kernels index inside the per-simulation blocks checked here (state [3][N],
+// spectrum [3][nz][NBx][Py][Ty], tensor [ncomp][Pzh][Pyh][Kx]) from item
+// coordinates checked here.
 int validate_items(mm_ctx* C) {
+    const PlanItems& P = C->plan;
     const size_t vsz = 2 * C->esz;
-    for (const WorkItem& w : C->xv) {
-        const SimDesc& d = C->sims[w.sim].d;
-        const int rows = d.ny * d.nz;
-        if (w.a < 0 || w.b < 1 || w.a + w.b > rows) return fail(C, MM_EBOUNDS, "x item rows out of range");
-        const long long last_cell = (long long)(w.a + w.b) * d.nx - 1;
-        if (d.off + 2LL * d.ncells + last_cell >= C->total_elems) return fail(C, MM_EBOUNDS, "x item state");
-        if (3ULL * w.b * d.Kx * vsz > C->smem_x) return fail(C, MM_EBOUNDS, "x item smem");
+    for (const SimHost& s : C->sims) {
+        const SimDesc& d = s.d;
+        if (d.off < 0 || d.off + 3LL * d.ncells > C->total_elems) return fail(C, MM_EBOUNDS, "state block");
         if (d.flags & F_DEMAG) {
-            const int row = w.a + w.b - 1, z = row / d.ny, y = row % d.ny;
-            const long long si = d.spec_off + (((2LL * d.nz + z) * d.Py + y) * d.Kx + d.Kx - 1);
-            if (si >= C->spec_elems) return fail(C, MM_EBOUNDS, "x item spectrum");
+            if (d.spec_off < 0 || d.spec_off + plan_spec_elems(d) > C->spec_elems)
+                return fail(C, MM_EBOUNDS, "spectrum block");
+            const long long plane = (long long)d.Pzh * d.Pyh * d.Kx;
+            if (d.tens_off < 0 || d.tens_off + d.ncomp * plane > C->tens_elems)
+                return fail(C, MM_EBOUNDS, "tensor block");
+            if ((d.NBx << d.lTy) < d.Kx || d.Ty != (1 << d.lTy)) return fail(C, MM_EBOUNDS, "kx blocks");
         }
         if (d.ms_off >= 0 && d.ms_off + d.ncells > C->ms_elems) return fail(C, MM_EBOUNDS, "Ms array");
     }
-    for (const WorkItem& w : C->y13v) {
+    for (const WorkItem& w : P.x) {
         const SimDesc& d = C->sims[w.sim].d;
-        if (w.a < 0 || w.a >= d.nz || w.b < 0 || w.b >= d.Kx || w.c < 0 || w.c > 2)
+        if (w.a < 0 || w.b < 1 || w.a + w.b > d.ny * d.nz) return fail(C, MM_EBOUNDS, "x item rows");
+        if (3ULL * w.b * padded_len(d.Kx) * vsz > P.smem_x) return fail(C, MM_EBOUNDS, "x item smem");
+    }
+    for (const WorkItem& w : P.y13) {
+        const SimDesc& d = C->sims[w.sim].d;
+        if (w.a < 0 || w.a >= d.nz || w.b < 0 || w.b >= d.NBx || w.c < 0 || w.c > 2)
             return fail(C, MM_EBOUNDS, "y item range");
-        const long long si = d.spec_off + (((2LL * d.nz + d.nz - 1) * d.Py + d.Py - 1) * d.Kx + d.Kx - 1);
-        if (si >= C->spec_elems) return fail(C, MM_EBOUNDS, "y item spectrum");
-        if ((size_t)d.Py * d.Ty * vsz > C->smem_y13) return fail(C, MM_EBOUNDS, "y item smem");
+        if ((size_t)d.Py * d.Ty * vsz > P.smem_y13) return fail(C, MM_EBOUNDS, "y item smem");
     }
-    for (const WorkItem& w : C->y2v) {
+    for (const WorkItem& w : P.y2) {
         const SimDesc& d = C->sims[w.sim].d;
-        if (w.a != 0 || d.nz != 1 || w.b < 0 || w.b >= d.Kx) return fail(C, MM_EBOUNDS, "y2 item range");
-        const long long si = d.spec_off + (((2LL * d.nz + 0) * d.Py + d.Py - 1) * d.Kx + d.Kx - 1);
-        if (si >= C->spec_elems) return fail(C, MM_EBOUNDS, "y2 item spectrum");
-        if (3ULL * d.Py * d.Ty * vsz > C->smem_y2) return fail(C, MM_EBOUNDS, "y2 item smem");
+        if (w.a != 0 || d.nz != 1 || w.b < 0 || w.b >= d.NBx) return fail(C, MM_EBOUNDS, "y2 item range");
+        if (3ULL * d.Py * d.Ty * vsz > P.smem_y2) return fail(C, MM_EBOUNDS, "y2 item smem");
     }
-    for (const WorkItem& w : C->zv) {
+    for (const WorkItem& w : P.z) {
         const SimDesc& d = C->sims[w.sim].d;
-        if (w.a < 0 || w.a >= d.Py || w.b < 0 || w.b >= d.Kx) return fail(C, MM_EBOUNDS, "z item range");
-        const long long si = d.spec_off + (((2LL * d.nz + d.nz - 1) * d.Py + w.a) * d.Kx + d.Kx - 1);
-        if (si >= C->spec_elems) return fail(C, MM_EBOUNDS, "z item spectrum");
-        if (3ULL * d.Pz * d.Tz * vsz > C->smem_z) return fail(C, MM_EBOUNDS, "z item smem");
+        if (w.a < 0 || w.a >= d.Py || w.b < 0 || w.b >= d.NBx) return fail(C, MM_EBOUNDS, "z item range");
+        if (3ULL * d.Pz * d.Ty * vsz > P.smem_z) return fail(C, MM_EBOUNDS, "z item smem");
     }
-    for (const SimHost& s : C->sims) {
-        const SimDesc& d = s.d;
-        if (d.flags & F_DEMAG) {
-            const long long plane = (long long)d.Pzh * d.Pyh * d.Kx;
-            if (d.tens_off + d.ncomp * plane > C->tens_elems) return fail(C, MM_EBOUNDS, "tensor block");
+    for (int nz = 2; nz <= kMaxClusterPlanes; ++nz) {
+        for (const WorkItem& w : P.yzc[nz]) {
+            const SimDesc& d = C->sims[w.sim].d;
+            if (d.nz != nz || d.Py < 2 || w.b < 0 || w.b >= d.NBx || d.Pz != plan_pad_len(nz, false))
+                return fail(C, MM_EBOUNDS, "yz item range");
+            if (3ULL * d.Py * d.Ty * vsz > P.smem_yzc) return fail(C, MM_EBOUNDS, "yz item smem");
         }
-        if (d.off + 3LL * d.ncells > C->total_elems) return fail(C, MM_EBOUNDS, "state block");
     }
-    const size_t cap = 227 * 1024 - 4096;
-    if (C->smem_x > cap || C->smem_y13 > cap + 4096 || C->smem_y2 > cap + 4096 || C->smem_z > cap + 4096)
+    const size_t cap = 227 * 1024;
+    if (P.smem_x > cap - 4096 || P.smem_y13 > cap || P.smem_y2 > cap || P.smem_z > cap || P.smem_yzc > cap)
         return fail(C, MM_EINVAL, "a padded FFT length needs more shared memory than one CTA has");
     return MM_OK;
 }
@@ -375,6 +365,7 @@ int mm_destroy(mm_ctx* C) {
                     C->zi, C->y2i, C->flag_d, C->status_d, C->diag_d};
     for (void* p : ptrs) if (p) cudaFree(p);
     for (int j = 0; j < 7; ++j) if (C->k[j]) cudaFree(C->k[j]);
+    for (int nz = 0; nz <= kMaxClusterPlanes; ++nz) if (C->yzci[nz]) cudaFree(C->yzci[nz]);
     if (C->own_stream) cudaStreamDestroy(C->stream);
     delete C;
     return MM_OK;
@@ -396,17 +387,10 @@ int mm_add_sim(mm_ctx* C, const mm_mesh* mesh, const mm_material* mat, const dou
     memset(&d, 0, sizeof(d));
     d.nx = mesh->nx; d.ny = mesh->ny; d.nz = mesh->nz;
     d.ncells = (int)ncells;
-    d.Px = pad_len(d.nx, true);
-    d.Py = pad_len(d.ny, false);
-    d.Pz = pad_len(d.nz, false);
     const int lim_yz = C->precision == MM_F32 ? 8192 : 4096;
-    if (d.Px > 8192 || d.Py > lim_yz || d.Pz > lim_yz)
+    if (plan_pad_len(d.nx, true) > 8192 || plan_pad_len(d.ny, false) > lim_yz || plan_pad_len(d.nz, false) > lim_yz)
         return fail(C, MM_EINVAL, "padded FFT length too large (max 8192 along x, %d along y/z)", lim_yz);
-    d.lPx = ilog2(d.Px); d.lPy = ilog2(d.Py); d.lPz = ilog2(d.Pz);
-    d.Kx = d.Px / 2 + 1;
-    d.Pyh = d.Py / 2 + 1;
-    d.Pzh = d.Pz / 2 + 1;
-    d.ncomp = d.Pz > 1 ? 6 : 4;
+    plan_geometry(d, C->precision == MM_F32);
     double un = std::sqrt(mat->u[0] * mat->u[0] + mat->u[1] * mat->u[1] + mat->u[2] * mat->u[2]);
     if (mat->Ku != 0.0 && !(un > 0)) return fail(C, MM_EINVAL, "anisotropy axis is zero");
     for (int i = 0; i < 3; ++i) d.u[i] = un > 0 ? mat->u[i] / un : 0.0;
@@ -464,7 +448,6 @@ int mm_precompute_demag(mm_ctx* C) {
     if (C->sims.empty()) return fail(C, MM_EINVAL, "no simulations");
     CK(cudaSetDevice(C->device));
     const bool f32 = C->precision == MM_F32;
-    const int EB = f32 ? 4096 : 2048;          // complex elements per component per CTA
     // geometries
     std::map<std::tuple<int, int, int, double, double, double>, int> gmap;
     for (SimHost& s : C->sims) {
@@ -495,7 +478,9 @@ int mm_precompute_demag(mm_ctx* C) {
                 }
         }
     }
-    // per-simulation layout, tiles and work items
+    // per-simulation layout and work items (tile shapes were fixed by plan_geometry)
+    PlanItems& P = C->plan;
+    const size_t vsz = 2 * C->esz;
     for (size_t i = 0; i < C->sims.size(); ++i) {
         SimHost& s = C->sims[i];
         SimDesc& d = s.d;
@@ -503,42 +488,20 @@ int mm_precompute_demag(mm_ctx* C) {
         C->total_elems += 3LL * d.ncells;
         d.tens_off = C->geoms[s.geom].tens_off;
         if (d.flags & F_MSARR) { d.ms_off = C->ms_elems; C->ms_elems += d.ncells; }
-        const bool demag = (d.flags & F_DEMAG) != 0;
-        if (demag) { d.spec_off = C->spec_elems; C->spec_elems += 3LL * d.nz * d.Py * d.Kx; }
+        if (d.flags & F_DEMAG) { d.spec_off = C->spec_elems; C->spec_elems += plan_spec_elems(d); }
         else d.spec_off = 0;
-        const int rows = d.ny * d.nz;
-        d.Rx = std::max(1, std::min(rows, EB / d.Kx));
-        const int kcap = std::min(32, 1 << ilog2(d.Kx));
-        if (d.Pz > 1) d.Ty = std::min(kcap, pow2floor(std::max(1, 3 * EB / d.Py)));
-        else d.Ty = std::min(kcap, pow2floor(std::max(1, EB / d.Py)));
-        d.Tz = std::min(kcap, pow2floor(std::max(1, EB / d.Pz)));
-        const int sid = (int)i;
-        C->xb.push_back((int)C->xv.size());
-        for (int r0 = 0; r0 < rows; r0 += d.Rx) C->xv.push_back({sid, r0, std::min(d.Rx, rows - r0), 0});
-        C->xc.push_back((int)C->xv.size() - C->xb.back());
-        C->y13b.push_back((int)C->y13v.size());
-        C->zb.push_back((int)C->zv.size());
-        C->y2b.push_back((int)C->y2v.size());
-        if (demag) {
-            if (d.Pz > 1) {
-                if (d.Py > 1)
-                    for (int z = 0; z < d.nz; ++z)
-                        for (int k0 = 0; k0 < d.Kx; k0 += d.Ty)
-                            for (int c = 0; c < 3; ++c) C->y13v.push_back({sid, z, k0, c});
-                for (int ky = 0; ky < d.Py; ++ky)
-                    for (int k0 = 0; k0 < d.Kx; k0 += d.Tz) C->zv.push_back({sid, ky, k0, 0});
-            } else if (d.Py > 1) {
-                for (int k0 = 0; k0 < d.Kx; k0 += d.Ty) C->y2v.push_back({sid, 0, k0, -1});
-            }
-        }
-        C->y13c.push_back((int)C->y13v.size() - C->y13b.back());
-        C->zc.push_back((int)C->zv.size() - C->zb.back());
-        C->y2c.push_back((int)C->y2v.size() - C->y2b.back());
-        const size_t vsz = 2 * C->esz;
-        C->smem_x = std::max(C->smem_x, 3 * (size_t)d.Rx * d.Kx * vsz);
-        if (demag && d.Pz > 1 && d.Py > 1) C->smem_y13 = std::max(C->smem_y13, (size_t)d.Py * d.Ty * vsz);
-        if (demag && d.Pz > 1) C->smem_z = std::max(C->smem_z, 3 * (size_t)d.Pz * d.Tz * vsz);
-        if (demag && d.Pz == 1 && d.Py > 1) C->smem_y2 = std::max(C->smem_y2, 3 * (size_t)d.Py * d.Ty * vsz);
+        const int g = std::min(d.nz, kMaxClusterPlanes);
+        C->xb.push_back((int)P.x.size());
+        C->y13b.push_back((int)P.y13.size());
+        C->zb.push_back((int)P.z.size());
+        C->y2b.push_back((int)P.y2.size());
+        C->yzcb.push_back((int)P.yzc[g].size());
+        plan_items(d, (int)i, vsz, P);
+        C->xc.push_back((int)P.x.size() - C->xb.back());
+        C->y13c.push_back((int)P.y13.size() - C->y13b.back());
+        C->zc.push_back((int)P.z.size() - C->zb.back());
+        C->y2c.push_back((int)P.y2.size() - C->y2b.back());
+        C->yzcc.push_back((int)P.yzc[g].size() - C->yzcb.back());
     }
     int rc = validate_items(C);
     if (rc) return rc;
@@ -567,10 +530,12 @@ int mm_precompute_demag(mm_ctx* C) {
             CK(cudaMemcpyAsync(*dst, v.data(), v.size() * sizeof(WorkItem), cudaMemcpyHostToDevice, C->stream));
         return MM_OK;
     };
-    if ((rc = up_items(&C->xi, C->xv))) return rc;
-    if ((rc = up_items(&C->y13i, C->y13v))) return rc;
-    if ((rc = up_items(&C->zi, C->zv))) return rc;
-    if ((rc = up_items(&C->y2i, C->y2v))) return rc;
+    if ((rc = up_items(&C->xi, P.x))) return rc;
+    if ((rc = up_items(&C->y13i, P.y13))) return rc;
+    if ((rc = up_items(&C->zi, P.z))) return rc;
+    if ((rc = up_items(&C->y2i, P.y2))) return rc;
+    for (int nz = 2; nz <= kMaxClusterPlanes; ++nz)
+        if ((rc = up_items(&C->yzci[nz], P.yzc[nz]))) return rc;
     CK(cudaMemcpyAsync(C->kvec_dev, C->k, 7 * sizeof(void*), cudaMemcpyHostToDevice, C->stream));
     CK(cudaMemsetAsync(C->spec, 0, (size_t)C->spec_elems * 2 * C->esz, C->stream));
     CK(cudaMemsetAsync(C->m, 0, sb, C->stream));

@@ -16,7 +16,7 @@ struct ItemSet {
 
 // Kernel kinds reported by the profiling hook.
 enum { KIND_XFWD = 0, KIND_YFWD, KIND_ZCOL, KIND_YINV, KIND_YFUSED, KIND_XINV, KIND_CONTROL, KIND_PROJECT,
-       KIND_NEB, KIND_COUNT };
+       KIND_NEB, KIND_YZC, KIND_COUNT };
 
 // Records a CUDA event on the launch stream after every kernel; the interval
 // between consecutive events is attributed to the kernel that ended it.
@@ -39,8 +39,9 @@ struct Launch {
     const SimDesc* desc = nullptr;
     SimState* state = nullptr;
     int nsims = 0;
-    ItemSet x, y13, z, y2;        // x rows, y fwd/inv (nz > 1), z fused, y fused (films)
-    size_t smem_x = 0, smem_y13 = 0, smem_z = 0, smem_y2 = 0;
+    ItemSet x, y13, z, y2;        // x rows, y fwd/inv (nz > 8), z fused, y fused (films)
+    ItemSet yzc[9];               // cluster-fused y/z per plane count nz = 2..8
+    size_t smem_x = 0, smem_y13 = 0, smem_z = 0, smem_y2 = 0, smem_yzc = 0;
     const void* tensor = nullptr;
     const void* Ms = nullptr;
     const void* tw = nullptr;

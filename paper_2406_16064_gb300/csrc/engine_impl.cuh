@@ -62,6 +62,28 @@ static void issue_passes(const Launch& L, PassParams<T> p, const T* ys, bool inc
         if (hk) hk->mark(KIND_YINV);
         ++n;
     }
+    for (int nz = 2; nz <= 8; ++nz) {
+        if (!L.yzc[nz].count) continue;
+        p.items = L.yzc[nz].dev;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)(L.yzc[nz].count * nz), 1, 1);
+        cfg.blockDim = dim3(MM_THREADS, 1, 1);
+        cfg.dynamicSmemBytes = L.smem_yzc;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = nz;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        // padded z length: the power of two >= 2 nz - 1
+        if (nz == 2) cudaLaunchKernelEx(&cfg, k_yzc<T, 4>, p);
+        else if (nz <= 4) cudaLaunchKernelEx(&cfg, k_yzc<T, 8>, p);
+        else cudaLaunchKernelEx(&cfg, k_yzc<T, 16>, p);
+        if (hk) hk->mark(KIND_YZC);
+        ++n;
+    }
     if (L.y2.count) {
         p.items = L.y2.dev;
         k_ycol<T, 2><<<L.y2.count, MM_THREADS, L.smem_y2, s>>>(p);
@@ -175,6 +197,9 @@ static void set_attrs() {
     cudaFuncSetAttribute(k_ycol<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     cudaFuncSetAttribute(k_ycol<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     cudaFuncSetAttribute(k_zcol<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_yzc<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_yzc<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_yzc<T, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
 }
 
 }  // namespace mm

@@ -3,8 +3,10 @@
 //
 // Layouts (all simulations of a batch live in one set of buffers):
 //   state  [3][nz][ny][nx] per simulation at element offset SimDesc::off
-//   spectrum [3][nz][Py][Kx] complex per simulation at SimDesc::spec_off;
-//          rows y < ny hold the x-transform, all Py rows the xy-transform
+//   spectrum [3][nz][NBx][Py][Ty] complex per simulation at SimDesc::spec_off:
+//          kx split into blocks of Ty columns so that a column tile is one
+//          contiguous run; rows y < ny hold the x-transform, all Py rows the
+//          xy-transform
 //   tensor [ncomp][Pz/2+1][Py/2+1][Kx] real per geometry at SimDesc::tens_off,
 //          ncomp = 6 (xx yy zz xy xz yz) or 4 when Pz == 1 (xz = yz = 0),
 //          holding -N^(k)/(Px Py Pz); other bins follow from the parities
@@ -33,8 +35,9 @@ struct SimDesc {
     int ncomp;               // 4 or 6
     int flags;
     int Rx;                  // rows per CTA in the x passes
-    int Ty;                  // kx columns per CTA in the y passes
-    int Tz;                  // kx columns per CTA in the z pass
+    int Ty;                  // kx block width (power of two): spectrum block and column tile
+    int lTy;                 // log2(Ty)
+    int NBx;                 // number of kx blocks, ceil(Kx / Ty)
     int group_begin, group_end;   // NEB chain members [begin, end), -1 if none
     int neb_index;                // image index in its chain
     int pad0;
@@ -95,11 +98,20 @@ __device__ __forceinline__ void split_id(int id, int ngroups, int nseq, int estr
     else { g = id / nseq; seq = id - g * nseq; }
 }
 
+// Element j of a unit-stride sequence sits at pidx(j) = j + j/16: one pad
+// slot per 16 complex values keeps the radix-4 access patterns off shared
+// memory bank conflicts.  Padded length of an n-element sequence:
+__host__ __device__ __forceinline__ int padded_len(int n) { return n + (n >> 4) + 1; }
+
+template <bool PAD>
+__device__ __forceinline__ int ix(int j, int estride) { return PAD ? j + (j >> 4) : j * estride; }
+
 // In-place decimation-in-time FFT of nseq sequences of length 2^logL held in
 // shared memory in BIT-REVERSED order; leaves them in natural order.
 // Radix-2 stages are fused in pairs (radix-4 butterflies), one leading
 // radix-2 stage when logL is odd.  Unnormalised.  Ends with __syncthreads().
-template <typename T, bool INV>
+// PAD: unit-stride sequences stored with pidx() padding (estride ignored).
+template <typename T, bool INV, bool PAD = false>
 __device__ void fft_dit(V2<T>* buf, int logL, int nseq, int sstride, int estride,
                         const V2<T>* __restrict__ tw) {
     const int L = 1 << logL;
@@ -109,7 +121,7 @@ __device__ void fft_dit(V2<T>* buf, int logL, int nseq, int sstride, int estride
         for (int id = threadIdx.x; id < tot; id += blockDim.x) {
             int seq, g; split_id(id, ng, nseq, estride, seq, g);
             V2<T>* p = buf + seq * sstride;
-            const int j0 = (2 * g) * estride, j1 = j0 + estride;
+            const int j0 = ix<PAD>(2 * g, estride), j1 = ix<PAD>(2 * g + 1, estride);
             V2<T> a = p[j0], b = p[j1];
             p[j0] = a + b; p[j1] = a - b;
         }
@@ -127,14 +139,16 @@ __device__ void fft_dit(V2<T>* buf, int logL, int nseq, int sstride, int estride
             const V2<T> w1 = twid<T, INV>(tw, r, lg + 1);
             const V2<T> w2 = twid<T, INV>(tw, r, lg + 2);
             const V2<T> w3 = mul_mi<T, INV>(w2);
-            V2<T> a0 = p[j0 * estride], a1 = cmul(p[(j0 + s) * estride], w1);
-            V2<T> a2 = p[(j0 + 2 * s) * estride], a3 = cmul(p[(j0 + 3 * s) * estride], w1);
+            const int i0 = ix<PAD>(j0, estride), i1 = ix<PAD>(j0 + s, estride);
+            const int i2 = ix<PAD>(j0 + 2 * s, estride), i3 = ix<PAD>(j0 + 3 * s, estride);
+            V2<T> a0 = p[i0], a1 = cmul(p[i1], w1);
+            V2<T> a2 = p[i2], a3 = cmul(p[i3], w1);
             V2<T> b0 = a0 + a1, b1 = a0 - a1, b2 = a2 + a3, b3 = a2 - a3;
             V2<T> c2 = cmul(b2, w2), c3 = cmul(b3, w3);
-            p[j0 * estride] = b0 + c2;
-            p[(j0 + 2 * s) * estride] = b0 - c2;
-            p[(j0 + s) * estride] = b1 + c3;
-            p[(j0 + 3 * s) * estride] = b1 - c3;
+            p[i0] = b0 + c2;
+            p[i2] = b0 - c2;
+            p[i1] = b1 + c3;
+            p[i3] = b1 - c3;
         }
         __syncthreads();
         lg += 2;
@@ -144,7 +158,7 @@ __device__ void fft_dit(V2<T>* buf, int logL, int nseq, int sstride, int estride
 // In-place decimation-in-frequency FFT: natural order in, BIT-REVERSED order
 // out.  Pairs of radix-2 stages fused, a trailing radix-2 stage when logL is
 // odd.  Unnormalised.  Ends with __syncthreads().
-template <typename T, bool INV>
+template <typename T, bool INV, bool PAD = false>
 __device__ void fft_dif(V2<T>* buf, int logL, int nseq, int sstride, int estride,
                         const V2<T>* __restrict__ tw) {
     const int L = 1 << logL;
@@ -160,14 +174,16 @@ __device__ void fft_dif(V2<T>* buf, int logL, int nseq, int sstride, int estride
             const V2<T> w1 = twid<T, INV>(tw, r, lS + 1);        // W_{2S}^r
             const V2<T> w1b = mul_mi<T, INV>(w1);                 // W_{2S}^{r+S/2}
             const V2<T> w2 = twid<T, INV>(tw, r, lS);             // W_S^r
-            V2<T> a0 = p[j0 * estride], a1 = p[(j0 + h) * estride];
-            V2<T> a2 = p[(j0 + S) * estride], a3 = p[(j0 + S + h) * estride];
+            const int i0 = ix<PAD>(j0, estride), i1 = ix<PAD>(j0 + h, estride);
+            const int i2 = ix<PAD>(j0 + S, estride), i3 = ix<PAD>(j0 + S + h, estride);
+            V2<T> a0 = p[i0], a1 = p[i1];
+            V2<T> a2 = p[i2], a3 = p[i3];
             V2<T> b0 = a0 + a2, b2 = cmul(a0 - a2, w1);
             V2<T> b1 = a1 + a3, b3 = cmul(a1 - a3, w1b);
-            p[j0 * estride] = b0 + b1;
-            p[(j0 + h) * estride] = cmul(b0 - b1, w2);
-            p[(j0 + S) * estride] = b2 + b3;
-            p[(j0 + S + h) * estride] = cmul(b2 - b3, w2);
+            p[i0] = b0 + b1;
+            p[i1] = cmul(b0 - b1, w2);
+            p[i2] = b2 + b3;
+            p[i3] = cmul(b2 - b3, w2);
         }
         __syncthreads();
         lS -= 2;
@@ -177,12 +193,47 @@ __device__ void fft_dif(V2<T>* buf, int logL, int nseq, int sstride, int estride
         for (int id = threadIdx.x; id < tot; id += blockDim.x) {
             int seq, g; split_id(id, ng, nseq, estride, seq, g);
             V2<T>* p = buf + seq * sstride;
-            const int j0 = (2 * g) * estride, j1 = j0 + estride;
+            const int j0 = ix<PAD>(2 * g, estride), j1 = ix<PAD>(2 * g + 1, estride);
             V2<T> a = p[j0], b = p[j1];
             p[j0] = a + b; p[j1] = a - b;
         }
         __syncthreads();
     }
+}
+
+// Length-PZ FFT of one sequence held in registers (PZ = 2, 4, 8, 16), natural
+// order in and out; radix-2 decimation in time, unnormalised.
+template <int PZ> struct Log2 { static constexpr int v = PZ == 2 ? 1 : PZ == 4 ? 2 : PZ == 8 ? 3 : 4; };
+
+template <int BITS>
+__host__ __device__ constexpr int brev_ct(int v) {
+    int r = 0;
+    for (int i = 0; i < BITS; ++i) r |= ((v >> i) & 1) << (BITS - 1 - i);
+    return r;
+}
+
+template <typename T, int PZ, bool INV>
+__device__ __forceinline__ void reg_fft(V2<T> (&x)[PZ], const V2<T>* __restrict__ tw) {
+    constexpr int LG = Log2<PZ>::v;
+    V2<T> y[PZ];
+#pragma unroll
+    for (int i = 0; i < PZ; ++i) y[brev_ct<LG>(i)] = x[i];
+#pragma unroll
+    for (int lg = 0; lg < LG; ++lg) {
+        const int s = 1 << lg;
+#pragma unroll
+        for (int base = 0; base < PZ; base += 2 * s) {
+#pragma unroll
+            for (int r = 0; r < s; ++r) {
+                const V2<T> w = twid<T, INV>(tw, r, lg + 1);
+                const V2<T> a = y[base + r], b = cmul(y[base + r + s], w);
+                y[base + r] = a + b;
+                y[base + r + s] = a - b;
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < PZ; ++i) x[i] = y[i];
 }
 
 // Parameters of every pass kernel (passed by value).

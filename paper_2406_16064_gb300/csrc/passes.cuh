@@ -1,17 +1,26 @@
 // Pass kernels of one LLG right-hand-side evaluation over a batch of
 // simulations (one launch per pass covers every simulation of the batch,
-// one CTA per work item):
+// one CTA -- or one thread-block cluster -- per work item):
 //
 //   k_xfwd   RK stage prologue y_s = y_n + h sum_j a_sj k_j (Dormand-Prince,
 //            Sec. "LLG equation"), M = Ms y_s, zero-padded real-to-complex
 //            FFT along x (half-length complex FFT + split), for the ny*nz
 //            non-zero rows only.
-//   k_ycol   column FFTs along y over tiles of kx columns: forward (only the
+//   k_ycol   column FFTs along y over blocks of kx columns: forward (only the
 //            ny non-zero input rows are read), inverse (only ny output rows
 //            written), or -- for films (Pz = 1) -- forward, tensor product,
 //            inverse in one kernel.
 //   k_zcol   forward FFT along z, tensor product H^ = -N^ M^ (Eq. 8 in
-//            Fourier space), inverse FFT along z; nz of Pz planes in/out.
+//            Fourier space), inverse FFT along z; nz of Pz planes in/out
+//            (meshes with nz > 8).
+//   k_yzc    thin films (1 < nz <= 8): one thread-block cluster of nz CTAs per
+//            kx block, CTA z owning plane z.  Each CTA transforms its plane
+//            along y; after a cluster barrier every CTA takes a share of the
+//            ky rows, gathers the nz planes from its peers' shared memory
+//            (distributed shared memory), does the zero-padded z FFT in
+//            registers, the tensor product and the inverse z FFT, and scatters
+//            the nz planes back; after a second barrier each CTA inverts its
+//            plane along y.  Replaces y forward + z + y inverse.
 //   k_xinv   complex-to-real inverse FFT along x (only the nx outputs), then
 //            per cell: exchange (Eq. 5), interfacial DMI (Eq. 14), uniaxial
 //            and cubic anisotropy, Zeeman, the LL torque (LL form of the
@@ -19,15 +28,25 @@
 //            stage-7 embedded error norm (FP64 ordered-bit max reductions),
 //            or the energies (FP64 sums) in energy mode.
 #pragma once
+#include <cooperative_groups.h>
+
 #include "mm_kernels.cuh"
 
 namespace mm {
 
 static constexpr double kMu0 = 4e-7 * 3.14159265358979323846;
 
+// spectrum element (c, z, y, kx) in the kx-blocked layout [3][nz][NBx][Py][Ty]
 template <typename T>
 __device__ __forceinline__ long long spec_index(const SimDesc& d, int c, int z, int y, int kx) {
-    return d.spec_off + ((((long long)c * d.nz + z) * d.Py + y) * d.Kx + kx);
+    return d.spec_off + (((((long long)c * d.nz + z) * d.NBx + (kx >> d.lTy)) * d.Py + y) << d.lTy) +
+           (kx & (d.Ty - 1));
+}
+
+// first element of block b of plane (c, z); element (y, j) sits at + y*Ty + j
+template <typename T>
+__device__ __forceinline__ long long spec_block(const SimDesc& d, int c, int z, int b) {
+    return d.spec_off + ((((long long)c * d.nz + z) * d.NBx + b) * d.Py << d.lTy);
 }
 
 // H = T M with T the stored (negated, scaled) tensor at bin (kx, ky, kz)
@@ -56,6 +75,7 @@ __device__ __forceinline__ bool sim_inactive(const PassParams<T>& p, int sim) {
 }
 
 // ---------------------------------------------------------------- x forward
+// Shared memory: 3*nrows sequences of Lh complex values, padded (pidx).
 template <typename T>
 __global__ void __launch_bounds__(MM_THREADS) k_xfwd(PassParams<T> p) {
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -65,6 +85,7 @@ __global__ void __launch_bounds__(MM_THREADS) k_xfwd(PassParams<T> p) {
     const SimDesc& d = p.desc[w.sim];
     const int nx = d.nx, ny = d.ny, N = d.ncells;
     const int lLh = d.lPx - 1, Lh = 1 << lLh;
+    const int SL = padded_len(Lh);
     const int row0 = w.a, nrows = w.b;
     const long long base = d.off - p.off_adjust;
     const bool demag = (d.flags & F_DEMAG) != 0;
@@ -125,35 +146,35 @@ __global__ void __launch_bounds__(MM_THREADS) k_xfwd(PassParams<T> p) {
             }
         }
         if (demag) {
-            const int pos = bitrev(n, lLh);
+            const int pos = ix<true>(bitrev(n, lLh), 1);
 #pragma unroll
-            for (int c = 0; c < 3; ++c) sm[((c * nrows + r) << lLh) + pos] = val[c];
+            for (int c = 0; c < 3; ++c) sm[(c * nrows + r) * SL + pos] = val[c];
         }
     }
     if (!demag) return;
     __syncthreads();
-    fft_dit<T, false>(sm, lLh, 3 * nrows, Lh, 1, p.tw);
+    fft_dit<T, false, true>(sm, lLh, 3 * nrows, SL, 1, p.tw);
     const int Kx = d.Kx;
     const int tot2 = 3 * nrows * Kx;
     for (int id = threadIdx.x; id < tot2; id += blockDim.x) {
         const int q = id / Kx, k = id - q * Kx;
         const int c = q / nrows, r = q - c * nrows;
-        const V2<T>* s = sm + (q << lLh);
-        const V2<T> Zk = s[k & (Lh - 1)];
-        const V2<T> Zm = cconj(s[(Lh - k) & (Lh - 1)]);
+        const int row = row0 + r;
+        const int z = row / ny, y = row - z * ny;
+        const V2<T>* s = sm + q * SL;
+        const V2<T> Zk = s[ix<true>(k & (Lh - 1), 1)];
+        const V2<T> Zm = cconj(s[ix<true>((Lh - k) & (Lh - 1), 1)]);
         const V2<T> E = cscale(Zk + Zm, (T)0.5);
         const V2<T> Dd = Zk - Zm;
         const V2<T> O = mk<T>(Dd.y * (T)0.5, -Dd.x * (T)0.5);
-        const V2<T> X = E + cmul(twid<T, false>(p.tw, k, d.lPx), O);
-        const int row = row0 + r;
-        const int z = row / ny, y = row - z * ny;
-        p.spec[spec_index<T>(d, c, z, y, k)] = X;
+        p.spec[spec_index<T>(d, c, z, y, k)] = E + cmul(twid<T, false>(p.tw, k, d.lPx), O);
     }
 }
 
 // ---------------------------------------------------------------- y columns
 // YMODE 0: forward (one component), 1: inverse (one component),
 //       2: forward + tensor product + inverse (three components, Pz == 1)
+// A CTA owns one kx block (Ty columns) of one plane.
 template <typename T, int YMODE>
 __global__ void __launch_bounds__(MM_THREADS) k_ycol(PassParams<T> p) {
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -161,62 +182,53 @@ __global__ void __launch_bounds__(MM_THREADS) k_ycol(PassParams<T> p) {
     const WorkItem w = p.items[blockIdx.x];
     if (sim_inactive(p, w.sim)) return;
     const SimDesc& d = p.desc[w.sim];
-    const int L = d.Py, lL = d.lPy, TT = d.Ty, ny = d.ny;
-    const int z = w.a, kx0 = w.b;
+    const int L = d.Py, lL = d.lPy, TT = d.Ty, lT = d.lTy, ny = d.ny;
+    const int z = w.a, b = w.b;
+    const int kx0 = b << lT;
     const int ncols = min(TT, d.Kx - kx0);
     constexpr int NC = (YMODE == 2) ? 3 : 1;
     const int c0 = (YMODE == 2) ? 0 : w.c;
-    const int es = NC * TT;                     // element stride: layout [y][cc][col]
-    const int tot = L * es;
-    for (int id = threadIdx.x; id < tot; id += blockDim.x) {
-        const int col = id % TT;
-        const int rest = id / TT;
-        const int cc = rest % NC;
-        const int y = rest / NC;
-        V2<T> v = mk<T>((T)0, (T)0);
-        int pos;
-        if (YMODE == 1) {
-            pos = y;
-            if (col < ncols) v = p.spec[spec_index<T>(d, c0 + cc, z, y, kx0 + col)];
-        } else {
-            pos = bitrev(y, lL);
-            if (col < ncols && y < ny) v = p.spec[spec_index<T>(d, c0 + cc, z, y, kx0 + col)];
+    const int es = NC * TT;                     // layout [y][cc][col]
+    long long gb[NC];
+#pragma unroll
+    for (int cc = 0; cc < NC; ++cc) gb[cc] = spec_block<T>(d, c0 + cc, z, b);
+    const int nload = (YMODE == 1) ? L : ny;
+#pragma unroll
+    for (int cc = 0; cc < NC; ++cc) {
+        for (int id = threadIdx.x; id < (L << lT); id += blockDim.x) {
+            const int col = id & (TT - 1), y = id >> lT;
+            const V2<T> v = y < nload ? p.spec[gb[cc] + id] : mk<T>((T)0, (T)0);
+            const int pos = (YMODE == 1) ? y : bitrev(y, lL);
+            sm[pos * es + cc * TT + col] = v;
         }
-        sm[pos * es + cc * TT + col] = v;
     }
     __syncthreads();
     if (YMODE == 0) {
         fft_dit<T, false>(sm, lL, es, 1, es, p.tw);
-        for (int id = threadIdx.x; id < tot; id += blockDim.x) {
-            const int col = id % TT;
-            const int y = id / TT;
-            if (col < ncols) p.spec[spec_index<T>(d, c0, z, y, kx0 + col)] = sm[y * es + col];
-        }
+        for (int id = threadIdx.x; id < (L << lT); id += blockDim.x)
+            p.spec[gb[0] + id] = sm[id];
         return;
     }
     if (YMODE == 2) {
         fft_dit<T, false>(sm, lL, es, 1, es, p.tw);
-        for (int id = threadIdx.x; id < L * TT; id += blockDim.x) {
-            const int col = id % TT;
-            const int y = id / TT;
+        for (int id = threadIdx.x; id < (L << lT); id += blockDim.x) {
+            const int col = id & (TT - 1), y = id >> lT;
             if (col < ncols) {
                 V2<T>* q = sm + y * es + col;
-                V2<T> a = q[0], b = q[TT], c = q[2 * TT];
-                tensor_apply<T>(d, p.tensor, kx0 + col, y, 0, a, b, c);
-                q[0] = a; q[TT] = b; q[2 * TT] = c;
+                V2<T> a = q[0], bb = q[TT], c = q[2 * TT];
+                tensor_apply<T>(d, p.tensor, kx0 + col, y, 0, a, bb, c);
+                q[0] = a; q[TT] = bb; q[2 * TT] = c;
             }
         }
         __syncthreads();
     }
     fft_dif<T, true>(sm, lL, es, 1, es, p.tw);
-    const int tot3 = ny * es;
-    for (int id = threadIdx.x; id < tot3; id += blockDim.x) {
-        const int col = id % TT;
-        const int rest = id / TT;
-        const int cc = rest % NC;
-        const int y = rest / NC;
-        if (col < ncols)
-            p.spec[spec_index<T>(d, c0 + cc, z, y, kx0 + col)] = sm[bitrev(y, lL) * es + cc * TT + col];
+#pragma unroll
+    for (int cc = 0; cc < NC; ++cc) {
+        for (int id = threadIdx.x; id < (ny << lT); id += blockDim.x) {
+            const int col = id & (TT - 1), y = id >> lT;
+            p.spec[gb[cc] + id] = sm[bitrev(y, lL) * es + cc * TT + col];
+        }
     }
 }
 
@@ -228,41 +240,130 @@ __global__ void __launch_bounds__(MM_THREADS) k_zcol(PassParams<T> p) {
     const WorkItem w = p.items[blockIdx.x];
     if (sim_inactive(p, w.sim)) return;
     const SimDesc& d = p.desc[w.sim];
-    const int L = d.Pz, lL = d.lPz, TT = d.Tz, nz = d.nz;
-    const int ky = w.a, kx0 = w.b;
+    const int L = d.Pz, lL = d.lPz, TT = d.Ty, lT = d.lTy, nz = d.nz;
+    const int ky = w.a, b = w.b;
+    const int kx0 = b << lT;
     const int ncols = min(TT, d.Kx - kx0);
     const int es = 3 * TT;                      // layout [z][c][col]
-    const int tot = L * es;
+    const int tot = (L * 3) << lT;
     for (int id = threadIdx.x; id < tot; id += blockDim.x) {
-        const int col = id % TT;
-        const int rest = id / TT;
+        const int col = id & (TT - 1);
+        const int rest = id >> lT;
         const int c = rest % 3;
         const int z = rest / 3;
         V2<T> v = mk<T>((T)0, (T)0);
-        if (col < ncols && z < nz) v = p.spec[spec_index<T>(d, c, z, ky, kx0 + col)];
+        if (z < nz) v = p.spec[spec_block<T>(d, c, z, b) + ((long long)ky << lT) + col];
         sm[bitrev(z, lL) * es + c * TT + col] = v;
     }
     __syncthreads();
     fft_dit<T, false>(sm, lL, es, 1, es, p.tw);
-    for (int id = threadIdx.x; id < L * TT; id += blockDim.x) {
-        const int col = id % TT;
-        const int z = id / TT;
+    for (int id = threadIdx.x; id < (L << lT); id += blockDim.x) {
+        const int col = id & (TT - 1);
+        const int z = id >> lT;
         if (col < ncols) {
             V2<T>* q = sm + z * es + col;
-            V2<T> a = q[0], b = q[TT], c = q[2 * TT];
-            tensor_apply<T>(d, p.tensor, kx0 + col, ky, z, a, b, c);
-            q[0] = a; q[TT] = b; q[2 * TT] = c;
+            V2<T> a = q[0], bb = q[TT], c = q[2 * TT];
+            tensor_apply<T>(d, p.tensor, kx0 + col, ky, z, a, bb, c);
+            q[0] = a; q[TT] = bb; q[2 * TT] = c;
         }
     }
     __syncthreads();
     fft_dif<T, true>(sm, lL, es, 1, es, p.tw);
-    const int tot3 = nz * es;
+    const int tot3 = (nz * 3) << lT;
     for (int id = threadIdx.x; id < tot3; id += blockDim.x) {
-        const int col = id % TT;
-        const int rest = id / TT;
+        const int col = id & (TT - 1);
+        const int rest = id >> lT;
         const int c = rest % 3;
         const int z = rest / 3;
-        if (col < ncols) p.spec[spec_index<T>(d, c, z, ky, kx0 + col)] = sm[bitrev(z, lL) * es + c * TT + col];
+        p.spec[spec_block<T>(d, c, z, b) + ((long long)ky << lT) + col] = sm[bitrev(z, lL) * es + c * TT + col];
+    }
+}
+
+// ------------------------------------------------ y + z fused, cluster per block
+template <typename T, int PZ>
+__device__ void yzc_zstep(const PassParams<T>& p, const SimDesc& d, V2<T>* const (&rem)[8], int rank, int nz,
+                          int es, int kx0, int ncols) {
+    const int TT = d.Ty, lT = d.lTy, Py = d.Py;
+    const int ky_lo = (int)(((long long)rank * Py) / nz);
+    const int ky_hi = (int)(((long long)(rank + 1) * Py) / nz);
+    const int nwork = (ky_hi - ky_lo) << lT;
+    for (int id = threadIdx.x; id < nwork; id += blockDim.x) {
+        const int col = id & (TT - 1);
+        const int ky = ky_lo + (id >> lT);
+        if (col >= ncols) continue;
+        V2<T> X[3][PZ];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+#pragma unroll
+            for (int k = 0; k < PZ; ++k) X[c][k] = mk<T>((T)0, (T)0);
+        }
+        const int o = ky * es + col;
+#pragma unroll
+        for (int zz = 0; zz < 8; ++zz) {
+            if (zz < nz && zz < PZ) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) X[c][zz] = rem[zz][o + c * TT];
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) reg_fft<T, PZ, false>(X[c], p.tw);
+#pragma unroll
+        for (int kz = 0; kz < PZ; ++kz) tensor_apply<T>(d, p.tensor, kx0 + col, ky, kz, X[0][kz], X[1][kz], X[2][kz]);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) reg_fft<T, PZ, true>(X[c], p.tw);
+#pragma unroll
+        for (int zz = 0; zz < 8; ++zz) {
+            if (zz < nz && zz < PZ) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) rem[zz][o + c * TT] = X[c][zz];
+            }
+        }
+    }
+}
+
+// FP32: two clusters' CTAs per SM (128 registers); FP64 keeps the registers it needs.
+template <typename T, int PZ>
+__global__ void __launch_bounds__(MM_THREADS, sizeof(T) == 4 ? 2 : 1) k_yzc(PassParams<T> p) {
+    namespace cg = cooperative_groups;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    V2<T>* sm = reinterpret_cast<V2<T>*>(smraw);
+    cg::cluster_group cl = cg::this_cluster();
+    const int ncl = (int)cl.num_blocks();
+    const int rank = (int)cl.block_rank();
+    const WorkItem w = p.items[blockIdx.x / ncl];
+    if (sim_inactive(p, w.sim)) return;          // uniform over the cluster: one simulation per cluster
+    const SimDesc& d = p.desc[w.sim];
+    const int L = d.Py, lL = d.lPy, TT = d.Ty, lT = d.lTy, ny = d.ny, nz = d.nz;
+    const int z = rank, b = w.b;
+    const int kx0 = b << lT;
+    const int ncols = min(TT, d.Kx - kx0);
+    const int es = 3 * TT;                      // layout [y][c][col]
+    long long gb[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) gb[c] = spec_block<T>(d, c, z, b);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        for (int id = threadIdx.x; id < (L << lT); id += blockDim.x) {
+            const int col = id & (TT - 1), y = id >> lT;
+            const V2<T> v = y < ny ? p.spec[gb[c] + id] : mk<T>((T)0, (T)0);
+            sm[bitrev(y, lL) * es + c * TT + col] = v;
+        }
+    }
+    __syncthreads();
+    fft_dit<T, false>(sm, lL, es, 1, es, p.tw);
+    cl.sync();                                  // every plane transformed along y
+    V2<T>* rem[8];
+#pragma unroll
+    for (int zz = 0; zz < 8; ++zz) rem[zz] = zz < nz ? cl.map_shared_rank(sm, zz) : sm;
+    yzc_zstep<T, PZ>(p, d, rem, rank, nz, es, kx0, ncols);   // PZ == d.Pz, fixed by nz per launch
+    cl.sync();                                  // every row back in its owner's plane
+    fft_dif<T, true>(sm, lL, es, 1, es, p.tw);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        for (int id = threadIdx.x; id < (ny << lT); id += blockDim.x) {
+            const int col = id & (TT - 1), y = id >> lT;
+            p.spec[gb[c] + id] = sm[bitrev(y, lL) * es + c * TT + col];
+        }
     }
 }
 
@@ -304,6 +405,7 @@ __device__ __forceinline__ T nb_ms(const PassParams<T>& p, const SimDesc& d, boo
     return msarr ? p.Ms[d.ms_off + cell] : (T)1;
 }
 
+// Shared memory: 3*nrows sequences of Kx complex values, padded (pidx).
 template <typename T>
 __global__ void __launch_bounds__(MM_THREADS) k_xinv(PassParams<T> p, const T* __restrict__ ys) {
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -315,26 +417,31 @@ __global__ void __launch_bounds__(MM_THREADS) k_xinv(PassParams<T> p, const T* _
     const SimDesc& d = p.desc[w.sim];
     const int nx = d.nx, ny = d.ny, nz = d.nz, N = d.ncells;
     const int lLh = d.lPx - 1, Lh = 1 << lLh, Kx = d.Kx;
+    const int SK = padded_len(Kx);
     const int row0 = w.a, nrows = w.b;
     const long long base = d.off - p.off_adjust;
     const bool demag = (d.flags & F_DEMAG) != 0;
     const bool msarr = (d.flags & F_MSARR) != 0;
     if (demag) {
-        const int tot = 3 * nrows * Kx;
-        for (int id = threadIdx.x; id < tot; id += blockDim.x) {
+        const int tot1 = 3 * nrows * Kx;
+        for (int id = threadIdx.x; id < tot1; id += blockDim.x) {
             const int q = id / Kx, k = id - q * Kx;
             const int c = q / nrows, r = q - c * nrows;
             const int row = row0 + r;
             const int z = row / ny, y = row - z * ny;
-            sm[q * Kx + k] = p.spec[spec_index<T>(d, c, z, y, k)];
+            sm[q * SK + ix<true>(k, 1)] = p.spec[spec_index<T>(d, c, z, y, k)];
         }
         __syncthreads();
         if (d.Py == 1 && d.Pz == 1) {            // x is the only transformed axis
             for (int id = threadIdx.x; id < nrows * Kx; id += blockDim.x) {
                 const int r = id / Kx, k = id - r * Kx;
-                V2<T> a = sm[(0 * nrows + r) * Kx + k], b = sm[(1 * nrows + r) * Kx + k], c = sm[(2 * nrows + r) * Kx + k];
+                const int pk = ix<true>(k, 1);
+                V2<T>* s0 = sm + (0 * nrows + r) * SK;
+                V2<T>* s1 = sm + (1 * nrows + r) * SK;
+                V2<T>* s2 = sm + (2 * nrows + r) * SK;
+                V2<T> a = s0[pk], b = s1[pk], c = s2[pk];
                 tensor_apply<T>(d, p.tensor, k, 0, 0, a, b, c);
-                sm[(0 * nrows + r) * Kx + k] = a; sm[(1 * nrows + r) * Kx + k] = b; sm[(2 * nrows + r) * Kx + k] = c;
+                s0[pk] = a; s1[pk] = b; s2[pk] = c;
             }
             __syncthreads();
         }
@@ -343,26 +450,26 @@ __global__ void __launch_bounds__(MM_THREADS) k_xinv(PassParams<T> p, const T* _
         const int tot2 = 3 * nrows * hk;
         for (int id = threadIdx.x; id < tot2; id += blockDim.x) {
             const int q = id / hk, k = id - q * hk;
-            V2<T>* s = sm + q * Kx;
+            V2<T>* s = sm + q * SK;
             if (k == 0) {
-                const V2<T> X0 = s[0], XL = cconj(s[Lh]);
+                const V2<T> X0 = s[ix<true>(0, 1)], XL = cconj(s[ix<true>(Lh, 1)]);
                 const V2<T> e = X0 + XL, o = X0 - XL;
-                s[0] = mk<T>(e.x - o.y, e.y + o.x);
+                s[ix<true>(0, 1)] = mk<T>(e.x - o.y, e.y + o.x);
             } else {
                 const int k2 = Lh - k;
-                const V2<T> Xa = s[k], Xb = s[k2];
+                const V2<T> Xa = s[ix<true>(k, 1)], Xb = s[ix<true>(k2, 1)];
                 const V2<T> ea = Xa + cconj(Xb);
                 const V2<T> ta = cmul(twid<T, true>(p.tw, k, d.lPx), Xa - cconj(Xb));
-                s[k] = mk<T>(ea.x - ta.y, ea.y + ta.x);
+                s[ix<true>(k, 1)] = mk<T>(ea.x - ta.y, ea.y + ta.x);
                 if (k2 != k) {
                     const V2<T> eb = Xb + cconj(Xa);
                     const V2<T> tb = cmul(twid<T, true>(p.tw, k2, d.lPx), Xb - cconj(Xa));
-                    s[k2] = mk<T>(eb.x - tb.y, eb.y + tb.x);
+                    s[ix<true>(k2, 1)] = mk<T>(eb.x - tb.y, eb.y + tb.x);
                 }
             }
         }
         __syncthreads();
-        fft_dif<T, true>(sm, lLh, 3 * nrows, Kx, 1, p.tw);
+        fft_dif<T, true, true>(sm, lLh, 3 * nrows, SK, 1, p.tw);
     }
 
     // per-cell local fields and torque
@@ -396,10 +503,10 @@ __global__ void __launch_bounds__(MM_THREADS) k_xinv(PassParams<T> p, const T* _
             const T inv = (T)1 / (mu0 * ms);
             T hd0 = 0, hd1 = 0, hd2 = 0;
             if (demag) {
-                const int pos = bitrev(x >> 1, lLh);
-                const V2<T> v0 = sm[(0 * nrows + r) * Kx + pos];
-                const V2<T> v1 = sm[(1 * nrows + r) * Kx + pos];
-                const V2<T> v2 = sm[(2 * nrows + r) * Kx + pos];
+                const int pos = ix<true>(bitrev(x >> 1, lLh), 1);
+                const V2<T> v0 = sm[(0 * nrows + r) * SK + pos];
+                const V2<T> v1 = sm[(1 * nrows + r) * SK + pos];
+                const V2<T> v2 = sm[(2 * nrows + r) * SK + pos];
                 hd0 = (x & 1) ? v0.y : v0.x;
                 hd1 = (x & 1) ? v1.y : v1.x;
                 hd2 = (x & 1) ? v2.y : v2.x;

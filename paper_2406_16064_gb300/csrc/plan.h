@@ -1,0 +1,90 @@
+// Host-side planning of one simulation: padded FFT lengths, tile shapes and
+// the work items of every pass.  Shared by the context API and the
+// allocation-free entry point so both lay out a simulation the same way.
+#pragma once
+#include <algorithm>
+#include <vector>
+
+#include "mm_kernels.cuh"
+
+namespace mm {
+
+inline int plan_ilog2(int v) {
+    int l = 0;
+    while ((1 << l) < v) ++l;
+    return l;
+}
+
+inline int plan_pow2floor(int v) {
+    int p = 1;
+    while (p * 2 <= v) p *= 2;
+    return p;
+}
+
+// padded FFT length: the smallest power of two >= 2n - 1 (1 for n == 1 unless min2)
+inline int plan_pad_len(int n, bool min2) {
+    if (n <= 1) return min2 ? 2 : 1;
+    int p = 1;
+    while (p < 2 * n - 1) p <<= 1;
+    return p;
+}
+
+// Largest plane count handled by the cluster-fused y/z pass (portable cluster size).
+constexpr int kMaxClusterPlanes = 8;
+
+// Fill the padded sizes, tensor bins and tile shapes of d from d.nx, d.ny, d.nz.
+//   Rx : rows per x-pass CTA, 3 * Rx * padded_len(Kx) <= 1536 complex values
+//   Ty : kx block width (power of two, <= 32): Py * Ty <= 4096 (FP32) / 2048 (FP64)
+inline void plan_geometry(SimDesc& d, bool f32) {
+    d.Px = plan_pad_len(d.nx, true);
+    d.Py = plan_pad_len(d.ny, false);
+    d.Pz = plan_pad_len(d.nz, false);
+    d.lPx = plan_ilog2(d.Px);
+    d.lPy = plan_ilog2(d.Py);
+    d.lPz = plan_ilog2(d.Pz);
+    d.Kx = d.Px / 2 + 1;
+    d.Pyh = d.Py / 2 + 1;
+    d.Pzh = d.Pz / 2 + 1;
+    d.ncomp = d.Pz > 1 ? 6 : 4;
+    const int rows = d.ny * d.nz;
+    d.Rx = std::max(1, std::min(rows, 1536 / (3 * padded_len(d.Kx))));
+    const int EB = f32 ? 4096 : 2048;
+    const int kcap = std::min(32, 1 << plan_ilog2(d.Kx));
+    d.Ty = std::min(kcap, plan_pow2floor(std::max(1, EB / d.Py)));
+    d.lTy = plan_ilog2(d.Ty);
+    d.NBx = (d.Kx + d.Ty - 1) >> d.lTy;
+}
+
+inline long long plan_spec_elems(const SimDesc& d) { return 3LL * d.nz * d.NBx * d.Py * d.Ty; }
+
+struct PlanItems {
+    std::vector<WorkItem> x, y13, z, y2, yzc[kMaxClusterPlanes + 1];
+    size_t smem_x = 0, smem_y13 = 0, smem_z = 0, smem_y2 = 0, smem_yzc = 0;
+};
+
+// Append the work items of simulation sid; vsz = bytes of one complex value.
+inline void plan_items(const SimDesc& d, int sid, size_t vsz, PlanItems& P) {
+    const int rows = d.ny * d.nz;
+    for (int r0 = 0; r0 < rows; r0 += d.Rx) P.x.push_back({sid, r0, std::min(d.Rx, rows - r0), 0});
+    P.smem_x = std::max(P.smem_x, 3 * (size_t)d.Rx * padded_len(d.Kx) * vsz);
+    if (!(d.flags & F_DEMAG)) return;
+    if (d.Pz > 1 && d.Py > 1 && d.nz <= kMaxClusterPlanes) {
+        for (int b = 0; b < d.NBx; ++b) P.yzc[d.nz].push_back({sid, 0, b, 0});
+        P.smem_yzc = std::max(P.smem_yzc, 3 * (size_t)d.Py * d.Ty * vsz);
+    } else if (d.Pz > 1) {
+        if (d.Py > 1) {
+            for (int z = 0; z < d.nz; ++z)
+                for (int b = 0; b < d.NBx; ++b)
+                    for (int c = 0; c < 3; ++c) P.y13.push_back({sid, z, b, c});
+            P.smem_y13 = std::max(P.smem_y13, (size_t)d.Py * d.Ty * vsz);
+        }
+        for (int ky = 0; ky < d.Py; ++ky)
+            for (int b = 0; b < d.NBx; ++b) P.z.push_back({sid, ky, b, 0});
+        P.smem_z = std::max(P.smem_z, 3 * (size_t)d.Pz * d.Ty * vsz);
+    } else if (d.Py > 1) {
+        for (int b = 0; b < d.NBx; ++b) P.y2.push_back({sid, 0, b, -1});
+        P.smem_y2 = std::max(P.smem_y2, 3 * (size_t)d.Py * d.Ty * vsz);
+    }
+}
+
+}  // namespace mm

@@ -26,6 +26,7 @@
 
 #include "engine.cuh"
 #include "mm.h"
+#include "plan.h"
 
 using namespace mm;
 
@@ -44,25 +45,6 @@ void* g_base[MM_STATIC_MAX_DEVICES] = {};
 int err(int code, const char* msg) {
     mm_internal_set_error(msg);
     return code;
-}
-
-int lg2(int v) {
-    int l = 0;
-    while ((1 << l) < v) ++l;
-    return l;
-}
-
-int padded(int n, bool min2) {
-    if (n <= 1) return min2 ? 2 : 1;
-    int p = 1;
-    while (p < 2 * n - 1) p <<= 1;
-    return p;
-}
-
-int floor2(int v) {
-    int p = 1;
-    while (p * 2 <= v) p *= 2;
-    return p;
 }
 
 // bump allocator over the static array (offsets only)
@@ -103,19 +85,17 @@ extern "C" int mm_rhs_eval_static(const mm_mesh* mesh, const mm_material* mat, i
     }
     unsigned char* base = (unsigned char*)g_base[dev];
 
-    // descriptor of the single simulation (same layout rules as a context)
+    // descriptor of the single simulation (same layout rules as a context: plan.h)
     SimDesc d;
     memset(&d, 0, sizeof(d));
     d.nx = mesh->nx; d.ny = mesh->ny; d.nz = mesh->nz;
     const long long n = (long long)d.nx * d.ny * d.nz;
     if (n > (1LL << 26)) return err(MM_EINVAL, "mm_rhs_eval_static: mesh too large for the static scratch");
     d.ncells = (int)n;
-    d.Px = padded(d.nx, true); d.Py = padded(d.ny, false); d.Pz = padded(d.nz, false);
     const int lim = f32 ? 8192 : 4096;
-    if (d.Px > 8192 || d.Py > lim || d.Pz > lim) return err(MM_EINVAL, "mm_rhs_eval_static: padded FFT too long");
-    d.lPx = lg2(d.Px); d.lPy = lg2(d.Py); d.lPz = lg2(d.Pz);
-    d.Kx = d.Px / 2 + 1; d.Pyh = d.Py / 2 + 1; d.Pzh = d.Pz / 2 + 1;
-    d.ncomp = d.Pz > 1 ? 6 : 4;
+    if (plan_pad_len(d.nx, true) > 8192 || plan_pad_len(d.ny, false) > lim || plan_pad_len(d.nz, false) > lim)
+        return err(MM_EINVAL, "mm_rhs_eval_static: padded FFT too long");
+    plan_geometry(d, f32);
     const double un = sqrt(mat->u[0] * mat->u[0] + mat->u[1] * mat->u[1] + mat->u[2] * mat->u[2]);
     if (mat->Ku != 0.0 && !(un > 0)) return err(MM_EINVAL, "mm_rhs_eval_static: anisotropy axis is zero");
     for (int i = 0; i < 3; ++i) { d.u[i] = un > 0 ? mat->u[i] / un : 0.0; d.H[i] = mat->H[i]; }
@@ -130,33 +110,13 @@ extern "C" int mm_rhs_eval_static(const mm_mesh* mesh, const mm_material* mat, i
     d.off = 0;
     d.spec_off = 0;
     d.tens_off = 0;
-    const int EB = f32 ? 4096 : 2048;
-    const int rows = d.ny * d.nz;
-    d.Rx = std::max(1, std::min(rows, EB / d.Kx));
-    const int kcap = std::min(32, 1 << lg2(d.Kx));
-    d.Ty = std::min(kcap, floor2(std::max(1, (d.Pz > 1 ? 3 : 1) * EB / d.Py)));
-    d.Tz = std::min(kcap, floor2(std::max(1, EB / d.Pz)));
     const bool demag = mat->demag != 0;
-    std::vector<WorkItem> xv, y13v, zv, y2v;
-    for (int r0 = 0; r0 < rows; r0 += d.Rx) xv.push_back({0, r0, std::min(d.Rx, rows - r0), 0});
-    if (demag) {
-        if (d.Pz > 1) {
-            if (d.Py > 1)
-                for (int z = 0; z < d.nz; ++z)
-                    for (int k0 = 0; k0 < d.Kx; k0 += d.Ty)
-                        for (int c = 0; c < 3; ++c) y13v.push_back({0, z, k0, c});
-            for (int ky = 0; ky < d.Py; ++ky)
-                for (int k0 = 0; k0 < d.Kx; k0 += d.Tz) zv.push_back({0, ky, k0, 0});
-        } else if (d.Py > 1) {
-            for (int k0 = 0; k0 < d.Kx; k0 += d.Ty) y2v.push_back({0, 0, k0, -1});
-        }
-    }
     const size_t vsz = 2 * e;
-    const size_t smem_x = 3 * (size_t)d.Rx * d.Kx * vsz;
-    const size_t smem_y13 = (size_t)d.Py * d.Ty * vsz;
-    const size_t smem_y2 = 3 * (size_t)d.Py * d.Ty * vsz;
-    const size_t smem_z = 3 * (size_t)d.Pz * d.Tz * vsz;
-    if (smem_x > 227 * 1024 - 4096 || smem_y13 > 227 * 1024 || smem_y2 > 227 * 1024 || smem_z > 227 * 1024)
+    PlanItems P;
+    plan_items(d, 0, vsz, P);
+    const std::vector<WorkItem>& yzv = P.yzc[std::min(d.nz, kMaxClusterPlanes)];
+    const size_t cap = 227 * 1024;
+    if (P.smem_x > cap - 4096 || P.smem_y13 > cap || P.smem_y2 > cap || P.smem_z > cap || P.smem_yzc > cap)
         return err(MM_EINVAL, "mm_rhs_eval_static: FFT tile exceeds shared memory");
 
     // carve the static array
@@ -166,12 +126,13 @@ extern "C" int mm_rhs_eval_static(const mm_mesh* mesh, const mm_material* mat, i
     const size_t o_desc = cv.take(sizeof(SimDesc));
     const size_t o_state = cv.take(sizeof(SimState));
     const size_t o_diag = cv.take(2 * sizeof(unsigned long long));
-    const size_t o_xi = cv.take(std::max<size_t>(1, xv.size()) * sizeof(WorkItem));
-    const size_t o_y13 = cv.take(std::max<size_t>(1, y13v.size()) * sizeof(WorkItem));
-    const size_t o_z = cv.take(std::max<size_t>(1, zv.size()) * sizeof(WorkItem));
-    const size_t o_y2 = cv.take(std::max<size_t>(1, y2v.size()) * sizeof(WorkItem));
+    const size_t o_xi = cv.take(std::max<size_t>(1, P.x.size()) * sizeof(WorkItem));
+    const size_t o_y13 = cv.take(std::max<size_t>(1, P.y13.size()) * sizeof(WorkItem));
+    const size_t o_z = cv.take(std::max<size_t>(1, P.z.size()) * sizeof(WorkItem));
+    const size_t o_y2 = cv.take(std::max<size_t>(1, P.y2.size()) * sizeof(WorkItem));
+    const size_t o_yz = cv.take(std::max<size_t>(1, yzv.size()) * sizeof(WorkItem));
     const long long tens_elems = (long long)d.ncomp * d.Pzh * d.Pyh * d.Kx;
-    const long long spec_elems = demag ? 3LL * d.nz * d.Py * d.Kx : 0;
+    const long long spec_elems = demag ? plan_spec_elems(d) : 0;
     const size_t o_tens = cv.take(demag ? (size_t)tens_elems * e : 16);
     const size_t o_spec = cv.take(demag ? (size_t)spec_elems * vsz : 16);
     const size_t o_oct = cv.take(demag ? (size_t)6 * n * 8 : 16);
@@ -191,10 +152,11 @@ extern "C" int mm_rhs_eval_static(const mm_mesh* mesh, const mm_material* mat, i
         return v.empty() ? cudaSuccess
                          : cudaMemcpyAsync(base + off, v.data(), v.size() * sizeof(WorkItem), cudaMemcpyHostToDevice, s);
     };
-    SCK(up(o_xi, xv));
-    SCK(up(o_y13, y13v));
-    SCK(up(o_z, zv));
-    SCK(up(o_y2, y2v));
+    SCK(up(o_xi, P.x));
+    SCK(up(o_y13, P.y13));
+    SCK(up(o_z, P.z));
+    SCK(up(o_y2, P.y2));
+    SCK(up(o_yz, yzv));
     launch_twiddles(s, base + o_twd, base + o_twf);
     upload_gauss_legendre();
     engine_set_attributes();
@@ -227,14 +189,16 @@ extern "C" int mm_rhs_eval_static(const mm_mesh* mesh, const mm_material* mat, i
     L.desc = (const SimDesc*)(base + o_desc);
     L.state = (SimState*)(base + o_state);
     L.nsims = 1;
-    L.x = {(const WorkItem*)(base + o_xi), (int)xv.size()};
-    L.y13 = {(const WorkItem*)(base + o_y13), (int)y13v.size()};
-    L.z = {(const WorkItem*)(base + o_z), (int)zv.size()};
-    L.y2 = {(const WorkItem*)(base + o_y2), (int)y2v.size()};
-    L.smem_x = smem_x;
-    L.smem_y13 = y13v.empty() ? 0 : smem_y13;
-    L.smem_z = zv.empty() ? 0 : smem_z;
-    L.smem_y2 = y2v.empty() ? 0 : smem_y2;
+    L.x = {(const WorkItem*)(base + o_xi), (int)P.x.size()};
+    L.y13 = {(const WorkItem*)(base + o_y13), (int)P.y13.size()};
+    L.z = {(const WorkItem*)(base + o_z), (int)P.z.size()};
+    L.y2 = {(const WorkItem*)(base + o_y2), (int)P.y2.size()};
+    if (!yzv.empty()) L.yzc[d.nz] = {(const WorkItem*)(base + o_yz), (int)yzv.size()};
+    L.smem_x = P.smem_x;
+    L.smem_y13 = P.smem_y13;
+    L.smem_z = P.smem_z;
+    L.smem_y2 = P.smem_y2;
+    L.smem_yzc = P.smem_yzc;
     L.tensor = base + o_tens;
     L.Ms = nullptr;
     L.tw = f32 ? (const void*)(base + o_twf) : (const void*)(base + o_twd);

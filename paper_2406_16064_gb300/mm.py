@@ -242,11 +242,11 @@ class Context:
 
     # ---- misc
     KINDS = ("x_forward", "y_forward", "z_fused", "y_inverse", "y_fused", "x_inverse_epilogue",
-             "control", "project", "neb")
+             "control", "project", "neb", "yz_cluster")
 
     def profile_attempts(self, reps):
-        ms = np.zeros(9)
-        cnt = (C.c_longlong * 9)()
+        ms = np.zeros(10)
+        cnt = (C.c_longlong * 10)()
         self._check(self.L.mm_profile_attempts(self.h, reps, _dptr(ms), cnt))
         return {k: (ms[i], cnt[i]) for i, k in enumerate(self.KINDS)}
 

@@ -34,6 +34,10 @@ MESHES = [
     (5, 1, 6, 1e-9, 2e-9, 3e-9),
     (32, 32, 1, 2.5e-9, 2.5e-9, 3e-9),
     (33, 17, 2, 2e-9, 2e-9, 1e-9),
+    (9, 6, 5, 2e-9, 2e-9, 1e-9),       # cluster of 5 planes, padded z length 16
+    (6, 5, 8, 2e-9, 2e-9, 1e-9),       # cluster of 8 planes
+    (5, 4, 9, 2e-9, 2e-9, 1e-9),       # more planes than a cluster: separate y and z passes
+    (70, 3, 1, 1e-9, 2e-9, 1e-9),      # several kx blocks with a ragged last block
 ]
 
 
