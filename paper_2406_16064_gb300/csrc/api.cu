@@ -166,7 +166,10 @@ int validate_items(mm_ctx* C) {
     for (const WorkItem& w : P.x) {
         const SimDesc& d = C->sims[w.sim].d;
         if (w.a < 0 || w.b < 1 || w.a + w.b > d.ny * d.nz) return fail(C, MM_EBOUNDS, "x item rows");
-        if (3ULL * w.b * padded_len(d.Kx) * vsz > P.smem_x) return fail(C, MM_EBOUNDS, "x item smem");
+        if (2 * 3ULL * w.b * padded_len(d.Kx) * vsz > P.smem_x) return fail(C, MM_EBOUNDS, "x item smem");
+        if (w.b > d.ny) return fail(C, MM_EBOUNDS, "x item spans more than two planes");
+        if (plan_spec_elems(d) >= (1LL << 31) || 3LL * d.ncells >= (1LL << 31))
+            return fail(C, MM_EINVAL, "simulation too large for 32-bit per-simulation offsets");
     }
     for (const WorkItem& w : P.y13) {
         const SimDesc& d = C->sims[w.sim].d;

@@ -92,7 +92,10 @@ static void issue_passes(const Launch& L, PassParams<T> p, const T* ys, bool inc
     }
     if (include_xinv) {
         p.items = L.x.dev;
-        k_xinv<T><<<L.x.count, MM_THREADS, L.smem_x, s>>>(p, ys);
+        if (p.mode == MODE_ENERGY || p.mode == MODE_NEB)
+            k_xinv<T, true><<<L.x.count, MM_THREADS, L.smem_x, s>>>(p, ys);
+        else
+            k_xinv<T, false><<<L.x.count, MM_THREADS, L.smem_x, s>>>(p, ys);
         if (hk) hk->mark(KIND_XINV);
         ++n;
     }
@@ -192,7 +195,8 @@ template <typename T>
 static void set_attrs() {
     const int mx = 227 * 1024;
     cudaFuncSetAttribute(k_xfwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    cudaFuncSetAttribute(k_xinv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx - 4096);
+    cudaFuncSetAttribute(k_xinv<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx - 4096);
+    cudaFuncSetAttribute(k_xinv<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx - 4096);
     cudaFuncSetAttribute(k_ycol<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     cudaFuncSetAttribute(k_ycol<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     cudaFuncSetAttribute(k_ycol<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);

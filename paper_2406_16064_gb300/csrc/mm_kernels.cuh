@@ -212,6 +212,30 @@ __host__ __device__ constexpr int brev_ct(int v) {
     return r;
 }
 
+// cos(2 pi r / 16) and sin(2 pi r / 16), r = 0..3 (the rest by symmetry)
+__device__ __forceinline__ double w16c(int r) {
+    return r == 0 ? 1.0 : r == 1 ? 0.92387953251128675613 : r == 2 ? 0.70710678118654752440 : 0.38268343236508977173;
+}
+
+// W_M^r = exp(-+2 pi i r / M) for M <= 16, from compile-time constants
+template <typename T, bool INV>
+__device__ __forceinline__ V2<T> small_twid(int r, int logM) {
+    const int q = r << (4 - logM);              // in sixteenths of a turn, 0..15
+    const int qm = q & 3;
+    const T c = (T)w16c(qm), s = (T)w16c(4 - qm == 4 ? 0 : 4 - qm);   // cos, sin of qm/16 turn
+    const T sn = qm == 0 ? (T)0 : s;
+    // rotate by the quarter turns in q >> 2: (c, -sn) * (-i)^(q>>2)
+    V2<T> w;
+    switch (q >> 2) {
+        case 0: w = mk<T>(c, -sn); break;
+        case 1: w = mk<T>(-sn, -c); break;
+        case 2: w = mk<T>(-c, sn); break;
+        default: w = mk<T>(sn, c); break;
+    }
+    if (INV) w.y = -w.y;
+    return w;
+}
+
 template <typename T, int PZ, bool INV>
 __device__ __forceinline__ void reg_fft(V2<T> (&x)[PZ], const V2<T>* __restrict__ tw) {
     constexpr int LG = Log2<PZ>::v;
@@ -225,8 +249,8 @@ __device__ __forceinline__ void reg_fft(V2<T> (&x)[PZ], const V2<T>* __restrict_
         for (int base = 0; base < PZ; base += 2 * s) {
 #pragma unroll
             for (int r = 0; r < s; ++r) {
-                const V2<T> w = twid<T, INV>(tw, r, lg + 1);
-                const V2<T> a = y[base + r], b = cmul(y[base + r + s], w);
+                const V2<T> w = small_twid<T, INV>(r, lg + 1);
+                const V2<T> a = y[base + r], b = r == 0 ? y[base + r + s] : cmul(y[base + r + s], w);
                 y[base + r] = a + b;
                 y[base + r + s] = a - b;
             }
@@ -234,6 +258,61 @@ __device__ __forceinline__ void reg_fft(V2<T> (&x)[PZ], const V2<T>* __restrict_
     }
 #pragma unroll
     for (int i = 0; i < PZ; ++i) x[i] = y[i];
+}
+
+// One Stockham auto-sort stage of radix R over nseq padded (pidx) sequences of
+// length 2^lL, from src to dst: butterfly j reads x[j + r L/R], multiplies by
+// W_{Ns R}^{(j mod Ns) r}, does an R-point DFT in registers and writes
+// x'[(j / Ns) Ns R + (j mod Ns) + r Ns], Ns = 2^lNs the length already
+// transformed.  Natural order in, natural order out after the last stage.
+template <typename T, bool INV, int R>
+__device__ __forceinline__ void stockham_stage(const V2<T>* src, V2<T>* dst, int lL, int lNs, int nseq, int sstride,
+                                               const V2<T>* __restrict__ tw) {
+    constexpr int LR = Log2<R>::v;
+    const int lnb = lL - LR;
+    const int nb = 1 << lnb;
+    const int tot = nseq << lnb;
+    for (int id = threadIdx.x; id < tot; id += blockDim.x) {
+        const int seq = id >> lnb, j = id & (nb - 1);
+        const V2<T>* s = src + seq * sstride;
+        V2<T>* d = dst + seq * sstride;
+        const int k = j & ((1 << lNs) - 1);
+        V2<T> v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = s[ix<true>(j + (r << lnb), 1)];
+        if (lNs > 0) {
+#pragma unroll
+            for (int r = 1; r < R; ++r) v[r] = cmul(v[r], twid<T, INV>(tw, k * r, lNs + LR));
+        }
+        reg_fft<T, R, INV>(v, tw);
+        const int o = ((j >> lNs) << (lNs + LR)) + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) d[ix<true>(o + (r << lNs), 1)] = v[r];
+    }
+}
+
+// Full unnormalised FFT of nseq padded sequences of length 2^lL (natural
+// order in and out) with Stockham stages of radix up to 2^MAXLR, ping-ponging
+// between a and b.  Returns the buffer that holds the result.  Ends with
+// __syncthreads().
+template <typename T, bool INV, int MAXLR>
+__device__ V2<T>* stockham_fft(V2<T>* a, V2<T>* b, int lL, int nseq, int sstride, const V2<T>* __restrict__ tw) {
+    int lNs = 0;
+    while (lNs < lL) {
+        const int rem = lL - lNs;
+        int lr = rem < MAXLR ? rem : MAXLR;
+        if (rem - lr == 1 && lr > 2) lr -= 1;          // avoid a trailing radix-2 stage
+        switch (lr) {
+            case 1: stockham_stage<T, INV, 2>(a, b, lL, lNs, nseq, sstride, tw); break;
+            case 2: stockham_stage<T, INV, 4>(a, b, lL, lNs, nseq, sstride, tw); break;
+            case 3: stockham_stage<T, INV, 8>(a, b, lL, lNs, nseq, sstride, tw); break;
+            default: stockham_stage<T, INV, (MAXLR >= 4 ? 16 : 8)>(a, b, lL, lNs, nseq, sstride, tw); break;
+        }
+        __syncthreads();
+        V2<T>* t = a; a = b; b = t;
+        lNs += lr;
+    }
+    return a;
 }
 
 // Parameters of every pass kernel (passed by value).

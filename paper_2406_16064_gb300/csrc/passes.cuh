@@ -75,26 +75,30 @@ __device__ __forceinline__ bool sim_inactive(const PassParams<T>& p, int sim) {
 }
 
 // ---------------------------------------------------------------- x forward
-// Shared memory: 3*nrows sequences of Lh complex values, padded (pidx).
+// Shared memory: two buffers of 3*nrows padded sequences (pidx) of Lh complex
+// values, sequence q = 3 r + c (row r of the tile, component c).
 template <typename T>
 __global__ void __launch_bounds__(MM_THREADS) k_xfwd(PassParams<T> p) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    V2<T>* sm = reinterpret_cast<V2<T>*>(smraw);
     const WorkItem w = p.items[blockIdx.x];
     if (sim_inactive(p, w.sim)) return;
     const SimDesc& d = p.desc[w.sim];
-    const int nx = d.nx, ny = d.ny, N = d.ncells;
+    const int nx = d.nx, ny = d.ny;
+    const long long N = d.ncells;
     const int lLh = d.lPx - 1, Lh = 1 << lLh;
     const int SL = padded_len(Lh);
     const int row0 = w.a, nrows = w.b;
-    const long long base = d.off - p.off_adjust;
+    const int nseq = 3 * nrows;
+    V2<T>* bufA = reinterpret_cast<V2<T>*>(smraw);
+    V2<T>* bufB = bufA + nseq * SL;
+    const long long base = d.off - p.off_adjust + (long long)row0 * nx;   // first cell of the tile
     const bool demag = (d.flags & F_DEMAG) != 0;
     const bool msarr = (d.flags & F_MSARR) != 0;
     const T hstep = (T)((p.mode == MODE_RK || p.mode == MODE_NEB) ? p.state[w.sim].h : 0.0);
+    const T* __restrict__ msp = msarr ? p.Ms + d.ms_off + (long long)row0 * nx : nullptr;
     const int tot = nrows << lLh;
     for (int id = threadIdx.x; id < tot; id += blockDim.x) {
         const int r = id >> lLh, n = id & (Lh - 1);
-        const long long row = row0 + r;
         V2<T> val[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) val[c] = mk<T>((T)0, (T)0);
@@ -102,42 +106,42 @@ __global__ void __launch_bounds__(MM_THREADS) k_xfwd(PassParams<T> p) {
         for (int h2 = 0; h2 < 2; ++h2) {
             const int x = 2 * n + h2;
             if (x < nx) {
-                const long long cell = row * nx + x;
+                const int cell = r * nx + x;                   // within the tile
                 T yv[3];
 #pragma unroll
-                for (int c = 0; c < 3; ++c) yv[c] = p.m[base + (long long)c * N + cell];
+                for (int c = 0; c < 3; ++c) yv[c] = p.m[base + c * N + cell];
                 if (p.nk > 0) {
                     T acc[3] = {(T)0, (T)0, (T)0};
                     for (int j = 0; j < p.nk; ++j) {
                         if (p.a[j] != 0.0) {
                             const T aj = (T)p.a[j];
-                            const T* kj = p.kvec[j];
+                            const T* kj = p.kvec[j] + base + cell;
 #pragma unroll
-                            for (int c = 0; c < 3; ++c) acc[c] += aj * kj[base + (long long)c * N + cell];
+                            for (int c = 0; c < 3; ++c) acc[c] += aj * kj[c * N];
                         }
                     }
 #pragma unroll
                     for (int c = 0; c < 3; ++c) yv[c] += hstep * acc[c];
                     if (p.write_y) {
 #pragma unroll
-                        for (int c = 0; c < 3; ++c) p.ybuf[base + (long long)c * N + cell] = yv[c];
+                        for (int c = 0; c < 3; ++c) p.ybuf[base + c * N + cell] = yv[c];
                     }
                     if (p.stage == 7) {
                         T ev[3] = {(T)0, (T)0, (T)0};
                         for (int j = 0; j < 6; ++j) {
                             if (p.e[j] != 0.0) {
                                 const T ej = (T)p.e[j];
-                                const T* kj = p.kvec[j];
+                                const T* kj = p.kvec[j] + base + cell;
 #pragma unroll
-                                for (int c = 0; c < 3; ++c) ev[c] += ej * kj[base + (long long)c * N + cell];
+                                for (int c = 0; c < 3; ++c) ev[c] += ej * kj[c * N];
                             }
                         }
 #pragma unroll
-                        for (int c = 0; c < 3; ++c) p.errp[base + (long long)c * N + cell] = ev[c];
+                        for (int c = 0; c < 3; ++c) p.errp[base + c * N + cell] = ev[c];
                     }
                 }
                 if (demag) {
-                    const T ms = msarr ? p.Ms[d.ms_off + cell] : (T)d.Ms;
+                    const T ms = msarr ? msp[cell] : (T)d.Ms;
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
                         if (h2 == 0) val[c].x = ms * yv[c]; else val[c].y = ms * yv[c];
@@ -146,28 +150,34 @@ __global__ void __launch_bounds__(MM_THREADS) k_xfwd(PassParams<T> p) {
             }
         }
         if (demag) {
-            const int pos = ix<true>(bitrev(n, lLh), 1);
+            const int pos = ix<true>(n, 1);
 #pragma unroll
-            for (int c = 0; c < 3; ++c) sm[(c * nrows + r) * SL + pos] = val[c];
+            for (int c = 0; c < 3; ++c) bufA[(3 * r + c) * SL + pos] = val[c];
         }
     }
     if (!demag) return;
     __syncthreads();
-    fft_dit<T, false, true>(sm, lLh, 3 * nrows, SL, 1, p.tw);
-    const int Kx = d.Kx;
-    const int tot2 = 3 * nrows * Kx;
-    for (int id = threadIdx.x; id < tot2; id += blockDim.x) {
-        const int q = id / Kx, k = id - q * Kx;
-        const int c = q / nrows, r = q - c * nrows;
-        const int row = row0 + r;
-        const int z = row / ny, y = row - z * ny;
-        const V2<T>* s = sm + q * SL;
+    const V2<T>* Z = stockham_fft<T, false, (sizeof(T) == 4 ? 4 : 3)>(bufA, bufB, lLh, nseq, SL, p.tw);
+    // split the half-length transform into X_k, k = 0..Lh, and store in the kx-blocked layout
+    const int z0 = row0 / ny, y0 = row0 - z0 * ny;       // rows of a tile span at most two planes
+    V2<T>* sp = p.spec + d.spec_off;
+    const int lT = d.lTy, TT = d.Ty;
+    const int plane = d.NBx * (d.Py << lT);               // elements of one (c, z) plane
+    const int tot2 = nseq << lLh;
+    for (int id = threadIdx.x; id < tot2 + nseq; id += blockDim.x) {
+        int q, k;
+        if (id < tot2) { q = id >> lLh; k = id & (Lh - 1); } else { q = id - tot2; k = Lh; }
+        const int r = q / 3, c = q - 3 * r;
+        int y = y0 + r, z = z0;
+        if (y >= ny) { y -= ny; ++z; }
+        const V2<T>* s = Z + q * SL;
         const V2<T> Zk = s[ix<true>(k & (Lh - 1), 1)];
         const V2<T> Zm = cconj(s[ix<true>((Lh - k) & (Lh - 1), 1)]);
         const V2<T> E = cscale(Zk + Zm, (T)0.5);
         const V2<T> Dd = Zk - Zm;
         const V2<T> O = mk<T>(Dd.y * (T)0.5, -Dd.x * (T)0.5);
-        p.spec[spec_index<T>(d, c, z, y, k)] = E + cmul(twid<T, false>(p.tw, k, d.lPx), O);
+        const int o = (c * d.nz + z) * plane + (((k >> lT) * d.Py + y) << lT) + (k & (TT - 1));
+        sp[o] = E + cmul(twid<T, false>(p.tw, k, d.lPx), O);
     }
 }
 
@@ -400,81 +410,73 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
     return r;
 }
 
-template <typename T>
-__device__ __forceinline__ T nb_ms(const PassParams<T>& p, const SimDesc& d, bool msarr, long long cell) {
-    return msarr ? p.Ms[d.ms_off + cell] : (T)1;
-}
-
-// Shared memory: 3*nrows sequences of Kx complex values, padded (pidx).
-template <typename T>
+// Shared memory: two buffers of 3*nrows padded sequences of Kx complex values.
+// ENERGY: energy accumulation (energy and NEB modes) instead of the RK reductions.
+template <typename T, bool ENERGY>
 __global__ void __launch_bounds__(MM_THREADS) k_xinv(PassParams<T> p, const T* __restrict__ ys) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    V2<T>* sm = reinterpret_cast<V2<T>*>(smraw);
     __shared__ unsigned long long red_u[MM_THREADS / 32];
     __shared__ double red_d[MM_THREADS / 32];
     const WorkItem w = p.items[blockIdx.x];
     if (sim_inactive(p, w.sim)) return;
     const SimDesc& d = p.desc[w.sim];
-    const int nx = d.nx, ny = d.ny, nz = d.nz, N = d.ncells;
+    const int nx = d.nx, ny = d.ny, nz = d.nz;
+    const long long N = d.ncells;
     const int lLh = d.lPx - 1, Lh = 1 << lLh, Kx = d.Kx;
     const int SK = padded_len(Kx);
     const int row0 = w.a, nrows = w.b;
-    const long long base = d.off - p.off_adjust;
+    const int nseq = 3 * nrows;
+    V2<T>* bufA = reinterpret_cast<V2<T>*>(smraw);
+    V2<T>* bufB = bufA + nseq * SK;
     const bool demag = (d.flags & F_DEMAG) != 0;
     const bool msarr = (d.flags & F_MSARR) != 0;
+    const int z0 = row0 / ny, y0 = row0 - z0 * ny;
+    const V2<T>* Hd = nullptr;
     if (demag) {
-        const int tot1 = 3 * nrows * Kx;
-        for (int id = threadIdx.x; id < tot1; id += blockDim.x) {
-            const int q = id / Kx, k = id - q * Kx;
-            const int c = q / nrows, r = q - c * nrows;
-            const int row = row0 + r;
-            const int z = row / ny, y = row - z * ny;
-            sm[q * SK + ix<true>(k, 1)] = p.spec[spec_index<T>(d, c, z, y, k)];
+        const V2<T>* sp = p.spec + d.spec_off;
+        const int lT = d.lTy, TT = d.Ty;
+        const int plane = d.NBx * (d.Py << lT);
+        const int tot1 = nseq << lLh;
+        for (int id = threadIdx.x; id < tot1 + nseq; id += blockDim.x) {
+            int q, k;
+            if (id < tot1) { q = id >> lLh; k = id & (Lh - 1); } else { q = id - tot1; k = Lh; }
+            const int r = q / 3, c = q - 3 * r;
+            int y = y0 + r, z = z0;
+            if (y >= ny) { y -= ny; ++z; }
+            const int o = (c * nz + z) * plane + (((k >> lT) * d.Py + y) << lT) + (k & (TT - 1));
+            bufA[q * SK + ix<true>(k, 1)] = sp[o];
         }
         __syncthreads();
         if (d.Py == 1 && d.Pz == 1) {            // x is the only transformed axis
             for (int id = threadIdx.x; id < nrows * Kx; id += blockDim.x) {
                 const int r = id / Kx, k = id - r * Kx;
                 const int pk = ix<true>(k, 1);
-                V2<T>* s0 = sm + (0 * nrows + r) * SK;
-                V2<T>* s1 = sm + (1 * nrows + r) * SK;
-                V2<T>* s2 = sm + (2 * nrows + r) * SK;
+                V2<T>* s0 = bufA + (3 * r + 0) * SK;
+                V2<T>* s1 = bufA + (3 * r + 1) * SK;
+                V2<T>* s2 = bufA + (3 * r + 2) * SK;
                 V2<T> a = s0[pk], b = s1[pk], c = s2[pk];
                 tensor_apply<T>(d, p.tensor, k, 0, 0, a, b, c);
                 s0[pk] = a; s1[pk] = b; s2[pk] = c;
             }
             __syncthreads();
         }
-        // Hermitian split: Z_k = (X_k + X*_{Lh-k}) + i W^{-k} (X_k - X*_{Lh-k}), k < Lh
-        const int hk = (Lh >> 1) + 1;
-        const int tot2 = 3 * nrows * hk;
-        for (int id = threadIdx.x; id < tot2; id += blockDim.x) {
-            const int q = id / hk, k = id - q * hk;
-            V2<T>* s = sm + q * SK;
-            if (k == 0) {
-                const V2<T> X0 = s[ix<true>(0, 1)], XL = cconj(s[ix<true>(Lh, 1)]);
-                const V2<T> e = X0 + XL, o = X0 - XL;
-                s[ix<true>(0, 1)] = mk<T>(e.x - o.y, e.y + o.x);
-            } else {
-                const int k2 = Lh - k;
-                const V2<T> Xa = s[ix<true>(k, 1)], Xb = s[ix<true>(k2, 1)];
-                const V2<T> ea = Xa + cconj(Xb);
-                const V2<T> ta = cmul(twid<T, true>(p.tw, k, d.lPx), Xa - cconj(Xb));
-                s[ix<true>(k, 1)] = mk<T>(ea.x - ta.y, ea.y + ta.x);
-                if (k2 != k) {
-                    const V2<T> eb = Xb + cconj(Xa);
-                    const V2<T> tb = cmul(twid<T, true>(p.tw, k2, d.lPx), Xb - cconj(Xa));
-                    s[ix<true>(k2, 1)] = mk<T>(eb.x - tb.y, eb.y + tb.x);
-                }
-            }
+        // Hermitian split into B: Z_k = (X_k + X*_{Lh-k}) + i W^{-k} (X_k - X*_{Lh-k}), k < Lh
+        for (int id = threadIdx.x; id < tot1; id += blockDim.x) {
+            const int q = id >> lLh, k = id & (Lh - 1);
+            const V2<T>* s = bufA + q * SK;
+            const V2<T> Xa = s[ix<true>(k, 1)], Xb = cconj(s[ix<true>(Lh - k, 1)]);
+            const V2<T> e = Xa + Xb;
+            const V2<T> t = cmul(twid<T, true>(p.tw, k, d.lPx), Xa - Xb);
+            bufB[q * SK + ix<true>(k, 1)] = mk<T>(e.x - t.y, e.y + t.x);
         }
         __syncthreads();
-        fft_dif<T, true, true>(sm, lLh, 3 * nrows, SK, 1, p.tw);
+        Hd = stockham_fft<T, true, (sizeof(T) == 4 ? 4 : 3)>(bufB, bufA, lLh, nseq, SK, p.tw);
     }
 
     // per-cell local fields and torque
     const T mu0 = (T)kMu0;
-    const T Dxx = (T)d.dx, Dyy = (T)d.dy, Dzz = (T)d.dz;
+    const T ex_x = (T)(1.0 / (d.dx * d.dx)), ex_y = (T)(1.0 / (d.dy * d.dy)), ex_z = (T)(1.0 / (d.dz * d.dz));
+    const T dm_x = (T)(1.0 / d.dx), dm_y = (T)(1.0 / d.dy);
     const T cA = (T)(2.0 * d.A), cD = (T)d.D, cK = (T)(2.0 * d.Ku), cC = (T)(4.0 * d.Kc);
     const T ux = (T)d.u[0], uy = (T)d.u[1], uz = (T)d.u[2];
     const T Hx0 = (T)d.H[0], Hy0 = (T)d.H[1], Hz0 = (T)d.H[2];
@@ -483,134 +485,132 @@ __global__ void __launch_bounds__(MM_THREADS) k_xinv(PassParams<T> p, const T* _
     const bool prec = (d.flags & F_PREC) != 0;
     const bool dmi = (d.flags & F_DMI) != 0 && d.D != 0.0;
     const bool do_ex = d.A != 0.0, do_uni = d.Ku != 0.0, do_cub = d.Kc != 0.0;
-    const bool energy = (p.mode == MODE_ENERGY || p.mode == MODE_NEB);
-    const bool write_k = (p.mode != MODE_ENERGY && p.mode != MODE_NEB);
-    const double V = d.dx * d.dy * d.dz;
+    const bool write_k = !ENERGY;
+    const int sy = nx, sz = nx * ny;
+    const long long tile = d.off - p.off_adjust + (long long)row0 * nx;
+    const T* __restrict__ m0p = ys + tile;
+    const T* __restrict__ m1p = m0p + N;
+    const T* __restrict__ m2p = m1p + N;
+    const T* __restrict__ msp = msarr ? p.Ms + d.ms_off + (long long)row0 * nx : nullptr;
     const double hstep = (p.mode == MODE_RK) ? p.state[w.sim].h : 0.0;
+    const double e7 = p.e[6];
+    const bool red1 = !ENERGY && p.mode == MODE_RK && p.stage == 1;
+    const bool red7 = !ENERGY && p.mode == MODE_RK && p.stage == 7;
     unsigned long long vmax = 0ull;
     double esum[6] = {0, 0, 0, 0, 0, 0};
-    const int tot = nrows * nx;
-    for (int id = threadIdx.x; id < tot; id += blockDim.x) {
-        const int r = id / nx, x = id - r * nx;
-        const int row = row0 + r;
-        const int z = row / ny, y = row - z * ny;
-        const long long cell = (long long)row * nx + x;
-        const T* mc = ys + base + cell;
-        const T m0 = mc[0], m1 = mc[N], m2 = mc[2 * (long long)N];
-        const T ms = msarr ? p.Ms[d.ms_off + cell] : (T)d.Ms;
-        T H0 = 0, H1 = 0, H2 = 0, k0 = 0, k1 = 0, k2 = 0;
-        if (ms > (T)0) {
-            const T inv = (T)1 / (mu0 * ms);
-            T hd0 = 0, hd1 = 0, hd2 = 0;
-            if (demag) {
-                const int pos = ix<true>(bitrev(x >> 1, lLh), 1);
-                const V2<T> v0 = sm[(0 * nrows + r) * SK + pos];
-                const V2<T> v1 = sm[(1 * nrows + r) * SK + pos];
-                const V2<T> v2 = sm[(2 * nrows + r) * SK + pos];
-                hd0 = (x & 1) ? v0.y : v0.x;
-                hd1 = (x & 1) ? v1.y : v1.x;
-                hd2 = (x & 1) ? v2.y : v2.x;
-            }
-            // exchange (Eq. 5) and interfacial DMI (Eq. 14), free boundaries
-            T ex0 = 0, ex1 = 0, ex2 = 0, dm0 = 0, dm1 = 0, dm2 = 0;
-            if (do_ex || dmi) {
-                const long long sx = 1, sy = nx, sz = (long long)nx * ny;
+    for (int r = 0; r < nrows; ++r) {
+        int y = y0 + r, z = z0;
+        if (y >= ny) { y -= ny; ++z; }
+        for (int x = threadIdx.x; x < nx; x += blockDim.x) {
+            const int cell = r * nx + x;                     // within the tile
+            const T m0 = m0p[cell], m1 = m1p[cell], m2 = m2p[cell];
+            const T ms = msarr ? msp[cell] : (T)d.Ms;
+            T H0 = 0, H1 = 0, H2 = 0, k0 = 0, k1 = 0, k2 = 0;
+            if (ms > (T)0) {
+                const T inv = (T)1 / (mu0 * ms);
+                T hd0 = 0, hd1 = 0, hd2 = 0;
+                if (demag) {
+                    const int pos = ix<true>(x >> 1, 1);
+                    const V2<T> v0 = Hd[(3 * r + 0) * SK + pos];
+                    const V2<T> v1 = Hd[(3 * r + 1) * SK + pos];
+                    const V2<T> v2 = Hd[(3 * r + 2) * SK + pos];
+                    hd0 = (x & 1) ? v0.y : v0.x;
+                    hd1 = (x & 1) ? v1.y : v1.x;
+                    hd2 = (x & 1) ? v2.y : v2.x;
+                }
+                // exchange (Eq. 5) and interfacial DMI (Eq. 14), free boundaries
+                T ex0 = 0, ex1 = 0, ex2 = 0, dm0 = 0, dm1 = 0, dm2 = 0;
+                if (do_ex || dmi) {
 #pragma unroll
-                for (int nb = 0; nb < 6; ++nb) {
-                    const int axis = nb >> 1;
-                    const int dir = (nb & 1) ? 1 : -1;
-                    bool ok;
-                    long long st;
-                    T Dl;
-                    if (axis == 0) { ok = dir < 0 ? x > 0 : x < nx - 1; st = sx; Dl = Dxx; }
-                    else if (axis == 1) { ok = dir < 0 ? y > 0 : y < ny - 1; st = sy; Dl = Dyy; }
-                    else { ok = dir < 0 ? z > 0 : z < nz - 1; st = sz; Dl = Dzz; }
-                    if (!ok) continue;
-                    const long long o = dir * st;
-                    if (msarr && !(nb_ms(p, d, msarr, cell + o) > (T)0)) continue;
-                    const T j0 = mc[o], j1 = mc[N + o], j2 = mc[2 * (long long)N + o];
-                    if (do_ex) {
-                        const T f = (T)1 / (Dl * Dl);
-                        ex0 += f * (j0 - m0); ex1 += f * (j1 - m1); ex2 += f * (j2 - m2);
-                    }
-                    if (dmi && axis < 2) {
-                        // sum_j e_ij x m_j / Delta: -x:-e_y, +x:+e_y, -y:+e_x, +y:-e_x
-                        const T f = (T)1 / Dl;
-                        if (axis == 0) {          // e_y x m = (mz, 0, -mx)
-                            const T s = (T)dir;
-                            dm0 += s * f * j2; dm2 -= s * f * j0;
-                        } else {                  // e_x x m = (0, -mz, my)
-                            const T s = (T)(-dir);
-                            dm1 -= s * f * j2; dm2 += s * f * j1;
+                    for (int nb = 0; nb < 6; ++nb) {
+                        const int axis = nb >> 1;
+                        const int dir = (nb & 1) ? 1 : -1;
+                        bool ok;
+                        int st;
+                        T fe, fd;
+                        if (axis == 0) { ok = dir < 0 ? x > 0 : x < nx - 1; st = 1; fe = ex_x; fd = dm_x; }
+                        else if (axis == 1) { ok = dir < 0 ? y > 0 : y < ny - 1; st = sy; fe = ex_y; fd = dm_y; }
+                        else { ok = dir < 0 ? z > 0 : z < nz - 1; st = sz; fe = ex_z; fd = (T)0; }
+                        if (!ok) continue;
+                        const int o = cell + dir * st;
+                        if (msarr && !(msp[o] > (T)0)) continue;
+                        const T j0 = m0p[o], j1 = m1p[o], j2 = m2p[o];
+                        if (do_ex) { ex0 += fe * (j0 - m0); ex1 += fe * (j1 - m1); ex2 += fe * (j2 - m2); }
+                        if (dmi && axis < 2) {
+                            // sum_j e_ij x m_j / Delta: -x:-e_y, +x:+e_y, -y:+e_x, +y:-e_x
+                            if (axis == 0) {          // e_y x m = (mz, 0, -mx)
+                                const T s = (T)dir * fd;
+                                dm0 += s * j2; dm2 -= s * j0;
+                            } else {                  // e_x x m = (0, -mz, my)
+                                const T s = (T)(-dir) * fd;
+                                dm1 -= s * j2; dm2 += s * j1;
+                            }
                         }
                     }
+                    ex0 *= cA * inv; ex1 *= cA * inv; ex2 *= cA * inv;
+                    dm0 *= -cD * inv; dm1 *= -cD * inv; dm2 *= -cD * inv;
                 }
-                ex0 *= cA * inv; ex1 *= cA * inv; ex2 *= cA * inv;
-                dm0 *= -cD * inv; dm1 *= -cD * inv; dm2 *= -cD * inv;
-            }
-            T un0 = 0, un1 = 0, un2 = 0, cu0 = 0, cu1 = 0, cu2 = 0;
-            if (do_uni) {
-                const T mu = m0 * ux + m1 * uy + m2 * uz;
-                const T f = cK * inv * mu;
-                un0 = f * ux; un1 = f * uy; un2 = f * uz;
-            }
-            if (do_cub) {
-                const T f = -cC * inv;
-                cu0 = f * m0 * m0 * m0; cu1 = f * m1 * m1 * m1; cu2 = f * m2 * m2 * m2;
-            }
-            H0 = hd0 + ex0 + dm0 + un0 + cu0 + Hx0;
-            H1 = hd1 + ex1 + dm1 + un1 + cu1 + Hy0;
-            H2 = hd2 + ex2 + dm2 + un2 + cu2 + Hz0;
-            if (energy) {
-                const double msV = (double)ms * V;
-                esum[0] += -0.5 * kMu0 * msV * ((double)m0 * ex0 + (double)m1 * ex1 + (double)m2 * ex2);
-                esum[1] += -0.5 * kMu0 * msV * ((double)m0 * dm0 + (double)m1 * dm1 + (double)m2 * dm2);
+                T un0 = 0, un1 = 0, un2 = 0, cu0 = 0, cu1 = 0, cu2 = 0;
                 if (do_uni) {
-                    const double mu = (double)m0 * d.u[0] + (double)m1 * d.u[1] + (double)m2 * d.u[2];
-                    esum[2] += -d.Ku * V * mu * mu;
+                    const T mu = m0 * ux + m1 * uy + m2 * uz;
+                    const T f = cK * inv * mu;
+                    un0 = f * ux; un1 = f * uy; un2 = f * uz;
                 }
                 if (do_cub) {
-                    const double a0 = m0, a1 = m1, a2 = m2;
-                    esum[3] += d.Kc * V * (a0 * a0 * a0 * a0 + a1 * a1 * a1 * a1 + a2 * a2 * a2 * a2);
+                    const T f = -cC * inv;
+                    cu0 = f * m0 * m0 * m0; cu1 = f * m1 * m1 * m1; cu2 = f * m2 * m2 * m2;
                 }
-                esum[4] += -kMu0 * msV * ((double)m0 * d.H[0] + (double)m1 * d.H[1] + (double)m2 * d.H[2]);
-                esum[5] += -0.5 * kMu0 * msV * ((double)m0 * hd0 + (double)m1 * hd1 + (double)m2 * hd2);
+                H0 = hd0 + ex0 + dm0 + un0 + cu0 + Hx0;
+                H1 = hd1 + ex1 + dm1 + un1 + cu1 + Hy0;
+                H2 = hd2 + ex2 + dm2 + un2 + cu2 + Hz0;
+                if (ENERGY) {
+                    const double V = d.dx * d.dy * d.dz;
+                    const double msV = (double)ms * V;
+                    esum[0] += -0.5 * kMu0 * msV * ((double)m0 * ex0 + (double)m1 * ex1 + (double)m2 * ex2);
+                    esum[1] += -0.5 * kMu0 * msV * ((double)m0 * dm0 + (double)m1 * dm1 + (double)m2 * dm2);
+                    if (do_uni) {
+                        const double mu = (double)m0 * d.u[0] + (double)m1 * d.u[1] + (double)m2 * d.u[2];
+                        esum[2] += -d.Ku * V * mu * mu;
+                    }
+                    if (do_cub) {
+                        const double a0 = m0, a1 = m1, a2 = m2;
+                        esum[3] += d.Kc * V * (a0 * a0 * a0 * a0 + a1 * a1 * a1 * a1 + a2 * a2 * a2 * a2);
+                    }
+                    esum[4] += -kMu0 * msV * ((double)m0 * d.H[0] + (double)m1 * d.H[1] + (double)m2 * d.H[2]);
+                    esum[5] += -0.5 * kMu0 * msV * ((double)m0 * hd0 + (double)m1 * hd1 + (double)m2 * hd2);
+                }
+                // LL form: dm/dt = -g~ m x H - alpha g~ m x (m x H)
+                const T c0 = m1 * H2 - m2 * H1, c1 = m2 * H0 - m0 * H2, c2 = m0 * H1 - m1 * H0;
+                const T dd0 = m1 * c2 - m2 * c1, dd1 = m2 * c0 - m0 * c2, dd2 = m0 * c1 - m1 * c0;
+                k0 = -agt * dd0; k1 = -agt * dd1; k2 = -agt * dd2;
+                if (prec) { k0 -= gt * c0; k1 -= gt * c1; k2 -= gt * c2; }
             }
-            // LL form: dm/dt = -g~ m x H - alpha g~ m x (m x H)
-            const T c0 = m1 * H2 - m2 * H1, c1 = m2 * H0 - m0 * H2, c2 = m0 * H1 - m1 * H0;
-            const T dd0 = m1 * c2 - m2 * c1, dd1 = m2 * c0 - m0 * c2, dd2 = m0 * c1 - m1 * c0;
-            k0 = -agt * dd0; k1 = -agt * dd1; k2 = -agt * dd2;
-            if (prec) { k0 -= gt * c0; k1 -= gt * c1; k2 -= gt * c2; }
-        }
-        const long long o = base + cell;
-        if (write_k) {
-            p.kout[o] = k0; p.kout[o + N] = k1; p.kout[o + 2 * (long long)N] = k2;
-        }
-        if (p.heff) {
-            p.heff[o] = H0; p.heff[o + N] = H1; p.heff[o + 2 * (long long)N] = H2;
-        }
-        if (p.mode == MODE_RK && p.stage == 1) {
-            const double v = sqrt((double)k0 * k0 + (double)k1 * k1 + (double)k2 * k2);
-            vmax = umax64(vmax, (unsigned long long)__double_as_longlong(v));
-        } else if (p.mode == MODE_RK && p.stage == 7) {
-            const double e7 = p.e[6];
-            const T* ep = p.errp + o;
-            const double v0 = fabs(hstep * ((double)ep[0] + e7 * k0));
-            const double v1 = fabs(hstep * ((double)ep[N] + e7 * k1));
-            const double v2 = fabs(hstep * ((double)ep[2 * (long long)N] + e7 * k2));
-            vmax = umax64(vmax, (unsigned long long)__double_as_longlong(v0));
-            vmax = umax64(vmax, (unsigned long long)__double_as_longlong(v1));
-            vmax = umax64(vmax, (unsigned long long)__double_as_longlong(v2));
+            const long long o = tile + cell;
+            if (write_k) {
+                p.kout[o] = k0; p.kout[o + N] = k1; p.kout[o + 2 * N] = k2;
+            }
+            if (p.heff) {
+                p.heff[o] = H0; p.heff[o + N] = H1; p.heff[o + 2 * N] = H2;
+            }
+            if (red1) {
+                const double v = sqrt((double)k0 * k0 + (double)k1 * k1 + (double)k2 * k2);
+                vmax = umax64(vmax, (unsigned long long)__double_as_longlong(v));
+            } else if (red7) {
+                const T* ep = p.errp + o;
+                const double v0 = fabs(hstep * ((double)ep[0] + e7 * k0));
+                const double v1 = fabs(hstep * ((double)ep[N] + e7 * k1));
+                const double v2 = fabs(hstep * ((double)ep[2 * N] + e7 * k2));
+                vmax = umax64(vmax, (unsigned long long)__double_as_longlong(v0));
+                vmax = umax64(vmax, (unsigned long long)__double_as_longlong(v1));
+                vmax = umax64(vmax, (unsigned long long)__double_as_longlong(v2));
+            }
         }
     }
-    if (p.mode == MODE_RK && (p.stage == 1 || p.stage == 7)) {
-        const unsigned long long r = block_max_u64(vmax, red_u);
-        if (threadIdx.x == 0) {
-            unsigned long long* dst = p.stage == 1 ? &p.state[w.sim].maxk_bits : &p.state[w.sim].err_bits;
-            atomicMax(dst, r);
-        }
+    if (red1 || red7) {
+        const unsigned long long rr = block_max_u64(vmax, red_u);
+        if (threadIdx.x == 0) atomicMax(red1 ? &p.state[w.sim].maxk_bits : &p.state[w.sim].err_bits, rr);
     }
-    if (energy) {
+    if (ENERGY) {
 #pragma unroll
         for (int t = 0; t < 6; ++t) {
             const double s = block_sum(esum[t], red_d);

@@ -33,7 +33,8 @@ inline int plan_pad_len(int n, bool min2) {
 constexpr int kMaxClusterPlanes = 8;
 
 // Fill the padded sizes, tensor bins and tile shapes of d from d.nx, d.ny, d.nz.
-//   Rx : rows per x-pass CTA, 3 * Rx * padded_len(Kx) <= 1536 complex values
+//   Rx : rows per x-pass CTA, 3 * Rx * padded_len(Kx) <= 4096 complex values per
+//        buffer (two buffers), Rx <= ny so a tile spans at most two planes
 //   Ty : kx block width (power of two, <= 32): Py * Ty <= 4096 (FP32) / 2048 (FP64)
 inline void plan_geometry(SimDesc& d, bool f32) {
     d.Px = plan_pad_len(d.nx, true);
@@ -47,7 +48,7 @@ inline void plan_geometry(SimDesc& d, bool f32) {
     d.Pzh = d.Pz / 2 + 1;
     d.ncomp = d.Pz > 1 ? 6 : 4;
     const int rows = d.ny * d.nz;
-    d.Rx = std::max(1, std::min(rows, 1536 / (3 * padded_len(d.Kx))));
+    d.Rx = std::max(1, std::min(std::min(rows, d.ny), 4096 / (3 * padded_len(d.Kx))));
     const int EB = f32 ? 4096 : 2048;
     const int kcap = std::min(32, 1 << plan_ilog2(d.Kx));
     d.Ty = std::min(kcap, plan_pow2floor(std::max(1, EB / d.Py)));
@@ -66,7 +67,7 @@ struct PlanItems {
 inline void plan_items(const SimDesc& d, int sid, size_t vsz, PlanItems& P) {
     const int rows = d.ny * d.nz;
     for (int r0 = 0; r0 < rows; r0 += d.Rx) P.x.push_back({sid, r0, std::min(d.Rx, rows - r0), 0});
-    P.smem_x = std::max(P.smem_x, 3 * (size_t)d.Rx * padded_len(d.Kx) * vsz);
+    P.smem_x = std::max(P.smem_x, 2 * 3 * (size_t)d.Rx * padded_len(d.Kx) * vsz);
     if (!(d.flags & F_DEMAG)) return;
     if (d.Pz > 1 && d.Py > 1 && d.nz <= kMaxClusterPlanes) {
         for (int b = 0; b < d.NBx; ++b) P.yzc[d.nz].push_back({sid, 0, b, 0});
