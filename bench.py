@@ -77,7 +77,7 @@ def pad(n, min2=False):
 def kernel_bytes(w, e):
     """Compulsory bytes per attempt of each kernel kind ('Roofline')."""
     out = {k: 0.0 for k in ("x_forward", "y_forward", "z_fused", "y_inverse", "y_fused",
-                            "x_inverse_epilogue", "project")}
+                            "x_inverse_epilogue", "project", "yz_cluster")}
     for s in w.sims:
         n = s.mesh.ncells
         nx, ny, nz = s.mesh.nx, s.mesh.ny, s.mesh.nz
@@ -93,7 +93,9 @@ def kernel_bytes(w, e):
             out["x_forward"] += 3 * e * n * st + (3 * e * n if st > 1 else 0) + (3 * e * n if st == 7 else 0)
             if demag:
                 out["x_forward"] += spec_rows
-                if Pz > 1:
+                if Pz > 1 and Py > 1 and nz <= 8:
+                    out["yz_cluster"] += 2 * spec_rows + tens
+                elif Pz > 1:
                     if Py > 1:
                         out["y_forward"] += spec_rows + spec_full
                         out["y_inverse"] += spec_full + spec_rows
@@ -258,21 +260,23 @@ def run_gpu(args, rank, world, dist):
     ms_max = float(t.item())
     value = world * ncell * 7 * args.steps / (ms_max / 1e3)
     # per-kernel durations inside the same step (events on the launching stream)
-    prof = ctx.profile_attempts(max(1, min(5, args.steps)))
     kb = kernel_bytes(w, e)
     hbm, peak_kind = peaks()
-    rows = {}
-    for k, (tms, cnt) in prof.items():
-        if cnt:
-            rows[k] = {"ms_per_attempt": tms / max(1, min(5, args.steps)), "launches": cnt,
-                       "achieved_gbs": (kb.get(k, 0.0) * max(1, min(5, args.steps))) / (tms / 1e3) / 1e9
-                       if k in kb and tms > 0 else None}
-    dom = max((k for k in rows if k in kb), key=lambda k: rows[k]["ms_per_attempt"])
     reps = max(1, min(5, args.steps))
-    launches_dom = prof[dom][1] / reps
-    avg_launch_ms = prof[dom][0] / prof[dom][1]
-    bytes_per_launch = kb[dom] / launches_dom
-    achieved = bytes_per_launch / (avg_launch_ms / 1e3) / 1e9
+    rows = {}
+    dom, achieved, bytes_per_launch, avg_launch_ms = None, None, None, None
+    if not w.neb:
+        prof = ctx.profile_attempts(reps)
+        for k, (tms, cnt) in prof.items():
+            if cnt:
+                rows[k] = {"ms_per_attempt": tms / reps, "launches": cnt,
+                           "achieved_gbs": (kb.get(k, 0.0) * reps) / (tms / 1e3) / 1e9
+                           if kb.get(k) and tms > 0 else None}
+        dom = max((k for k in rows if kb.get(k)), key=lambda k: rows[k]["ms_per_attempt"])
+        launches_dom = prof[dom][1] / reps
+        avg_launch_ms = prof[dom][0] / prof[dom][1]
+        bytes_per_launch = kb[dom] / launches_dom
+        achieved = bytes_per_launch / (avg_launch_ms / 1e3) / 1e9
     step_ms = ms_max / args.steps
     step_bytes = step_bytes_survey(w, e)
     # end to end through the C ABI with host buffers: H2D of m, one attempt, D2H of m
@@ -295,7 +299,7 @@ def run_gpu(args, rank, world, dist):
                    "l2": f"inputs larger than L2: working set ~{int(step_bytes / 7 / 1e6)} MB per RHS "
                          f"(state, 7 stage vectors, spectrum, tensor) vs 129 MB L2"},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "peak_kind": f"of {peak_kind}",
+                     "frac": achieved / hbm if achieved else None, "peak_kind": f"of {peak_kind}",
                      "bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_launch_ms, "traffic": None,
                      "step_algorithmic_gbs": step_bytes / (step_ms / 1e3) / 1e9,
                      "step_frac": step_bytes / (step_ms / 1e3) / 1e9 / hbm},

@@ -41,7 +41,15 @@ static void issue_passes(const Launch& L, PassParams<T> p, const T* ys, bool inc
     cudaStream_t s = L.stream;
     ProfileHook* hk = L.hook;
     p.items = L.x.dev;
-    k_xfwd<T><<<L.x.count, MM_THREADS, L.smem_x, s>>>(p);
+    switch (p.nk) {
+        case 0: k_xfwd<T, 0><<<L.x.count, MM_THREADS, L.smem_x, s>>>(p); break;
+        case 1: k_xfwd<T, 1><<<L.x.count, MM_THREADS, L.smem_x, s>>>(p); break;
+        case 2: k_xfwd<T, 2><<<L.x.count, MM_THREADS, L.smem_x, s>>>(p); break;
+        case 3: k_xfwd<T, 3><<<L.x.count, MM_THREADS, L.smem_x, s>>>(p); break;
+        case 4: k_xfwd<T, 4><<<L.x.count, MM_THREADS, L.smem_x, s>>>(p); break;
+        case 5: k_xfwd<T, 5><<<L.x.count, MM_THREADS, L.smem_x, s>>>(p); break;
+        default: k_xfwd<T, 6><<<L.x.count, MM_THREADS, L.smem_x, s>>>(p); break;
+    }
     if (hk) hk->mark(KIND_XFWD);
     long long n = 1;
     if (L.y13.count) {
@@ -194,7 +202,13 @@ void engine_neb_attempt(const Launch& L, const RkBuffers& B) {
 template <typename T>
 static void set_attrs() {
     const int mx = 227 * 1024;
-    cudaFuncSetAttribute(k_xfwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_xfwd<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_xfwd<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_xfwd<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_xfwd<T, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_xfwd<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_xfwd<T, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_xfwd<T, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     cudaFuncSetAttribute(k_xinv<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx - 4096);
     cudaFuncSetAttribute(k_xinv<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx - 4096);
     cudaFuncSetAttribute(k_ycol<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);

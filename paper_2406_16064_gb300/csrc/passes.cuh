@@ -77,7 +77,9 @@ __device__ __forceinline__ bool sim_inactive(const PassParams<T>& p, int sim) {
 // ---------------------------------------------------------------- x forward
 // Shared memory: two buffers of 3*nrows padded sequences (pidx) of Lh complex
 // values, sequence q = 3 r + c (row r of the tile, component c).
-template <typename T>
+// NK: number of stage vectors combined by the RK prologue (compile time, so
+// the prologue's loads unroll and overlap); p.nk must equal NK.
+template <typename T, int NK>
 __global__ void __launch_bounds__(MM_THREADS) k_xfwd(PassParams<T> p) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const WorkItem w = p.items[blockIdx.x];
@@ -110,9 +112,10 @@ __global__ void __launch_bounds__(MM_THREADS) k_xfwd(PassParams<T> p) {
                 T yv[3];
 #pragma unroll
                 for (int c = 0; c < 3; ++c) yv[c] = p.m[base + c * N + cell];
-                if (p.nk > 0) {
+                if (NK > 0) {
                     T acc[3] = {(T)0, (T)0, (T)0};
-                    for (int j = 0; j < p.nk; ++j) {
+#pragma unroll
+                    for (int j = 0; j < NK; ++j) {
                         if (p.a[j] != 0.0) {
                             const T aj = (T)p.a[j];
                             const T* kj = p.kvec[j] + base + cell;
@@ -126,8 +129,9 @@ __global__ void __launch_bounds__(MM_THREADS) k_xfwd(PassParams<T> p) {
 #pragma unroll
                         for (int c = 0; c < 3; ++c) p.ybuf[base + c * N + cell] = yv[c];
                     }
-                    if (p.stage == 7) {
+                    if (NK == 6 && p.stage == 7) {
                         T ev[3] = {(T)0, (T)0, (T)0};
+#pragma unroll
                         for (int j = 0; j < 6; ++j) {
                             if (p.e[j] != 0.0) {
                                 const T ej = (T)p.e[j];

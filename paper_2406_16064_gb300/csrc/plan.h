@@ -48,9 +48,12 @@ inline void plan_geometry(SimDesc& d, bool f32) {
     d.Pzh = d.Pz / 2 + 1;
     d.ncomp = d.Pz > 1 ? 6 : 4;
     const int rows = d.ny * d.nz;
-    d.Rx = std::max(1, std::min(std::min(rows, d.ny), 4096 / (3 * padded_len(d.Kx))));
+    // small meshes: keep at least ~rows/64 CTAs (one row each for <= 64 rows) so a
+    // lone small simulation still spreads over many SMs
+    const int rcap = std::max(1, (rows + 63) / 64);
+    d.Rx = std::max(1, std::min(std::min(std::min(rows, d.ny), rcap), 4096 / (3 * padded_len(d.Kx))));
     const int EB = f32 ? 4096 : 2048;
-    const int kcap = std::min(32, 1 << plan_ilog2(d.Kx));
+    const int kcap = std::min(32, std::max(1, plan_pow2floor(std::max(1, d.Kx / 8))));
     d.Ty = std::min(kcap, plan_pow2floor(std::max(1, EB / d.Py)));
     d.lTy = plan_ilog2(d.Ty);
     d.NBx = (d.Kx + d.Ty - 1) >> d.lTy;

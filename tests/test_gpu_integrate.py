@@ -144,6 +144,35 @@ def test_uneven_batch_relax_matches_per_sim_oracle():
         assert max_rel(ctx.get_m(i), m) < 1e-8
 
 
+def test_field_sweep_uneven_batch_matches_oracle():
+    """Listing-2 style sweep on an uneven batch: every simulation relaxes at each field
+    (max |dm/dt| < 1e-2 rad/ns) and ends where the oracle's own sweep ends."""
+    w = synth.uneven_batch(seed=7, count=3, precision="f64", choices=[(8, 8, 1), (6, 4, 2), (12, 6, 1)])
+    ctx = make_ctx("f64", w.sims)
+    ctx.set_m(np.concatenate([s.m0.ravel() for s in w.sims]))
+    ctx.reset_time()
+    offs, _ = ctx.layout()
+    sweep = (-100.0, 0.0, 100.0)
+    for H in sweep:
+        for i in range(len(w.sims)):
+            ctx.set_field(i, (0.0, 0.0, H * synth.MT))
+        ctx.relax(1e-6, max_dmdt=w.max_dmdt, max_steps=50000, sync_every=32)
+        for i in range(len(w.sims)):
+            assert ctx.status(i)["status"] == 2
+    mg = ctx.get_m(-1)
+    for i, s in enumerate(w.sims):
+        Ms = F.ms_array(s.mesh, s.mat)
+        Nt = D.mesh_tensor(s.mesh)
+        m = s.m0.copy()
+        for H in sweep:
+            mat = synth.Material(**{**s.mat.__dict__, "H": (0.0, 0.0, H * synth.MT)})
+            f = lambda y, mat=mat: F.rhs(s.mesh, mat, y, Ms, Nt, "direct")[0]
+            m, st = I.run(f, m, 1e-6, max_dmdt=w.max_dmdt, max_steps=50000)
+            assert st.last_maxdmdt < w.max_dmdt
+        n = 3 * s.mesh.ncells
+        assert np.abs(mg[offs[i]:offs[i] + n] - m.ravel()).max() < 1e-3, i
+
+
 def test_neb_single_cell_matches_closed_form_and_oracle():
     mesh = synth.Mesh(1, 1, 1, 3e-9, 3e-9, 3e-9)
     Ku, Ms0 = 5e5, 8e5
