@@ -125,6 +125,7 @@ Launch make_launch(mm_ctx* C, int sim) {
         else if (C->sims[sim].d.nz == nz) L.yzc[nz] = {C->yzci[nz] + C->yzcb[sim], C->yzcc[sim]};
     }
     L.smem_x = P.smem_x;
+    L.smem_xi = P.smem_xi;
     L.smem_y13 = P.smem_y13;
     L.smem_z = P.smem_z;
     L.smem_y2 = P.smem_y2;
@@ -167,7 +168,7 @@ int validate_items(mm_ctx* C) {
         const SimDesc& d = C->sims[w.sim].d;
         if (w.a < 0 || w.b < 1 || w.a + w.b > d.ny * d.nz) return fail(C, MM_EBOUNDS, "x item rows");
         if (2 * 3ULL * w.b * padded_len(d.Kx) * vsz > P.smem_x) return fail(C, MM_EBOUNDS, "x item smem");
-        if (w.b > d.ny) return fail(C, MM_EBOUNDS, "x item spans more than two planes");
+        if ((w.a % d.ny) + w.b > d.ny) return fail(C, MM_EBOUNDS, "x item crosses a plane");
         if (plan_spec_elems(d) >= (1LL << 31) || 3LL * d.ncells >= (1LL << 31))
             return fail(C, MM_EINVAL, "simulation too large for 32-bit per-simulation offsets");
     }
@@ -196,7 +197,8 @@ int validate_items(mm_ctx* C) {
         }
     }
     const size_t cap = 227 * 1024;
-    if (P.smem_x > cap - 4096 || P.smem_y13 > cap || P.smem_y2 > cap || P.smem_z > cap || P.smem_yzc > cap)
+    if (P.smem_x > cap - 4096 || P.smem_xi > cap - 4096 || P.smem_y13 > cap || P.smem_y2 > cap || P.smem_z > cap ||
+        P.smem_yzc > cap)
         return fail(C, MM_EINVAL, "a padded FFT length needs more shared memory than one CTA has");
     return MM_OK;
 }

@@ -41,7 +41,7 @@ struct Launch {
     int nsims = 0;
     ItemSet x, y13, z, y2;        // x rows, y fwd/inv (nz > 8), z fused, y fused (films)
     ItemSet yzc[9];               // cluster-fused y/z per plane count nz = 2..8
-    size_t smem_x = 0, smem_y13 = 0, smem_z = 0, smem_y2 = 0, smem_yzc = 0;
+    size_t smem_x = 0, smem_xi = 0, smem_y13 = 0, smem_z = 0, smem_y2 = 0, smem_yzc = 0;
     const void* tensor = nullptr;
     const void* Ms = nullptr;
     const void* tw = nullptr;

@@ -7,20 +7,6 @@
 
 namespace mm {
 
-// Dormand & Prince (1980) RK5(4)7M: a_{s,j} for stages 2..7 and the error
-// weights e_j = b_j - bhat_j.
-static const double kDP_A[7][6] = {
-    {0, 0, 0, 0, 0, 0},
-    {1.0 / 5, 0, 0, 0, 0, 0},
-    {3.0 / 40, 9.0 / 40, 0, 0, 0, 0},
-    {44.0 / 45, -56.0 / 15, 32.0 / 9, 0, 0, 0},
-    {19372.0 / 6561, -25360.0 / 2187, 64448.0 / 6561, -212.0 / 729, 0, 0},
-    {9017.0 / 3168, -355.0 / 33, 46732.0 / 5247, 49.0 / 176, -5103.0 / 18656, 0},
-    {35.0 / 384, 0, 500.0 / 1113, 125.0 / 192, -2187.0 / 6784, 11.0 / 84},
-};
-static const double kDP_E[7] = {71.0 / 57600, 0, -71.0 / 16695, 71.0 / 1920, -17253.0 / 339200, 22.0 / 525,
-                                -1.0 / 40};
-
 template <typename T>
 static PassParams<T> base_params(const Launch& L) {
     PassParams<T> p;
@@ -31,7 +17,7 @@ static PassParams<T> base_params(const Launch& L) {
     p.tensor = reinterpret_cast<const T*>(L.tensor);
     p.Ms = reinterpret_cast<const T*>(L.Ms);
     p.tw = reinterpret_cast<const V2<T>*>(L.tw);
-    for (int j = 0; j < 7; ++j) p.e[j] = kDP_E[j];
+    for (int j = 0; j < 7; ++j) p.e[j] = dp_e(j);
     return p;
 }
 
@@ -41,14 +27,14 @@ static void issue_passes(const Launch& L, PassParams<T> p, const T* ys, bool inc
     cudaStream_t s = L.stream;
     ProfileHook* hk = L.hook;
     p.items = L.x.dev;
-    switch (p.nk) {
-        case 0: k_xfwd<T, 0><<<L.x.count, MM_THREADS, L.smem_x, s>>>(p); break;
-        case 1: k_xfwd<T, 1><<<L.x.count, MM_THREADS, L.smem_x, s>>>(p); break;
+    switch ((p.mode == MODE_RK || p.mode == MODE_NEB) ? p.stage : 0) {
         case 2: k_xfwd<T, 2><<<L.x.count, MM_THREADS, L.smem_x, s>>>(p); break;
         case 3: k_xfwd<T, 3><<<L.x.count, MM_THREADS, L.smem_x, s>>>(p); break;
         case 4: k_xfwd<T, 4><<<L.x.count, MM_THREADS, L.smem_x, s>>>(p); break;
         case 5: k_xfwd<T, 5><<<L.x.count, MM_THREADS, L.smem_x, s>>>(p); break;
-        default: k_xfwd<T, 6><<<L.x.count, MM_THREADS, L.smem_x, s>>>(p); break;
+        case 6: k_xfwd<T, 6><<<L.x.count, MM_THREADS, L.smem_x, s>>>(p); break;
+        case 7: k_xfwd<T, 7><<<L.x.count, MM_THREADS, L.smem_x, s>>>(p); break;
+        default: k_xfwd<T, 0><<<L.x.count, MM_THREADS, L.smem_x, s>>>(p); break;
     }
     if (hk) hk->mark(KIND_XFWD);
     long long n = 1;
@@ -101,9 +87,9 @@ static void issue_passes(const Launch& L, PassParams<T> p, const T* ys, bool inc
     if (include_xinv) {
         p.items = L.x.dev;
         if (p.mode == MODE_ENERGY || p.mode == MODE_NEB)
-            k_xinv<T, true><<<L.x.count, MM_THREADS, L.smem_x, s>>>(p, ys);
+            k_xinv<T, true><<<L.x.count, MM_THREADS, L.smem_xi, s>>>(p, ys);
         else
-            k_xinv<T, false><<<L.x.count, MM_THREADS, L.smem_x, s>>>(p, ys);
+            k_xinv<T, false><<<L.x.count, MM_THREADS, L.smem_xi, s>>>(p, ys);
         if (hk) hk->mark(KIND_XINV);
         ++n;
     }
@@ -132,7 +118,7 @@ void engine_attempt(const Launch& L, const RkBuffers& B) {
         p.stage = st;
         p.nk = st - 1;
         p.write_y = st > 1;
-        for (int j = 0; j < 6; ++j) p.a[j] = kDP_A[st - 1][j];
+        for (int j = 0; j < 6; ++j) p.a[j] = dp_a(st, j);
         p.m = reinterpret_cast<const T*>(B.m);
         p.ybuf = reinterpret_cast<T*>(B.ybuf);
         p.kvec = reinterpret_cast<T* const*>(B.kvec_dev);
@@ -164,7 +150,7 @@ void engine_neb_attempt(const Launch& L, const RkBuffers& B) {
         p.stage = st;
         p.nk = st - 1;
         p.write_y = st > 1;
-        for (int j = 0; j < 6; ++j) p.a[j] = kDP_A[st - 1][j];
+        for (int j = 0; j < 6; ++j) p.a[j] = dp_a(st, j);
         p.m = reinterpret_cast<const T*>(B.m);
         p.ybuf = reinterpret_cast<T*>(B.ybuf);
         p.kvec = reinterpret_cast<T* const*>(B.kvec_dev);
@@ -184,7 +170,7 @@ void engine_neb_attempt(const Launch& L, const RkBuffers& B) {
         q.errp = reinterpret_cast<const T*>(B.errp);
         q.Ms = reinterpret_cast<const T*>(L.Ms);
         q.stage = st;
-        q.e7 = kDP_E[6];
+        q.e7 = dp_e(6);
         k_neb_tangent<T><<<L.x.count, MM_THREADS, 0, s>>>(q);
         k_neb_force<T><<<L.x.count, MM_THREADS, 0, s>>>(q);
         if (L.launches) *L.launches += 3;
@@ -203,12 +189,12 @@ template <typename T>
 static void set_attrs() {
     const int mx = 227 * 1024;
     cudaFuncSetAttribute(k_xfwd<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    cudaFuncSetAttribute(k_xfwd<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     cudaFuncSetAttribute(k_xfwd<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     cudaFuncSetAttribute(k_xfwd<T, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     cudaFuncSetAttribute(k_xfwd<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     cudaFuncSetAttribute(k_xfwd<T, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     cudaFuncSetAttribute(k_xfwd<T, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_xfwd<T, 7>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     cudaFuncSetAttribute(k_xinv<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx - 4096);
     cudaFuncSetAttribute(k_xinv<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx - 4096);
     cudaFuncSetAttribute(k_ycol<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);

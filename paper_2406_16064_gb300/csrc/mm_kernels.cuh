@@ -341,6 +341,26 @@ __device__ void fft_dif(V2<T>* buf, int logL, int nseq, int sstride, int estride
     }
 }
 
+// Dormand & Prince (1980) RK5(4)7M: a_{s,j} (stage s = 2..7, j = 0..s-2) and the
+// error weights e_j = b_j - bhat_j (j = 0..6).  constexpr so that stage kernels
+// fold them (and skip the zero ones) at compile time.
+__host__ __device__ constexpr double dp_a(int s, int j) {
+    return s == 2 ? (j == 0 ? 1.0 / 5 : 0.0)
+         : s == 3 ? (j == 0 ? 3.0 / 40 : j == 1 ? 9.0 / 40 : 0.0)
+         : s == 4 ? (j == 0 ? 44.0 / 45 : j == 1 ? -56.0 / 15 : j == 2 ? 32.0 / 9 : 0.0)
+         : s == 5 ? (j == 0 ? 19372.0 / 6561 : j == 1 ? -25360.0 / 2187 : j == 2 ? 64448.0 / 6561
+                    : j == 3 ? -212.0 / 729 : 0.0)
+         : s == 6 ? (j == 0 ? 9017.0 / 3168 : j == 1 ? -355.0 / 33 : j == 2 ? 46732.0 / 5247
+                    : j == 3 ? 49.0 / 176 : j == 4 ? -5103.0 / 18656 : 0.0)
+         : s == 7 ? (j == 0 ? 35.0 / 384 : j == 1 ? 0.0 : j == 2 ? 500.0 / 1113 : j == 3 ? 125.0 / 192
+                    : j == 4 ? -2187.0 / 6784 : j == 5 ? 11.0 / 84 : 0.0)
+         : 0.0;
+}
+__host__ __device__ constexpr double dp_e(int j) {
+    return j == 0 ? 71.0 / 57600 : j == 1 ? 0.0 : j == 2 ? -71.0 / 16695 : j == 3 ? 71.0 / 1920
+         : j == 4 ? -17253.0 / 339200 : j == 5 ? 22.0 / 525 : j == 6 ? -1.0 / 40 : 0.0;
+}
+
 // Parameters of every pass kernel (passed by value).
 enum { MODE_RHS = 0, MODE_RK = 1, MODE_ENERGY = 2, MODE_NEB = 3 };
 

@@ -77,9 +77,10 @@ __device__ __forceinline__ bool sim_inactive(const PassParams<T>& p, int sim) {
 // ---------------------------------------------------------------- x forward
 // Shared memory: two buffers of 3*nrows padded sequences (pidx) of Lh complex
 // values, sequence q = 3 r + c (row r of the tile, component c).
-// NK: number of stage vectors combined by the RK prologue (compile time, so
-// the prologue's loads unroll and overlap); p.nk must equal NK.
-template <typename T, int NK>
+// S: Dormand-Prince stage of the RK prologue (2..7), or 0 for none (stage 1
+// and the non-RK modes).  The stage's coefficients are compile-time
+// constants, so zero ones vanish and the stage vectors' loads issue together.
+template <typename T, int S>
 __global__ void __launch_bounds__(MM_THREADS) k_xfwd(PassParams<T> p) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const WorkItem w = p.items[blockIdx.x];
@@ -112,12 +113,12 @@ __global__ void __launch_bounds__(MM_THREADS) k_xfwd(PassParams<T> p) {
                 T yv[3];
 #pragma unroll
                 for (int c = 0; c < 3; ++c) yv[c] = p.m[base + c * N + cell];
-                if (NK > 0) {
+                if (S >= 2) {
                     T acc[3] = {(T)0, (T)0, (T)0};
 #pragma unroll
-                    for (int j = 0; j < NK; ++j) {
-                        if (p.a[j] != 0.0) {
-                            const T aj = (T)p.a[j];
+                    for (int j = 0; j < S - 1; ++j) {
+                        if (dp_a(S, j) != 0.0) {
+                            const T aj = (T)dp_a(S, j);
                             const T* kj = p.kvec[j] + base + cell;
 #pragma unroll
                             for (int c = 0; c < 3; ++c) acc[c] += aj * kj[c * N];
@@ -125,16 +126,14 @@ __global__ void __launch_bounds__(MM_THREADS) k_xfwd(PassParams<T> p) {
                     }
 #pragma unroll
                     for (int c = 0; c < 3; ++c) yv[c] += hstep * acc[c];
-                    if (p.write_y) {
 #pragma unroll
-                        for (int c = 0; c < 3; ++c) p.ybuf[base + c * N + cell] = yv[c];
-                    }
-                    if (NK == 6 && p.stage == 7) {
+                    for (int c = 0; c < 3; ++c) p.ybuf[base + c * N + cell] = yv[c];
+                    if (S == 7) {
                         T ev[3] = {(T)0, (T)0, (T)0};
 #pragma unroll
                         for (int j = 0; j < 6; ++j) {
-                            if (p.e[j] != 0.0) {
-                                const T ej = (T)p.e[j];
+                            if (dp_e(j) != 0.0) {
+                                const T ej = (T)dp_e(j);
                                 const T* kj = p.kvec[j] + base + cell;
 #pragma unroll
                                 for (int c = 0; c < 3; ++c) ev[c] += ej * kj[c * N];
@@ -163,7 +162,7 @@ __global__ void __launch_bounds__(MM_THREADS) k_xfwd(PassParams<T> p) {
     __syncthreads();
     const V2<T>* Z = stockham_fft<T, false, (sizeof(T) == 4 ? 4 : 3)>(bufA, bufB, lLh, nseq, SL, p.tw);
     // split the half-length transform into X_k, k = 0..Lh, and store in the kx-blocked layout
-    const int z0 = row0 / ny, y0 = row0 - z0 * ny;       // rows of a tile span at most two planes
+    const int z0 = row0 / ny, y0 = row0 - z0 * ny;       // a tile never crosses a plane
     V2<T>* sp = p.spec + d.spec_off;
     const int lT = d.lTy, TT = d.Ty;
     const int plane = d.NBx * (d.Py << lT);               // elements of one (c, z) plane
@@ -172,8 +171,7 @@ __global__ void __launch_bounds__(MM_THREADS) k_xfwd(PassParams<T> p) {
         int q, k;
         if (id < tot2) { q = id >> lLh; k = id & (Lh - 1); } else { q = id - tot2; k = Lh; }
         const int r = q / 3, c = q - 3 * r;
-        int y = y0 + r, z = z0;
-        if (y >= ny) { y -= ny; ++z; }
+        const int y = y0 + r, z = z0;
         const V2<T>* s = Z + q * SL;
         const V2<T> Zk = s[ix<true>(k & (Lh - 1), 1)];
         const V2<T> Zm = cconj(s[ix<true>((Lh - k) & (Lh - 1), 1)]);
@@ -207,13 +205,25 @@ __global__ void __launch_bounds__(MM_THREADS) k_ycol(PassParams<T> p) {
 #pragma unroll
     for (int cc = 0; cc < NC; ++cc) gb[cc] = spec_block<T>(d, c0 + cc, z, b);
     const int nload = (YMODE == 1) ? L : ny;
+    for (int b0 = threadIdx.x; b0 < (L << lT); b0 += 4 * blockDim.x) {   // 4 NC loads in flight
+        V2<T> v[NC][4];
 #pragma unroll
-    for (int cc = 0; cc < NC; ++cc) {
-        for (int id = threadIdx.x; id < (L << lT); id += blockDim.x) {
-            const int col = id & (TT - 1), y = id >> lT;
-            const V2<T> v = y < nload ? p.spec[gb[cc] + id] : mk<T>((T)0, (T)0);
-            const int pos = (YMODE == 1) ? y : bitrev(y, lL);
-            sm[pos * es + cc * TT + col] = v;
+        for (int u = 0; u < 4; ++u) {
+            const int id = b0 + u * blockDim.x;
+            const int y = id >> lT;
+#pragma unroll
+            for (int cc = 0; cc < NC; ++cc)
+                v[cc][u] = (id < (L << lT) && y < nload) ? p.spec[gb[cc] + id] : mk<T>((T)0, (T)0);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int id = b0 + u * blockDim.x;
+            if (id < (L << lT)) {
+                const int col = id & (TT - 1), y = id >> lT;
+                const int pos = (YMODE == 1) ? y : bitrev(y, lL);
+#pragma unroll
+                for (int cc = 0; cc < NC; ++cc) sm[pos * es + cc * TT + col] = v[cc][u];
+            }
         }
     }
     __syncthreads();
@@ -260,14 +270,29 @@ __global__ void __launch_bounds__(MM_THREADS) k_zcol(PassParams<T> p) {
     const int ncols = min(TT, d.Kx - kx0);
     const int es = 3 * TT;                      // layout [z][c][col]
     const int tot = (L * 3) << lT;
-    for (int id = threadIdx.x; id < tot; id += blockDim.x) {
-        const int col = id & (TT - 1);
-        const int rest = id >> lT;
-        const int c = rest % 3;
-        const int z = rest / 3;
-        V2<T> v = mk<T>((T)0, (T)0);
-        if (z < nz) v = p.spec[spec_block<T>(d, c, z, b) + ((long long)ky << lT) + col];
-        sm[bitrev(z, lL) * es + c * TT + col] = v;
+    for (int b0 = threadIdx.x; b0 < tot; b0 += 4 * blockDim.x) {   // four loads in flight
+        V2<T> v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int id = b0 + u * blockDim.x;
+            const int col = id & (TT - 1);
+            const int rest = id >> lT;
+            const int c = rest % 3;
+            const int z = rest / 3;
+            v[u] = (id < tot && z < nz) ? p.spec[spec_block<T>(d, c, z, b) + ((long long)ky << lT) + col]
+                                        : mk<T>((T)0, (T)0);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int id = b0 + u * blockDim.x;
+            if (id < tot) {
+                const int col = id & (TT - 1);
+                const int rest = id >> lT;
+                const int c = rest % 3;
+                const int z = rest / 3;
+                sm[bitrev(z, lL) * es + c * TT + col] = v[u];
+            }
+        }
     }
     __syncthreads();
     fft_dit<T, false>(sm, lL, es, 1, es, p.tw);
@@ -355,12 +380,24 @@ __global__ void __launch_bounds__(MM_THREADS, sizeof(T) == 4 ? 2 : 1) k_yzc(Pass
     long long gb[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) gb[c] = spec_block<T>(d, c, z, b);
+    for (int b0 = threadIdx.x; b0 < (L << lT); b0 += 4 * blockDim.x) {   // 12 loads in flight
+        V2<T> v[3][4];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        for (int id = threadIdx.x; id < (L << lT); id += blockDim.x) {
-            const int col = id & (TT - 1), y = id >> lT;
-            const V2<T> v = y < ny ? p.spec[gb[c] + id] : mk<T>((T)0, (T)0);
-            sm[bitrev(y, lL) * es + c * TT + col] = v;
+        for (int u = 0; u < 4; ++u) {
+            const int id = b0 + u * blockDim.x;
+            const int y = id >> lT;
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                v[c][u] = (id < (L << lT) && y < ny) ? p.spec[gb[c] + id] : mk<T>((T)0, (T)0);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int id = b0 + u * blockDim.x;
+            if (id < (L << lT)) {
+                const int col = id & (TT - 1), y = id >> lT;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) sm[bitrev(y, lL) * es + c * TT + col] = v[c][u];
+            }
         }
     }
     __syncthreads();
@@ -417,7 +454,7 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 // Shared memory: two buffers of 3*nrows padded sequences of Kx complex values.
 // ENERGY: energy accumulation (energy and NEB modes) instead of the RK reductions.
 template <typename T, bool ENERGY>
-__global__ void __launch_bounds__(MM_THREADS) k_xinv(PassParams<T> p, const T* __restrict__ ys) {
+__global__ void __launch_bounds__(MM_THREADS, sizeof(T) == 4 ? 4 : 2) k_xinv(PassParams<T> p, const T* __restrict__ ys) {
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ unsigned long long red_u[MM_THREADS / 32];
     __shared__ double red_d[MM_THREADS / 32];
@@ -434,21 +471,34 @@ __global__ void __launch_bounds__(MM_THREADS) k_xinv(PassParams<T> p, const T* _
     V2<T>* bufB = bufA + nseq * SK;
     const bool demag = (d.flags & F_DEMAG) != 0;
     const bool msarr = (d.flags & F_MSARR) != 0;
-    const int z0 = row0 / ny, y0 = row0 - z0 * ny;
+    const int z0 = row0 / ny, y0 = row0 - z0 * ny;      // a tile never crosses a plane
+    const long long tile = d.off - p.off_adjust + (long long)row0 * nx;
     const V2<T>* Hd = nullptr;
     if (demag) {
         const V2<T>* sp = p.spec + d.spec_off;
         const int lT = d.lTy, TT = d.Ty;
         const int plane = d.NBx * (d.Py << lT);
         const int tot1 = nseq << lLh;
-        for (int id = threadIdx.x; id < tot1 + nseq; id += blockDim.x) {
-            int q, k;
-            if (id < tot1) { q = id >> lLh; k = id & (Lh - 1); } else { q = id - tot1; k = Lh; }
-            const int r = q / 3, c = q - 3 * r;
-            int y = y0 + r, z = z0;
-            if (y >= ny) { y -= ny; ++z; }
-            const int o = (c * nz + z) * plane + (((k >> lT) * d.Py + y) << lT) + (k & (TT - 1));
-            bufA[q * SK + ix<true>(k, 1)] = sp[o];
+        // four loads in flight per thread before their shared-memory stores
+        for (int b0 = threadIdx.x; b0 < tot1 + nseq; b0 += 4 * blockDim.x) {
+            V2<T> v[4];
+            int dst[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int id = b0 + u * blockDim.x;
+                dst[u] = -1;
+                if (id < tot1 + nseq) {
+                    int q, k;
+                    if (id < tot1) { q = id >> lLh; k = id & (Lh - 1); } else { q = id - tot1; k = Lh; }
+                    const int r = q / 3, c = q - 3 * r;
+                    const int o = (c * nz + z0) * plane + (((k >> lT) * d.Py + y0 + r) << lT) + (k & (TT - 1));
+                    v[u] = sp[o];
+                    dst[u] = q * SK + ix<true>(k, 1);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (dst[u] >= 0) bufA[dst[u]] = v[u];
         }
         __syncthreads();
         if (d.Py == 1 && d.Pz == 1) {            // x is the only transformed axis
@@ -490,11 +540,10 @@ __global__ void __launch_bounds__(MM_THREADS) k_xinv(PassParams<T> p, const T* _
     const bool dmi = (d.flags & F_DMI) != 0 && d.D != 0.0;
     const bool do_ex = d.A != 0.0, do_uni = d.Ku != 0.0, do_cub = d.Kc != 0.0;
     const bool write_k = !ENERGY;
-    const int sy = nx, sz = nx * ny;
-    const long long tile = d.off - p.off_adjust + (long long)row0 * nx;
     const T* __restrict__ m0p = ys + tile;
     const T* __restrict__ m1p = m0p + N;
     const T* __restrict__ m2p = m1p + N;
+    const int sz = nx * ny;
     const T* __restrict__ msp = msarr ? p.Ms + d.ms_off + (long long)row0 * nx : nullptr;
     const double hstep = (p.mode == MODE_RK) ? p.state[w.sim].h : 0.0;
     const double e7 = p.e[6];
@@ -503,8 +552,7 @@ __global__ void __launch_bounds__(MM_THREADS) k_xinv(PassParams<T> p, const T* _
     unsigned long long vmax = 0ull;
     double esum[6] = {0, 0, 0, 0, 0, 0};
     for (int r = 0; r < nrows; ++r) {
-        int y = y0 + r, z = z0;
-        if (y >= ny) { y -= ny; ++z; }
+        const int y = y0 + r, z = z0;
         for (int x = threadIdx.x; x < nx; x += blockDim.x) {
             const int cell = r * nx + x;                     // within the tile
             const T m0 = m0p[cell], m1 = m1p[cell], m2 = m2p[cell];
@@ -533,7 +581,7 @@ __global__ void __launch_bounds__(MM_THREADS) k_xinv(PassParams<T> p, const T* _
                         int st;
                         T fe, fd;
                         if (axis == 0) { ok = dir < 0 ? x > 0 : x < nx - 1; st = 1; fe = ex_x; fd = dm_x; }
-                        else if (axis == 1) { ok = dir < 0 ? y > 0 : y < ny - 1; st = sy; fe = ex_y; fd = dm_y; }
+                        else if (axis == 1) { ok = dir < 0 ? y > 0 : y < ny - 1; st = nx; fe = ex_y; fd = dm_y; }
                         else { ok = dir < 0 ? z > 0 : z < nz - 1; st = sz; fe = ex_z; fd = (T)0; }
                         if (!ok) continue;
                         const int o = cell + dir * st;

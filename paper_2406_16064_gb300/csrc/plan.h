@@ -34,7 +34,7 @@ constexpr int kMaxClusterPlanes = 8;
 
 // Fill the padded sizes, tensor bins and tile shapes of d from d.nx, d.ny, d.nz.
 //   Rx : rows per x-pass CTA, 3 * Rx * padded_len(Kx) <= 4096 complex values per
-//        buffer (two buffers), Rx <= ny so a tile spans at most two planes
+//        buffer (two buffers), Rx <= ny; tiles never cross a plane
 //   Ty : kx block width (power of two, <= 32): Py * Ty <= 4096 (FP32) / 2048 (FP64)
 inline void plan_geometry(SimDesc& d, bool f32) {
     d.Px = plan_pad_len(d.nx, true);
@@ -61,16 +61,23 @@ inline void plan_geometry(SimDesc& d, bool f32) {
 
 inline long long plan_spec_elems(const SimDesc& d) { return 3LL * d.nz * d.NBx * d.Py * d.Ty; }
 
+// x-inverse shared memory: two FFT buffers of 3*Rx padded rows.
+inline size_t plan_xinv_smem(const SimDesc& d, size_t vsz) {
+    return 2 * 3 * (size_t)d.Rx * padded_len(d.Kx) * vsz;
+}
+
 struct PlanItems {
     std::vector<WorkItem> x, y13, z, y2, yzc[kMaxClusterPlanes + 1];
-    size_t smem_x = 0, smem_y13 = 0, smem_z = 0, smem_y2 = 0, smem_yzc = 0;
+    size_t smem_x = 0, smem_xi = 0, smem_y13 = 0, smem_z = 0, smem_y2 = 0, smem_yzc = 0;
 };
 
 // Append the work items of simulation sid; vsz = bytes of one complex value.
 inline void plan_items(const SimDesc& d, int sid, size_t vsz, PlanItems& P) {
-    const int rows = d.ny * d.nz;
-    for (int r0 = 0; r0 < rows; r0 += d.Rx) P.x.push_back({sid, r0, std::min(d.Rx, rows - r0), 0});
+    // x tiles: Rx consecutive rows of one plane (never crossing a plane)
+    for (int z = 0; z < d.nz; ++z)
+        for (int y0 = 0; y0 < d.ny; y0 += d.Rx) P.x.push_back({sid, z * d.ny + y0, std::min(d.Rx, d.ny - y0), 0});
     P.smem_x = std::max(P.smem_x, 2 * 3 * (size_t)d.Rx * padded_len(d.Kx) * vsz);
+    P.smem_xi = std::max(P.smem_xi, plan_xinv_smem(d, vsz));
     if (!(d.flags & F_DEMAG)) return;
     if (d.Pz > 1 && d.Py > 1 && d.nz <= kMaxClusterPlanes) {
         for (int b = 0; b < d.NBx; ++b) P.yzc[d.nz].push_back({sid, 0, b, 0});

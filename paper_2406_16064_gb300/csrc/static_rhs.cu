@@ -116,7 +116,8 @@ extern "C" int mm_rhs_eval_static(const mm_mesh* mesh, const mm_material* mat, i
     plan_items(d, 0, vsz, P);
     const std::vector<WorkItem>& yzv = P.yzc[std::min(d.nz, kMaxClusterPlanes)];
     const size_t cap = 227 * 1024;
-    if (P.smem_x > cap - 4096 || P.smem_y13 > cap || P.smem_y2 > cap || P.smem_z > cap || P.smem_yzc > cap)
+    if (P.smem_x > cap - 4096 || P.smem_xi > cap - 4096 || P.smem_y13 > cap || P.smem_y2 > cap ||
+        P.smem_z > cap || P.smem_yzc > cap)
         return err(MM_EINVAL, "mm_rhs_eval_static: FFT tile exceeds shared memory");
 
     // carve the static array
@@ -195,6 +196,7 @@ extern "C" int mm_rhs_eval_static(const mm_mesh* mesh, const mm_material* mat, i
     L.y2 = {(const WorkItem*)(base + o_y2), (int)P.y2.size()};
     if (!yzv.empty()) L.yzc[d.nz] = {(const WorkItem*)(base + o_yz), (int)yzv.size()};
     L.smem_x = P.smem_x;
+    L.smem_xi = P.smem_xi;
     L.smem_y13 = P.smem_y13;
     L.smem_z = P.smem_z;
     L.smem_y2 = P.smem_y2;
