@@ -346,8 +346,27 @@ __device__ void yzc_zstep(const PassParams<T>& p, const SimDesc& d, V2<T>* const
         }
 #pragma unroll
         for (int c = 0; c < 3; ++c) reg_fft<T, PZ, false>(X[c], p.tw);
+        {
+            // H = T M per kz; the ky fold is hoisted, the kz fold is compile time
+            const bool fy = ky > (Py >> 1);
+            const int kyh = fy ? Py - ky : ky;
+            const T sy = fy ? (T)-1 : (T)1;
+            const long long PS = (long long)d.Pyh * d.Kx;            // kz-plane stride
+            const long long CS = (long long)d.Pzh * PS;              // component stride
+            const T* tb = p.tensor + d.tens_off + (long long)kyh * d.Kx + kx0 + col;
 #pragma unroll
-        for (int kz = 0; kz < PZ; ++kz) tensor_apply<T>(d, p.tensor, kx0 + col, ky, kz, X[0][kz], X[1][kz], X[2][kz]);
+            for (int kz = 0; kz < PZ; ++kz) {
+                const int kzh = kz <= PZ / 2 ? kz : PZ - kz;
+                const T sz = kz <= PZ / 2 ? (T)1 : (T)-1;
+                const T* t = tb + kzh * PS;
+                const T xx = t[0], yy = t[CS], zz = t[2 * CS];
+                const T xy = sy * t[3 * CS], xz = sz * t[4 * CS], yz = sy * sz * t[5 * CS];
+                const V2<T> a = X[0][kz], b = X[1][kz], c = X[2][kz];
+                X[0][kz] = mk<T>(xx * a.x + xy * b.x + xz * c.x, xx * a.y + xy * b.y + xz * c.y);
+                X[1][kz] = mk<T>(xy * a.x + yy * b.x + yz * c.x, xy * a.y + yy * b.y + yz * c.y);
+                X[2][kz] = mk<T>(xz * a.x + yz * b.x + zz * c.x, xz * a.y + yz * b.y + zz * c.y);
+            }
+        }
 #pragma unroll
         for (int c = 0; c < 3; ++c) reg_fft<T, PZ, true>(X[c], p.tw);
 #pragma unroll
@@ -570,37 +589,42 @@ __global__ void __launch_bounds__(MM_THREADS, sizeof(T) == 4 ? 4 : 2) k_xinv(Pas
                     hd1 = (x & 1) ? v1.y : v1.x;
                     hd2 = (x & 1) ? v2.y : v2.x;
                 }
-                // exchange (Eq. 5) and interfacial DMI (Eq. 14), free boundaries
+                // exchange (Eq. 5) and interfacial DMI (Eq. 14), free boundaries.  The six
+                // neighbours are loaded unconditionally (a missing one reads the cell
+                // itself) and masked afterwards, so all loads can be in flight together.
                 T ex0 = 0, ex1 = 0, ex2 = 0, dm0 = 0, dm1 = 0, dm2 = 0;
                 if (do_ex || dmi) {
+                    bool ok[6] = {x > 0, x < nx - 1, y > 0, y < ny - 1, z > 0, z < nz - 1};
+                    const int off[6] = {-1, 1, -nx, nx, -sz, sz};
+                    T j0[6], j1[6], j2[6];
 #pragma unroll
                     for (int nb = 0; nb < 6; ++nb) {
-                        const int axis = nb >> 1;
-                        const int dir = (nb & 1) ? 1 : -1;
-                        bool ok;
-                        int st;
-                        T fe, fd;
-                        if (axis == 0) { ok = dir < 0 ? x > 0 : x < nx - 1; st = 1; fe = ex_x; fd = dm_x; }
-                        else if (axis == 1) { ok = dir < 0 ? y > 0 : y < ny - 1; st = nx; fe = ex_y; fd = dm_y; }
-                        else { ok = dir < 0 ? z > 0 : z < nz - 1; st = sz; fe = ex_z; fd = (T)0; }
-                        if (!ok) continue;
-                        const int o = cell + dir * st;
-                        if (msarr && !(msp[o] > (T)0)) continue;
-                        const T j0 = m0p[o], j1 = m1p[o], j2 = m2p[o];
-                        if (do_ex) { ex0 += fe * (j0 - m0); ex1 += fe * (j1 - m1); ex2 += fe * (j2 - m2); }
-                        if (dmi && axis < 2) {
-                            // sum_j e_ij x m_j / Delta: -x:-e_y, +x:+e_y, -y:+e_x, +y:-e_x
-                            if (axis == 0) {          // e_y x m = (mz, 0, -mx)
-                                const T s = (T)dir * fd;
-                                dm0 += s * j2; dm2 -= s * j0;
-                            } else {                  // e_x x m = (0, -mz, my)
-                                const T s = (T)(-dir) * fd;
-                                dm1 -= s * j2; dm2 += s * j1;
-                            }
-                        }
+                        const int o = cell + (ok[nb] ? off[nb] : 0);
+                        j0[nb] = m0p[o]; j1[nb] = m1p[o]; j2[nb] = m2p[o];
                     }
-                    ex0 *= cA * inv; ex1 *= cA * inv; ex2 *= cA * inv;
-                    dm0 *= -cD * inv; dm1 *= -cD * inv; dm2 *= -cD * inv;
+                    if (msarr) {
+#pragma unroll
+                        for (int nb = 0; nb < 6; ++nb) ok[nb] = ok[nb] && msp[cell + (ok[nb] ? off[nb] : 0)] > (T)0;
+                    }
+                    if (do_ex) {
+                        const T fe[6] = {ex_x, ex_x, ex_y, ex_y, ex_z, ex_z};
+#pragma unroll
+                        for (int nb = 0; nb < 6; ++nb) {
+                            const T f = ok[nb] ? fe[nb] : (T)0;
+                            ex0 += f * (j0[nb] - m0); ex1 += f * (j1[nb] - m1); ex2 += f * (j2[nb] - m2);
+                        }
+                        ex0 *= cA * inv; ex1 *= cA * inv; ex2 *= cA * inv;
+                    }
+                    if (dmi) {
+                        // sum_j e_ij x m_j / Delta: -x:-e_y, +x:+e_y, -y:+e_x, +y:-e_x;
+                        // e_y x m = (mz, 0, -mx), e_x x m = (0, -mz, my)
+                        const T sxm = ok[0] ? -dm_x : (T)0, sxp = ok[1] ? dm_x : (T)0;
+                        const T sym = ok[2] ? dm_y : (T)0, syp = ok[3] ? -dm_y : (T)0;
+                        dm0 = sxm * j2[0] + sxp * j2[1];
+                        dm2 = -(sxm * j0[0] + sxp * j0[1]) + sym * j1[2] + syp * j1[3];
+                        dm1 = -(sym * j2[2] + syp * j2[3]);
+                        dm0 *= -cD * inv; dm1 *= -cD * inv; dm2 *= -cD * inv;
+                    }
                 }
                 T un0 = 0, un1 = 0, un2 = 0, cu0 = 0, cu1 = 0, cu2 = 0;
                 if (do_uni) {
