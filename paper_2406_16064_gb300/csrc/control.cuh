@@ -37,7 +37,7 @@ static __global__ void k_after_stage1(const SimDesc* desc, SimState* st, int nsi
     if (s >= nsims) return;
     SimState& S = st[s];
     if (S.status != 0) return;
-    const double mk = bits_to_double(group_max(desc, st, s, false));
+    const double mk = sqrt(bits_to_double(group_max(desc, st, s, false)));   // max |dm/dt|^2 -> max |dm/dt|
     S.maxk = mk;
     S.err_bits = 0ull;
     if (!(mk == mk) || isinf(mk)) { S.status = -4; return; }
@@ -72,6 +72,19 @@ static __global__ void k_controller(const SimDesc* desc, SimState* st, int nsims
     if (S.status == 0 && !(h > 1e-24)) S.status = -5;
 }
 
+// 1/sqrt(s) for the projection: the sum of squares s is formed in FP64; an
+// FP32 rsqrt seed (relative error ~1e-7) is refined by Newton-Raphson steps
+// y <- y (3 - s y^2) / 2 in FP64, each squaring the relative error (one step
+// for FP32 states, two for FP64).  Returns 1 for s = 0.
+template <typename T>
+__device__ __forceinline__ double inv_norm(double s) {
+    if (!(s > 0.0)) return 1.0;
+    double y = (double)rsqrtf((float)s);
+    y = y * (1.5 - 0.5 * s * y * y);
+    if (sizeof(T) == 8) y = y * (1.5 - 0.5 * s * y * y);
+    return y;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(MM_THREADS) k_project(const SimDesc* __restrict__ desc, const SimState* st,
                                                         const WorkItem* __restrict__ items, T* m, const T* y) {
@@ -81,18 +94,27 @@ __global__ void __launch_bounds__(MM_THREADS) k_project(const SimDesc* __restric
     const SimDesc& d = desc[w.sim];
     if (d.group_begin >= 0 && (d.neb_index == 0 || d.neb_index == d.group_end - d.group_begin - 1))
         return;                                    // NEB end images stay bit-fixed
-    const int N = d.ncells;
-    const long long c0 = (long long)w.a * d.nx;
+    const long long N = d.ncells;
+    const long long c0 = d.off + (long long)w.a * d.nx;
     const int cnt = w.b * d.nx;
-    for (int id = threadIdx.x; id < cnt; id += blockDim.x) {
-        const long long o = d.off + c0 + id;
-        const double a = y[o], b = y[o + N], c = y[o + 2 * (long long)N];
-        const double n = sqrt(a * a + b * b + c * c);
-        if (n > 0.0) {
-            const double inv = 1.0 / n;
-            m[o] = (T)(a * inv); m[o + N] = (T)(b * inv); m[o + 2 * (long long)N] = (T)(c * inv);
-        } else {
-            m[o] = (T)a; m[o + N] = (T)b; m[o + 2 * (long long)N] = (T)c;
+    // four cells per thread per pass: all twelve loads in flight before the stores
+    for (int b0 = threadIdx.x; b0 < cnt; b0 += 4 * blockDim.x) {
+        double v[4][3];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int id = b0 + u * blockDim.x;
+            const long long o = c0 + (id < cnt ? id : 0);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) v[u][c] = y[o + c * N];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int id = b0 + u * blockDim.x;
+            if (id >= cnt) continue;
+            const long long o = c0 + id;
+            const double inv = inv_norm<T>(v[u][0] * v[u][0] + v[u][1] * v[u][1] + v[u][2] * v[u][2]);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) m[o + c * N] = (T)(v[u][c] * inv);
         }
     }
 }
@@ -230,7 +252,7 @@ __global__ void __launch_bounds__(MM_THREADS) k_neb_force(NebParams<T> p) {
         }
         for (int c = 0; c < 3; ++c) p.kout[off + c * (long long)N + cell] = (T)k[c];
         if (p.stage == 1) {
-            const double v = sqrt(k[0] * k[0] + k[1] * k[1] + k[2] * k[2]);
+            const double v = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];      // squared norm
             vmax = umax64(vmax, (unsigned long long)__double_as_longlong(v));
         } else if (p.stage == 7) {
             for (int c = 0; c < 3; ++c) {

@@ -54,7 +54,7 @@ struct SimState {
     double t, h, t_end, rtol, max_dmdt;
     double err, maxk;
     unsigned long long err_bits;     // max of |h sum e_j k_j| as ordered bits (NaN wins)
-    unsigned long long maxk_bits;    // max |dm/dt| over cells at stage 1
+    unsigned long long maxk_bits;    // max |dm/dt|^2 over cells at stage 1 (ordered bits)
     long long n_acc, n_rej;
     int status, accepted, pad1, pad2;
     double E[8];                     // energy accumulators (ex, dmi, uni, cub, zee, demag)

@@ -548,6 +548,7 @@ __global__ void __launch_bounds__(MM_THREADS, sizeof(T) == 4 ? 4 : 2) k_xinv(Pas
 
     // per-cell local fields and torque
     const T mu0 = (T)kMu0;
+    const T inv_u = d.Ms > 0.0 ? (T)(1.0 / (kMu0 * d.Ms)) : (T)0;   // 1/(mu0 Ms) for uniform Ms
     const T ex_x = (T)(1.0 / (d.dx * d.dx)), ex_y = (T)(1.0 / (d.dy * d.dy)), ex_z = (T)(1.0 / (d.dz * d.dz));
     const T dm_x = (T)(1.0 / d.dx), dm_y = (T)(1.0 / d.dy);
     const T cA = (T)(2.0 * d.A), cD = (T)d.D, cK = (T)(2.0 * d.Ku), cC = (T)(4.0 * d.Kc);
@@ -578,7 +579,7 @@ __global__ void __launch_bounds__(MM_THREADS, sizeof(T) == 4 ? 4 : 2) k_xinv(Pas
             const T ms = msarr ? msp[cell] : (T)d.Ms;
             T H0 = 0, H1 = 0, H2 = 0, k0 = 0, k1 = 0, k2 = 0;
             if (ms > (T)0) {
-                const T inv = (T)1 / (mu0 * ms);
+                const T inv = msarr ? (T)1 / (mu0 * ms) : inv_u;
                 T hd0 = 0, hd1 = 0, hd2 = 0;
                 if (demag) {
                     const int pos = ix<true>(x >> 1, 1);
@@ -669,7 +670,9 @@ __global__ void __launch_bounds__(MM_THREADS, sizeof(T) == 4 ? 4 : 2) k_xinv(Pas
                 p.heff[o] = H0; p.heff[o + N] = H1; p.heff[o + 2 * N] = H2;
             }
             if (red1) {
-                const double v = sqrt((double)k0 * k0 + (double)k1 * k1 + (double)k2 * k2);
+                // squared norm (FP32 is exact enough for a threshold / step-size
+                // estimate; the max is taken over ordered bits, sqrt once per simulation)
+                const double v = (double)(k0 * k0 + k1 * k1 + k2 * k2);
                 vmax = umax64(vmax, (unsigned long long)__double_as_longlong(v));
             } else if (red7) {
                 const T* ep = p.errp + o;
