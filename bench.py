@@ -11,7 +11,11 @@ perpendicular anisotropy, ~200 reversed disks (FP32 path; the FP64 path is
 measured on the same workload and reported beside it).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                  [--workload film|film_relax_32|cube|neb|batch]
+                  [--workload film|film_relax_32|cube|neb|batch|sweep]
+
+`--workload sweep` times the N x N x 1 family of the paper's throughput
+comparison (demag + exchange + Zeeman, N = 128 ... 4096, FP32) and reports each
+N as RHS cell-updates/s and as Heun-equivalent cells/s (RHS rate / 2).
 """
 from __future__ import annotations
 
@@ -58,6 +62,8 @@ def workload(name, world=1):
         return synth.neb_chain()
     if name == "batch":
         return synth.uneven_batch(count=64 * world)
+    if name == "sweep":
+        return synth.square_film(512)
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -230,6 +236,52 @@ def setup_ctx(mm, w, precision, stream, rtol):
     return ctx
 
 
+SWEEP_N = (128, 256, 512, 1024, 2048, 4096)
+
+
+def run_sweep(args, rank, world, dist):
+    import torch
+    from paper_2406_16064_gb300 import mm
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream()
+    prec = args.precision or "f32"
+    rows = []
+    launches = 0
+    with Clocks(dev) as clk:
+        for n in (tuple(int(v) for v in args.sweep_n.split(",")) if args.sweep_n else SWEEP_N):
+            w = synth.square_film(n, precision=prec)
+            ctx = setup_ctx(mm, w, prec, stream, w.rtol)
+            k = int(max(10, min(args.steps, args.steps * (512 * 512) // (n * n))))
+            ctx.rk45_attempts(args.warmup)
+            n0 = ctx.launches()
+            if dist:
+                dist.barrier()
+            ms = timed_attempts(ctx, torch, stream, k)
+            torch.cuda.synchronize()
+            t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+            if dist:
+                dist.barrier()
+                dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            launches += ctx.launches() - n0
+            rate = world * n * n * 7 * k / (float(t.item()) / 1e3)
+            prof = ctx.profile_attempts(2)
+            rows.append({"n": n, "value": rate, "heun_equivalent_cells_per_s": rate / 2,
+                         "ms_per_step": float(t.item()) / k, "steps": k,
+                         "kernels_ms_per_step": {kk: v[0] / 2 for kk, v in prof.items() if v[1]}})
+            ctx.close()
+            del ctx
+    best = max(rows, key=lambda r: r["value"])
+    line = {"metric": METRIC, "value": best["value"], "unit": UNIT, "n_gpus": world, "steps": best["steps"],
+            "warmup": args.warmup, "ms_per_step": best["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": prec, "data": "synthetic",
+            "config": {"workload": f"square_film_NxNx1_{prec}", "n_best": best["n"], "rhs_per_step": 7,
+                       "terms": "demag + exchange + Zeeman",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "sweep": rows, "clocks": clk.summary(), "gpu_launches": launches}
+    return line
+
+
 def run_gpu(args, rank, world, dist):
     import torch
     from paper_2406_16064_gb300 import mm
@@ -276,18 +328,17 @@ def run_gpu(args, rank, world, dist):
     reps = max(1, min(5, args.steps))
     rows = {}
     dom, achieved, bytes_per_launch, avg_launch_ms = None, None, None, None
-    if not w.neb:
-        prof = ctx.profile_attempts(reps)
-        for k, (tms, cnt) in prof.items():
-            if cnt:
-                rows[k] = {"ms_per_attempt": tms / reps, "launches": cnt,
-                           "achieved_gbs": (kb.get(k, 0.0) * reps) / (tms / 1e3) / 1e9
-                           if kb.get(k) and tms > 0 else None}
-        dom = max((k for k in rows if kb.get(k)), key=lambda k: rows[k]["ms_per_attempt"])
-        launches_dom = prof[dom][1] / reps
-        avg_launch_ms = prof[dom][0] / prof[dom][1]
-        bytes_per_launch = kb[dom] / launches_dom
-        achieved = bytes_per_launch / (avg_launch_ms / 1e3) / 1e9
+    prof = ctx.profile_attempts(reps)
+    for k, (tms, cnt) in prof.items():
+        if cnt:
+            rows[k] = {"ms_per_attempt": tms / reps, "launches": cnt,
+                       "achieved_gbs": (kb.get(k, 0.0) * reps) / (tms / 1e3) / 1e9
+                       if kb.get(k) and tms > 0 else None}
+    dom = max((k for k in rows if kb.get(k)), key=lambda k: rows[k]["ms_per_attempt"])
+    launches_dom = prof[dom][1] / reps
+    avg_launch_ms = prof[dom][0] / prof[dom][1]
+    bytes_per_launch = kb[dom] / launches_dom
+    achieved = bytes_per_launch / (avg_launch_ms / 1e3) / 1e9
     step_ms = ms_max / args.steps
     step_bytes = step_bytes_survey(w, e)
     # end to end through the C ABI with host buffers: H2D of m, one attempt, D2H of m
@@ -351,6 +402,7 @@ def main():
     ap.add_argument("--precision", default=None)
     ap.add_argument("--no-f64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--sweep-n", default=None, help="comma-separated N for --workload sweep")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -364,7 +416,7 @@ def main():
             import torch.distributed as dist
             torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
             dist.init_process_group("nccl")
-        line = run_gpu(args, rank, world, dist)
+        line = (run_sweep if args.workload == "sweep" else run_gpu)(args, rank, world, dist)
         if dist:
             dist.destroy_process_group()
     if rank == 0 and line is not None:

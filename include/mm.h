@@ -169,8 +169,9 @@ int mm_neb_setup(mm_ctx *ctx, int first_sim, int n_images, double k_spring);
  * host) receives the energy of every simulation afterwards. */
 int mm_neb_relax(mm_ctx *ctx, double rtol, long long n_steps, double *energies_out);
 
-/* Profiling aid: runs `reps` RK45 attempts with direct launches (no graph)
- * and a CUDA event recorded on the context stream after every kernel.
+/* Profiling aid: runs `reps` RK45 attempts (NEB attempts in a context with
+ * chains) with direct launches (no graph) and a CUDA event recorded on the
+ * context stream after every kernel kind.
  * ms[k] / counts[k] receive the summed duration and the launch count of each
  * kernel kind k: 0 x-forward pass (with the RK prologue), 1 y forward,
  * 2 z fused, 3 y inverse, 4 y fused (films), 5 x-inverse + field/torque

@@ -871,7 +871,6 @@ int mm_profile_attempts(mm_ctx* C, int reps, double* ms, long long* counts) {
     int rc = check_ready(C);
     if (rc) return rc;
     if (reps < 1 || !ms || !counts) return fail(C, MM_EINVAL, "bad arguments");
-    if (C->neb) return fail(C, MM_EINVAL, "profiling covers plain RK45 contexts");
     ProfileHook H;
     H.stream = C->stream;
     H.cap = 64 * reps + 2;
@@ -885,9 +884,15 @@ int mm_profile_attempts(mm_ctx* C, int reps, double* ms, long long* counts) {
     RkBuffers B;
     B.m = C->m; B.ybuf = C->ybuf; B.kvec_dev = C->kvec_dev; B.errp = C->errp;
     for (int j = 0; j < 7; ++j) B.kvec[j] = C->k[j];
+    B.heff = C->heff;
+    B.tau = C->tau;
     H.mark(-1);
     for (int r = 0; r < reps; ++r) {
-        if (C->precision == MM_F32) engine_attempt<float>(L, B); else engine_attempt<double>(L, B);
+        if (C->neb) {
+            if (C->precision == MM_F32) engine_neb_attempt<float>(L, B); else engine_neb_attempt<double>(L, B);
+        } else {
+            if (C->precision == MM_F32) engine_attempt<float>(L, B); else engine_attempt<double>(L, B);
+        }
     }
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(C->stream));

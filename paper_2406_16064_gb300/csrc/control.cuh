@@ -168,37 +168,50 @@ __global__ void __launch_bounds__(MM_THREADS) k_neb_tangent(NebParams<T> p) {
             const double dmin = fmin(fabs(Ep - E0), fabs(Em - E0));
             if (Ep > Em) { wp = dmax; wm = dmin; } else { wp = dmin; wm = dmax; }
         }
+        // only the direction of tau matters (it is normalised per image): scale the
+        // weights to <= 1 so the per-cell products stay in range in FP32
+        const double wn = fmax(wp, wm);
+        if (wn > 0.0) { wp /= wn; wm /= wn; }
     }
     const long long off = d.off;
     const long long offn = has_next ? p.desc[w.sim + 1].off : off;
     const long long offp = free_img ? p.desc[w.sim - 1].off : off;
+    // per-cell geometry in the context precision, sums in FP64
     double t2 = 0.0, ht = 0.0, th2 = 0.0;
+    const T wpt = (T)wp, wmt = (T)wm;
     const long long c0 = (long long)w.a * d.nx;
     const int cnt = w.b * d.nx;
     for (int id = threadIdx.x; id < cnt; id += blockDim.x) {
         const long long cell = c0 + id;
-        double m[3], mn[3], mp[3];
+        T m[3], mn[3], mp[3];
+#pragma unroll
         for (int c = 0; c < 3; ++c) {
             m[c] = p.ys[off + c * (long long)N + cell];
             mn[c] = p.ys[offn + c * (long long)N + cell];
             mp[c] = p.ys[offp + c * (long long)N + cell];
         }
         if (has_next) {
-            const double cx = m[1] * mn[2] - m[2] * mn[1], cy = m[2] * mn[0] - m[0] * mn[2],
-                         cz = m[0] * mn[1] - m[1] * mn[0];
-            const double th = atan2(sqrt(cx * cx + cy * cy + cz * cz), m[0] * mn[0] + m[1] * mn[1] + m[2] * mn[2]);
-            th2 += th * th;
+            const T cx = m[1] * mn[2] - m[2] * mn[1], cy = m[2] * mn[0] - m[0] * mn[2],
+                    cz = m[0] * mn[1] - m[1] * mn[0];
+            const T th = atan2(sqrt(cx * cx + cy * cy + cz * cz), m[0] * mn[0] + m[1] * mn[1] + m[2] * mn[2]);
+            th2 += (double)(th * th);
         }
         if (free_img) {
-            double t[3];
-            for (int c = 0; c < 3; ++c) t[c] = wp * (mn[c] - m[c]) + wm * (m[c] - mp[c]);
-            const double tm = t[0] * m[0] + t[1] * m[1] + t[2] * m[2];
+            T t[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) t[c] = wpt * (mn[c] - m[c]) + wmt * (m[c] - mp[c]);
+            const T tm = t[0] * m[0] + t[1] * m[1] + t[2] * m[2];
+#pragma unroll
             for (int c = 0; c < 3; ++c) t[c] -= tm * m[c];
+            T tt = 0, htc = 0;
+#pragma unroll
             for (int c = 0; c < 3; ++c) {
-                p.tau[off + c * (long long)N + cell] = (T)t[c];
-                t2 += t[c] * t[c];
-                ht += (double)p.heff[off + c * (long long)N + cell] * t[c];
+                p.tau[off + c * (long long)N + cell] = t[c];
+                tt += t[c] * t[c];
+                htc += p.heff[off + c * (long long)N + cell] * t[c];
             }
+            t2 += (double)tt;
+            ht += (double)htc;
         }
     }
     const double s0 = block_sum(t2, red);
@@ -232,31 +245,35 @@ __global__ void __launch_bounds__(MM_THREADS) k_neb_force(NebParams<T> p) {
     const long long off = d.off;
     const long long c0 = (long long)w.a * d.nx;
     const int cnt = w.b * d.nx;
+    const T inv_tt = (T)inv_t, Htt = (T)Ht, springt = (T)spring, agtt = (T)agt;
     unsigned long long vmax = 0ull;
     for (int id = threadIdx.x; id < cnt; id += blockDim.x) {
         const long long cell = c0 + id;
         const bool mag = !msarr || p.Ms[d.ms_off + cell] > (T)0;
-        double k[3] = {0.0, 0.0, 0.0};
+        T k[3] = {(T)0, (T)0, (T)0};
         if (free_img && mag) {
-            double m[3], F[3];
+            T m[3], F[3];
+#pragma unroll
             for (int c = 0; c < 3; ++c) {
                 m[c] = p.ys[off + c * (long long)N + cell];
-                const double tc = (double)p.tau[off + c * (long long)N + cell] * inv_t;
-                F[c] = (double)p.heff[off + c * (long long)N + cell] - Ht * tc + spring * tc;
+                const T tc = p.tau[off + c * (long long)N + cell] * inv_tt;
+                F[c] = p.heff[off + c * (long long)N + cell] - Htt * tc + springt * tc;
             }
-            const double c0x = m[1] * F[2] - m[2] * F[1], c0y = m[2] * F[0] - m[0] * F[2],
-                         c0z = m[0] * F[1] - m[1] * F[0];
-            k[0] = -agt * (m[1] * c0z - m[2] * c0y);
-            k[1] = -agt * (m[2] * c0x - m[0] * c0z);
-            k[2] = -agt * (m[0] * c0y - m[1] * c0x);
+            const T c0x = m[1] * F[2] - m[2] * F[1], c0y = m[2] * F[0] - m[0] * F[2],
+                    c0z = m[0] * F[1] - m[1] * F[0];
+            k[0] = -agtt * (m[1] * c0z - m[2] * c0y);
+            k[1] = -agtt * (m[2] * c0x - m[0] * c0z);
+            k[2] = -agtt * (m[0] * c0y - m[1] * c0x);
         }
-        for (int c = 0; c < 3; ++c) p.kout[off + c * (long long)N + cell] = (T)k[c];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) p.kout[off + c * (long long)N + cell] = k[c];
         if (p.stage == 1) {
-            const double v = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];      // squared norm
+            const double v = (double)(k[0] * k[0] + k[1] * k[1] + k[2] * k[2]);      // squared norm
             vmax = umax64(vmax, (unsigned long long)__double_as_longlong(v));
         } else if (p.stage == 7) {
+#pragma unroll
             for (int c = 0; c < 3; ++c) {
-                const double v = fabs(hstep * ((double)p.errp[off + c * (long long)N + cell] + p.e7 * (double)(T)k[c]));
+                const double v = fabs(hstep * ((double)p.errp[off + c * (long long)N + cell] + p.e7 * (double)k[c]));
                 vmax = umax64(vmax, (unsigned long long)__double_as_longlong(v));
             }
         }

@@ -21,38 +21,51 @@ static PassParams<T> base_params(const Launch& L) {
     return p;
 }
 
+// Threads of an x- or column-pass CTA.  Long rows and columns need large
+// shared-memory tiles, which cap the CTAs resident on an SM (228 KB each); the
+// CTA then widens so the SM still holds about MM_XTHREADS_MAX<T> threads (32
+// warps FP32, 16 FP64, the register budget of those kernels' launch bounds).
+template <typename T>
+static int wide_threads(size_t smem) {
+    int b = (int)(233472 / (smem + 1024));
+    if (b < 1) b = 1;
+    const int nt = 32 * ((MM_XTHREADS_MAX<T> / b) / 32);
+    return nt < MM_THREADS ? MM_THREADS : nt;
+}
+
 template <typename T>
 static void issue_passes(const Launch& L, PassParams<T> p, const T* ys, bool include_xinv = true) {
     if (L.x.count == 0) return;
     cudaStream_t s = L.stream;
     ProfileHook* hk = L.hook;
     p.items = L.x.dev;
+    const int ntx = wide_threads<T>(L.smem_x), ntxi = wide_threads<T>(L.smem_xi + 2048);
     switch ((p.mode == MODE_RK || p.mode == MODE_NEB) ? p.stage : 0) {
-        case 2: k_xfwd<T, 2><<<L.x.count, MM_THREADS, L.smem_x, s>>>(p); break;
-        case 3: k_xfwd<T, 3><<<L.x.count, MM_THREADS, L.smem_x, s>>>(p); break;
-        case 4: k_xfwd<T, 4><<<L.x.count, MM_THREADS, L.smem_x, s>>>(p); break;
-        case 5: k_xfwd<T, 5><<<L.x.count, MM_THREADS, L.smem_x, s>>>(p); break;
-        case 6: k_xfwd<T, 6><<<L.x.count, MM_THREADS, L.smem_x, s>>>(p); break;
-        case 7: k_xfwd<T, 7><<<L.x.count, MM_THREADS, L.smem_x, s>>>(p); break;
-        default: k_xfwd<T, 0><<<L.x.count, MM_THREADS, L.smem_x, s>>>(p); break;
+        case 2: k_xfwd<T, 2><<<L.x.count, ntx, L.smem_x, s>>>(p); break;
+        case 3: k_xfwd<T, 3><<<L.x.count, ntx, L.smem_x, s>>>(p); break;
+        case 4: k_xfwd<T, 4><<<L.x.count, ntx, L.smem_x, s>>>(p); break;
+        case 5: k_xfwd<T, 5><<<L.x.count, ntx, L.smem_x, s>>>(p); break;
+        case 6: k_xfwd<T, 6><<<L.x.count, ntx, L.smem_x, s>>>(p); break;
+        case 7: k_xfwd<T, 7><<<L.x.count, ntx, L.smem_x, s>>>(p); break;
+        default: k_xfwd<T, 0><<<L.x.count, ntx, L.smem_x, s>>>(p); break;
     }
     if (hk) hk->mark(KIND_XFWD);
     long long n = 1;
     if (L.y13.count) {
         p.items = L.y13.dev;
-        k_ycol<T, 0><<<L.y13.count, MM_THREADS, L.smem_y13, s>>>(p);
+        k_ycol<T, 0><<<L.y13.count, wide_threads<T>(L.smem_y13), L.smem_y13, s>>>(p);
         if (hk) hk->mark(KIND_YFWD);
         ++n;
     }
     if (L.z.count) {
         p.items = L.z.dev;
-        k_zcol<T><<<L.z.count, MM_THREADS, L.smem_z, s>>>(p);
+        k_zcol<T><<<L.z.count, wide_threads<T>(L.smem_z), L.smem_z, s>>>(p);
         if (hk) hk->mark(KIND_ZCOL);
         ++n;
     }
     if (L.y13.count) {
         p.items = L.y13.dev;
-        k_ycol<T, 1><<<L.y13.count, MM_THREADS, L.smem_y13, s>>>(p);
+        k_ycol<T, 1><<<L.y13.count, wide_threads<T>(L.smem_y13), L.smem_y13, s>>>(p);
         if (hk) hk->mark(KIND_YINV);
         ++n;
     }
@@ -80,16 +93,16 @@ static void issue_passes(const Launch& L, PassParams<T> p, const T* ys, bool inc
     }
     if (L.y2.count) {
         p.items = L.y2.dev;
-        k_ycol<T, 2><<<L.y2.count, MM_THREADS, L.smem_y2, s>>>(p);
+        k_ycol<T, 2><<<L.y2.count, wide_threads<T>(L.smem_y2), L.smem_y2, s>>>(p);
         if (hk) hk->mark(KIND_YFUSED);
         ++n;
     }
     if (include_xinv) {
         p.items = L.x.dev;
         if (p.mode == MODE_ENERGY || p.mode == MODE_NEB)
-            k_xinv<T, true><<<L.x.count, MM_THREADS, L.smem_xi, s>>>(p, ys);
+            k_xinv<T, true><<<L.x.count, ntxi, L.smem_xi, s>>>(p, ys);
         else
-            k_xinv<T, false><<<L.x.count, MM_THREADS, L.smem_xi, s>>>(p, ys);
+            k_xinv<T, false><<<L.x.count, ntxi, L.smem_xi, s>>>(p, ys);
         if (hk) hk->mark(KIND_XINV);
         ++n;
     }
@@ -145,6 +158,7 @@ void engine_neb_attempt(const Launch& L, const RkBuffers& B) {
     cudaStream_t s = L.stream;
     for (int st = 1; st <= 7; ++st) {
         k_neb_reset<<<blocks_for(L.nsims), 128, 0, s>>>(L.state, L.nsims);
+        if (L.hook) L.hook->mark(KIND_CONTROL);
         PassParams<T> p = base_params<T>(L);
         p.mode = MODE_NEB;
         p.stage = st;
@@ -173,15 +187,19 @@ void engine_neb_attempt(const Launch& L, const RkBuffers& B) {
         q.e7 = dp_e(6);
         k_neb_tangent<T><<<L.x.count, MM_THREADS, 0, s>>>(q);
         k_neb_force<T><<<L.x.count, MM_THREADS, 0, s>>>(q);
+        if (L.hook) L.hook->mark(KIND_NEB);
         if (L.launches) *L.launches += 3;
         if (st == 1) {
             k_after_stage1<<<blocks_for(L.nsims), 128, 0, s>>>(L.desc, L.state, L.nsims);
+            if (L.hook) L.hook->mark(KIND_CONTROL);
             if (L.launches) *L.launches += 1;
         }
     }
     k_controller<<<blocks_for(L.nsims), 128, 0, s>>>(L.desc, L.state, L.nsims);
+    if (L.hook) L.hook->mark(KIND_CONTROL);
     k_project<T><<<L.x.count, MM_THREADS, 0, s>>>(L.desc, L.state, L.x.dev, reinterpret_cast<T*>(B.m),
                                                   reinterpret_cast<const T*>(B.ybuf));
+    if (L.hook) L.hook->mark(KIND_PROJECT);
     if (L.launches) *L.launches += 2;
 }
 

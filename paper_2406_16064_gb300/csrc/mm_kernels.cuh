@@ -19,6 +19,10 @@
 #define MM_LOG2_LMAX 13
 #define MM_LMAX (1 << MM_LOG2_LMAX)
 #define MM_THREADS 256
+// Largest x-pass CTA (threads) per precision; as launch bounds with one CTA
+// per SM it caps the x kernels at 64 (FP32) / 128 (FP64) registers a thread.
+template <typename T>
+constexpr int MM_XTHREADS_MAX = sizeof(T) == 4 ? 1024 : 512;
 
 #ifndef MM_CHECKED
 #define MM_CHECKED 0

@@ -81,7 +81,7 @@ __device__ __forceinline__ bool sim_inactive(const PassParams<T>& p, int sim) {
 // and the non-RK modes).  The stage's coefficients are compile-time
 // constants, so zero ones vanish and the stage vectors' loads issue together.
 template <typename T, int S>
-__global__ void __launch_bounds__(MM_THREADS) k_xfwd(PassParams<T> p) {
+__global__ void __launch_bounds__(MM_XTHREADS_MAX<T>, 1) k_xfwd(PassParams<T> p) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const WorkItem w = p.items[blockIdx.x];
     if (sim_inactive(p, w.sim)) return;
@@ -186,9 +186,15 @@ __global__ void __launch_bounds__(MM_THREADS) k_xfwd(PassParams<T> p) {
 // ---------------------------------------------------------------- y columns
 // YMODE 0: forward (one component), 1: inverse (one component),
 //       2: forward + tensor product + inverse (three components, Pz == 1)
-// A CTA owns one kx block (Ty columns) of one plane.
+// A CTA owns one kx block (Ty columns) of one plane.  Shared memory holds the
+// block as rows [y][cc][col] (row stride NC*Ty).  The forward is a
+// decimation-in-frequency FFT (natural order in, bit-reversed out) and the
+// inverse a decimation-in-time FFT (bit-reversed in, natural out), so neither
+// needs a permutation: the spectrum between them is in bit-reversed row
+// order, in shared memory (YMODE 2) or in the global spectrum (YMODE 0 -> z
+// pass -> YMODE 1), and the tensor product reads bin ky = bitrev(row).
 template <typename T, int YMODE>
-__global__ void __launch_bounds__(MM_THREADS) k_ycol(PassParams<T> p) {
+__global__ void __launch_bounds__(MM_XTHREADS_MAX<T>, 1) k_ycol(PassParams<T> p) {
     extern __shared__ __align__(16) unsigned char smraw[];
     V2<T>* sm = reinterpret_cast<V2<T>*>(smraw);
     const WorkItem w = p.items[blockIdx.x];
@@ -200,7 +206,7 @@ __global__ void __launch_bounds__(MM_THREADS) k_ycol(PassParams<T> p) {
     const int ncols = min(TT, d.Kx - kx0);
     constexpr int NC = (YMODE == 2) ? 3 : 1;
     const int c0 = (YMODE == 2) ? 0 : w.c;
-    const int es = NC * TT;                     // layout [y][cc][col]
+    const int es = NC * TT;
     long long gb[NC];
 #pragma unroll
     for (int cc = 0; cc < NC; ++cc) gb[cc] = spec_block<T>(d, c0 + cc, z, b);
@@ -220,55 +226,60 @@ __global__ void __launch_bounds__(MM_THREADS) k_ycol(PassParams<T> p) {
             const int id = b0 + u * blockDim.x;
             if (id < (L << lT)) {
                 const int col = id & (TT - 1), y = id >> lT;
-                const int pos = (YMODE == 1) ? y : bitrev(y, lL);
 #pragma unroll
-                for (int cc = 0; cc < NC; ++cc) sm[pos * es + cc * TT + col] = v[cc][u];
+                for (int cc = 0; cc < NC; ++cc) sm[y * es + cc * TT + col] = v[cc][u];
             }
         }
     }
     __syncthreads();
     if (YMODE == 0) {
-        fft_dit<T, false>(sm, lL, es, 1, es, p.tw);
+        fft_dif<T, false>(sm, lL, es, 1, es, p.tw);
         for (int id = threadIdx.x; id < (L << lT); id += blockDim.x)
-            p.spec[gb[0] + id] = sm[id];
+            p.spec[gb[0] + id] = sm[id];             // NC == 1: row stride Ty
         return;
     }
     if (YMODE == 2) {
-        fft_dit<T, false>(sm, lL, es, 1, es, p.tw);
+        fft_dif<T, false>(sm, lL, es, 1, es, p.tw);
         for (int id = threadIdx.x; id < (L << lT); id += blockDim.x) {
-            const int col = id & (TT - 1), y = id >> lT;
+            const int col = id & (TT - 1), r = id >> lT;
             if (col < ncols) {
-                V2<T>* q = sm + y * es + col;
+                V2<T>* q = sm + r * es + col;
                 V2<T> a = q[0], bb = q[TT], c = q[2 * TT];
-                tensor_apply<T>(d, p.tensor, kx0 + col, y, 0, a, bb, c);
+                tensor_apply<T>(d, p.tensor, kx0 + col, bitrev(r, lL), 0, a, bb, c);
                 q[0] = a; q[TT] = bb; q[2 * TT] = c;
             }
         }
         __syncthreads();
     }
-    fft_dif<T, true>(sm, lL, es, 1, es, p.tw);
+    fft_dit<T, true>(sm, lL, es, 1, es, p.tw);
 #pragma unroll
     for (int cc = 0; cc < NC; ++cc) {
         for (int id = threadIdx.x; id < (ny << lT); id += blockDim.x) {
             const int col = id & (TT - 1), y = id >> lT;
-            p.spec[gb[cc] + id] = sm[bitrev(y, lL) * es + cc * TT + col];
+            p.spec[gb[cc] + id] = sm[y * es + cc * TT + col];
         }
     }
 }
 
 // ---------------------------------------------------------------- z columns
+// One CTA per (global row, kx block): the three components' z columns, rows
+// [z][c][col] (row stride 3*Ty).  Forward decimation in frequency, the
+// tensor product at kz = bitrev(row), inverse decimation in time.  The y pass
+// before it leaves the rows of each plane in bit-reversed order, so global
+// row w.a holds bin ky = bitrev(w.a) (Py = 1: row 0, bin 0).
 template <typename T>
-__global__ void __launch_bounds__(MM_THREADS) k_zcol(PassParams<T> p) {
+__global__ void __launch_bounds__(MM_XTHREADS_MAX<T>, 1) k_zcol(PassParams<T> p) {
     extern __shared__ __align__(16) unsigned char smraw[];
     V2<T>* sm = reinterpret_cast<V2<T>*>(smraw);
     const WorkItem w = p.items[blockIdx.x];
     if (sim_inactive(p, w.sim)) return;
     const SimDesc& d = p.desc[w.sim];
     const int L = d.Pz, lL = d.lPz, TT = d.Ty, lT = d.lTy, nz = d.nz;
-    const int ky = w.a, b = w.b;
+    const int row = w.a, b = w.b;
+    const int ky = bitrev(row, d.lPy);
     const int kx0 = b << lT;
     const int ncols = min(TT, d.Kx - kx0);
-    const int es = 3 * TT;                      // layout [z][c][col]
+    const int es = 3 * TT;
     const int tot = (L * 3) << lT;
     for (int b0 = threadIdx.x; b0 < tot; b0 += 4 * blockDim.x) {   // four loads in flight
         V2<T> v[4];
@@ -279,7 +290,7 @@ __global__ void __launch_bounds__(MM_THREADS) k_zcol(PassParams<T> p) {
             const int rest = id >> lT;
             const int c = rest % 3;
             const int z = rest / 3;
-            v[u] = (id < tot && z < nz) ? p.spec[spec_block<T>(d, c, z, b) + ((long long)ky << lT) + col]
+            v[u] = (id < tot && z < nz) ? p.spec[spec_block<T>(d, c, z, b) + ((long long)row << lT) + col]
                                         : mk<T>((T)0, (T)0);
         }
 #pragma unroll
@@ -290,31 +301,31 @@ __global__ void __launch_bounds__(MM_THREADS) k_zcol(PassParams<T> p) {
                 const int rest = id >> lT;
                 const int c = rest % 3;
                 const int z = rest / 3;
-                sm[bitrev(z, lL) * es + c * TT + col] = v[u];
+                sm[z * es + c * TT + col] = v[u];
             }
         }
     }
     __syncthreads();
-    fft_dit<T, false>(sm, lL, es, 1, es, p.tw);
+    fft_dif<T, false>(sm, lL, es, 1, es, p.tw);
     for (int id = threadIdx.x; id < (L << lT); id += blockDim.x) {
         const int col = id & (TT - 1);
-        const int z = id >> lT;
+        const int r = id >> lT;
         if (col < ncols) {
-            V2<T>* q = sm + z * es + col;
+            V2<T>* q = sm + r * es + col;
             V2<T> a = q[0], bb = q[TT], c = q[2 * TT];
-            tensor_apply<T>(d, p.tensor, kx0 + col, ky, z, a, bb, c);
+            tensor_apply<T>(d, p.tensor, kx0 + col, ky, bitrev(r, lL), a, bb, c);
             q[0] = a; q[TT] = bb; q[2 * TT] = c;
         }
     }
     __syncthreads();
-    fft_dif<T, true>(sm, lL, es, 1, es, p.tw);
+    fft_dit<T, true>(sm, lL, es, 1, es, p.tw);
     const int tot3 = (nz * 3) << lT;
     for (int id = threadIdx.x; id < tot3; id += blockDim.x) {
         const int col = id & (TT - 1);
         const int rest = id >> lT;
         const int c = rest % 3;
         const int z = rest / 3;
-        p.spec[spec_block<T>(d, c, z, b) + ((long long)ky << lT) + col] = sm[bitrev(z, lL) * es + c * TT + col];
+        p.spec[spec_block<T>(d, c, z, b) + ((long long)row << lT) + col] = sm[z * es + c * TT + col];
     }
 }
 
@@ -323,12 +334,13 @@ template <typename T, int PZ>
 __device__ void yzc_zstep(const PassParams<T>& p, const SimDesc& d, V2<T>* const (&rem)[8], int rank, int nz,
                           int es, int kx0, int ncols) {
     const int TT = d.Ty, lT = d.lTy, Py = d.Py;
-    const int ky_lo = (int)(((long long)rank * Py) / nz);
+    const int ky_lo = (int)(((long long)rank * Py) / nz);    // share of rows
     const int ky_hi = (int)(((long long)(rank + 1) * Py) / nz);
     const int nwork = (ky_hi - ky_lo) << lT;
     for (int id = threadIdx.x; id < nwork; id += blockDim.x) {
         const int col = id & (TT - 1);
-        const int ky = ky_lo + (id >> lT);
+        const int r = ky_lo + (id >> lT);              // row of the bit-reversed y spectrum
+        const int ky = bitrev(r, d.lPy);
         if (col >= ncols) continue;
         V2<T> X[3][PZ];
 #pragma unroll
@@ -336,7 +348,7 @@ __device__ void yzc_zstep(const PassParams<T>& p, const SimDesc& d, V2<T>* const
 #pragma unroll
             for (int k = 0; k < PZ; ++k) X[c][k] = mk<T>((T)0, (T)0);
         }
-        const int o = ky * es + col;
+        const int o = r * es + col;
 #pragma unroll
         for (int zz = 0; zz < 8; ++zz) {
             if (zz < nz && zz < PZ) {
@@ -395,7 +407,7 @@ __global__ void __launch_bounds__(MM_THREADS, sizeof(T) == 4 ? 2 : 1) k_yzc(Pass
     const int z = rank, b = w.b;
     const int kx0 = b << lT;
     const int ncols = min(TT, d.Kx - kx0);
-    const int es = 3 * TT;                      // layout [y][c][col]
+    const int es = 3 * TT;                      // rows [y][c][col] at y * es
     long long gb[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) gb[c] = spec_block<T>(d, c, z, b);
@@ -415,24 +427,24 @@ __global__ void __launch_bounds__(MM_THREADS, sizeof(T) == 4 ? 2 : 1) k_yzc(Pass
             if (id < (L << lT)) {
                 const int col = id & (TT - 1), y = id >> lT;
 #pragma unroll
-                for (int c = 0; c < 3; ++c) sm[bitrev(y, lL) * es + c * TT + col] = v[c][u];
+                for (int c = 0; c < 3; ++c) sm[y * es + c * TT + col] = v[c][u];
             }
         }
     }
     __syncthreads();
-    fft_dit<T, false>(sm, lL, es, 1, es, p.tw);
+    fft_dif<T, false>(sm, lL, es, 1, es, p.tw);   // rows leave in bit-reversed order
     cl.sync();                                  // every plane transformed along y
     V2<T>* rem[8];
 #pragma unroll
     for (int zz = 0; zz < 8; ++zz) rem[zz] = zz < nz ? cl.map_shared_rank(sm, zz) : sm;
     yzc_zstep<T, PZ>(p, d, rem, rank, nz, es, kx0, ncols);   // PZ == d.Pz, fixed by nz per launch
     cl.sync();                                  // every row back in its owner's plane
-    fft_dif<T, true>(sm, lL, es, 1, es, p.tw);
+    fft_dit<T, true>(sm, lL, es, 1, es, p.tw);    // bit-reversed in, natural out
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         for (int id = threadIdx.x; id < (ny << lT); id += blockDim.x) {
             const int col = id & (TT - 1), y = id >> lT;
-            p.spec[gb[c] + id] = sm[bitrev(y, lL) * es + c * TT + col];
+            p.spec[gb[c] + id] = sm[y * es + c * TT + col];
         }
     }
 }
@@ -473,10 +485,10 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 // Shared memory: two buffers of 3*nrows padded sequences of Kx complex values.
 // ENERGY: energy accumulation (energy and NEB modes) instead of the RK reductions.
 template <typename T, bool ENERGY>
-__global__ void __launch_bounds__(MM_THREADS, sizeof(T) == 4 ? 4 : 2) k_xinv(PassParams<T> p, const T* __restrict__ ys) {
+__global__ void __launch_bounds__(MM_XTHREADS_MAX<T>, 1) k_xinv(PassParams<T> p, const T* __restrict__ ys) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    __shared__ unsigned long long red_u[MM_THREADS / 32];
-    __shared__ double red_d[MM_THREADS / 32];
+    __shared__ unsigned long long red_u[32];
+    __shared__ double red_e[ENERGY ? 6 * 32 : 1];
     const WorkItem w = p.items[blockIdx.x];
     if (sim_inactive(p, w.sim)) return;
     const SimDesc& d = p.desc[w.sim];
@@ -641,20 +653,16 @@ __global__ void __launch_bounds__(MM_THREADS, sizeof(T) == 4 ? 4 : 2) k_xinv(Pas
                 H1 = hd1 + ex1 + dm1 + un1 + cu1 + Hy0;
                 H2 = hd2 + ex2 + dm2 + un2 + cu2 + Hz0;
                 if (ENERGY) {
-                    const double V = d.dx * d.dy * d.dz;
-                    const double msV = (double)ms * V;
-                    esum[0] += -0.5 * kMu0 * msV * ((double)m0 * ex0 + (double)m1 * ex1 + (double)m2 * ex2);
-                    esum[1] += -0.5 * kMu0 * msV * ((double)m0 * dm0 + (double)m1 * dm1 + (double)m2 * dm2);
-                    if (do_uni) {
-                        const double mu = (double)m0 * d.u[0] + (double)m1 * d.u[1] + (double)m2 * d.u[2];
-                        esum[2] += -d.Ku * V * mu * mu;
-                    }
-                    if (do_cub) {
-                        const double a0 = m0, a1 = m1, a2 = m2;
-                        esum[3] += d.Kc * V * (a0 * a0 * a0 * a0 + a1 * a1 * a1 * a1 + a2 * a2 * a2 * a2);
-                    }
-                    esum[4] += -kMu0 * msV * ((double)m0 * d.H[0] + (double)m1 * d.H[1] + (double)m2 * d.H[2]);
-                    esum[5] += -0.5 * kMu0 * msV * ((double)m0 * hd0 + (double)m1 * hd1 + (double)m2 * hd2);
+                    // per-cell densities in the context precision, summed in FP64; the
+                    // constant factors are applied once per CTA
+                    esum[0] += (double)(ms * (m0 * ex0 + m1 * ex1 + m2 * ex2));
+                    esum[1] += (double)(ms * (m0 * dm0 + m1 * dm1 + m2 * dm2));
+                    const T mu = m0 * ux + m1 * uy + m2 * uz;
+                    esum[2] += (double)(mu * mu);
+                    const T q0 = m0 * m0, q1 = m1 * m1, q2 = m2 * m2;
+                    esum[3] += (double)(q0 * q0 + q1 * q1 + q2 * q2);
+                    esum[4] += (double)(ms * (m0 * Hx0 + m1 * Hy0 + m2 * Hz0));
+                    esum[5] += (double)(ms * (m0 * hd0 + m1 * hd1 + m2 * hd2));
                 }
                 // LL form: dm/dt = -g~ m x H - alpha g~ m x (m x H)
                 const T c0 = m1 * H2 - m2 * H1, c1 = m2 * H0 - m0 * H2, c2 = m0 * H1 - m1 * H0;
@@ -690,10 +698,26 @@ __global__ void __launch_bounds__(MM_THREADS, sizeof(T) == 4 ? 4 : 2) k_xinv(Pas
         if (threadIdx.x == 0) atomicMax(red1 ? &p.state[w.sim].maxk_bits : &p.state[w.sim].err_bits, rr);
     }
     if (ENERGY) {
+        // E_ex, E_dmi, E_d = -mu0/2 V sum Ms m.H;  E_zee = -mu0 V sum Ms m.H_ext;
+        // E_uni = -Ku V sum (m.u)^2;  E_cub = Kc V sum (mx^4 + my^4 + mz^4)
+        const double V = d.dx * d.dy * d.dz;
+        const double scale[6] = {-0.5 * kMu0 * V, -0.5 * kMu0 * V, -d.Ku * V, d.Kc * V, -kMu0 * V,
+                                 -0.5 * kMu0 * V};
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
         for (int t = 0; t < 6; ++t) {
-            const double s = block_sum(esum[t], red_d);
-            if (threadIdx.x == 0) atomicAdd(&p.state[w.sim].E[t], s);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) esum[t] += __shfl_xor_sync(0xffffffffu, esum[t], o);
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int t = 0; t < 6; ++t) red_e[t * 32 + wid] = esum[t];
+        }
+        __syncthreads();
+        if (threadIdx.x < 6) {
+            double e = 0.0;
+            for (int i = 0; i < (int)(blockDim.x >> 5); ++i) e += red_e[threadIdx.x * 32 + i];
+            atomicAdd(&p.state[w.sim].E[threadIdx.x], e * scale[threadIdx.x]);
         }
     }
 }

@@ -301,6 +301,15 @@ def neb_chain(seed: int = 4, n_images: int = 32, n: int = 128, precision: str = 
                     rtol=1e-5, steps=500, neb={"k_spring": 1e5, "n_images": n_images})
 
 
+def square_film(n: int, seed: int = 6, precision: str = "f32") -> Workload:
+    """N x N x 1 film with demag, exchange and Zeeman only, random start (the
+    mesh family of the paper's throughput comparison, Sec. 4 'Performance')."""
+    mesh = Mesh(n, n, 1, 2e-9, 2e-9, 2e-9)
+    mat = Material(Ms=8e5, A=1.3e-11, alpha=0.1, H=(0.0, 0.0, 10 * MT))
+    return Workload(f"square_film_{n}x{n}x1_{precision}", [Sim(mesh, mat, random_state(seed, mesh))],
+                    precision=precision, rtol=1e-6 if precision == "f64" else 1e-5)
+
+
 MESH_CHOICES = [(64, 64, 1), (128, 64, 2), (256, 256, 1), (512, 256, 4)]
 
 

@@ -216,6 +216,28 @@ def test_neb_small_film_chain_matches_oracle():
     assert np.abs(E - Eo).max() < 1e-8 * np.abs(Eo).max()
 
 
+def test_neb_small_film_chain_f32_matches_oracle():
+    """FP32 chain (per-cell tangent, distance and force in FP32, sums in FP64)
+    against the FP64 oracle over the first steps, before the two step-size
+    sequences part: m within 1e-5, energies within 1e-5 relative (the FP32
+    field bar)."""
+    mesh = synth.Mesh(12, 12, 1, 1e-9, 1e-9, 0.5e-9)
+    mat = synth.Material(Ms=5.8e5, A=1.5e-11, D=3e-3, dmi=1, Ku=8e5, alpha=0.5, precession=0)
+    w = synth.neb_chain(n_images=6, n=12, radius=3e-9)
+    chain = np.stack([s.m0 for s in w.sims])
+    ctx = make_ctx("f32", [synth.Sim(mesh, mat, chain[i]) for i in range(6)])
+    ctx.set_m(chain.ravel())
+    ctx.neb_setup(0, 6, 1e5)
+    ctx.reset_time()
+    E = ctx.neb_relax(1e-5, 2)
+    Ms = F.ms_array(mesh, mat)
+    Nt = D.mesh_tensor(mesh)
+    c, Eo, st = NB.relax(mesh, mat, Ms, chain, 1e5, 1e-5, 2, Nt, "direct")
+    mg = ctx.get_m(-1).reshape(chain.shape)
+    assert np.abs(mg - c).max() < 1e-5
+    assert np.abs(E - Eo).max() < 1e-5 * np.abs(Eo).max()
+
+
 def test_bounded_wait_times_out_cleanly():
     from paper_2406_16064_gb300 import mm
     mesh = synth.Mesh(2, 2, 1, 1e-9, 1e-9, 1e-9)
@@ -237,3 +259,24 @@ def test_nan_input_reports_enan():
     with pytest.raises(mm.MMError) as e:
         ctx.relax(1e-6, t_end=1e-12, max_steps=10, sync_every=1)
     assert e.value.code == mm.MM_ENAN
+
+
+def test_profile_attempts_counts_every_kernel_kind():
+    """Per-kind event timing: 7 x-forward and 7 x-inverse launches per attempt,
+    one projection; in a NEB context also 7 NEB force launches."""
+    mesh = synth.Mesh(12, 12, 1, 1e-9, 1e-9, 0.5e-9)
+    mat = synth.Material(Ms=5.8e5, A=1.5e-11, D=3e-3, dmi=1, Ku=8e5, alpha=0.5, precession=0)
+    w = synth.neb_chain(n_images=4, n=12, radius=3e-9)
+    chain = np.stack([s.m0 for s in w.sims])
+    for neb in (False, True):
+        ctx = make_ctx("f32", [synth.Sim(mesh, mat, chain[i]) for i in range(4)])
+        ctx.set_m(chain.ravel())
+        if neb:
+            ctx.neb_setup(0, 4, 1e5)
+        ctx.reset_time()
+        ctx.rk45_setup(1e-5, t_end=0.0, max_dmdt=0.0)
+        prof = ctx.profile_attempts(2)
+        assert prof["x_forward"][1] == 14 and prof["x_inverse_epilogue"][1] == 14
+        assert prof["y_fused"][1] == 14 and prof["project"][1] == 2
+        assert prof["neb"][1] == (14 if neb else 0)
+        assert all(t > 0 for t, c in prof.values() if c)

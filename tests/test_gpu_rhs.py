@@ -72,6 +72,32 @@ def test_rhs_f32_matches_oracle(mesh):
     assert rms_rel(dmdt, ref_k) < TOL32
 
 
+# Long rows: x tiles of one row whose shared memory limits an SM to 1-3 CTAs,
+# so the x passes launch wider CTAs (512 / 1024 threads FP32, 512 FP64).
+LONG_ROWS = [
+    ("f32", (2048, 3, 1, 2e-9, 2e-9, 2e-9)),   # 2 CTAs per SM -> 512 threads
+    ("f32", (4096, 2, 1, 2e-9, 2e-9, 2e-9)),   # 1 CTA per SM -> 1024 threads
+    ("f32", (1500, 3, 2, 1e-9, 2e-9, 1e-9)),   # ragged row, two planes (cluster path)
+    ("f64", (2048, 2, 1, 2e-9, 2e-9, 2e-9)),   # 1 CTA per SM -> 512 threads
+    ("f64", (700, 3, 3, 2e-9, 1e-9, 1e-9)),    # 2 CTAs per SM -> 256 threads
+]
+
+
+@pytest.mark.parametrize("precision,mesh", LONG_ROWS)
+def test_rhs_long_rows_wide_ctas(precision, mesh):
+    m = synth.Mesh(*mesh)
+    sim = synth.Sim(m, _mat(), synth.random_state(6, m))
+    ctx = make_ctx(precision, [sim])
+    dmdt, heff = ctx.rhs_host(sim.m0.ravel())
+    ref_k, ref_H = oracle_rhs(sim, method="fft")
+    if precision == "f64":
+        assert max_rel(heff, ref_H) < TOL64
+        assert max_rel(dmdt, ref_k) < TOL64
+    else:
+        assert rms_rel(heff, ref_H) < TOL32
+        assert rms_rel(dmdt, ref_k) < TOL32
+
+
 def test_rhs_masked_cells_and_terms_off():
     m = synth.Mesh(9, 7, 3, 2e-9, 2e-9, 2e-9)
     Ms = np.full(m.shape, 8e5)
