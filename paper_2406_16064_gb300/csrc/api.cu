@@ -157,8 +157,7 @@ int validate_items(mm_ctx* C) {
         if (d.flags & F_DEMAG) {
             if (d.spec_off < 0 || d.spec_off + plan_spec_elems(d) > C->spec_elems)
                 return fail(C, MM_EBOUNDS, "spectrum block");
-            const long long plane = (long long)d.Pzh * d.Pyh * d.Kx;
-            if (d.tens_off < 0 || d.tens_off + d.ncomp * plane > C->tens_elems)
+            if (d.tens_off < 0 || d.tens_off + plan_tens_elems(d) > C->tens_elems)
                 return fail(C, MM_EBOUNDS, "tensor block");
             if ((d.NBx << d.lTy) < d.Kx || d.Ty != (1 << d.lTy)) return fail(C, MM_EBOUNDS, "kx blocks");
         }
@@ -242,8 +241,10 @@ int precompute_geometry(mm_ctx* C, Geom& g, const SimDesc& d) {
         launch_newell_place(C->stream, C->oct + g.oct_off, c, g.nx, g.ny, g.nz, d.Px, d.Py, d.Pz, buf);
         for (int ax = 0; ax < 3; ++ax) launch_fft_axis_f64(C->stream, buf, d.Px, d.Py, d.Pz, ax, C->twd);
         char* out = (char*)C->tens + (size_t)g.tens_off * C->esz;
+        const bool blocked = plan_uses_yzc(d);
         launch_newell_extract(C->stream, buf, c, d.Px, d.Py, d.Kx, d.Pyh, d.Pzh, scale, out,
-                              C->precision == MM_F32, C->diag_d, C->diag_d + 1);
+                              C->precision == MM_F32, blocked ? d.Ty : 0, yzc_qp(d.Pz), C->diag_d,
+                              C->diag_d + 1);
         C->launches += 5;
         CK(cudaGetLastError());
     }
@@ -403,10 +404,10 @@ int mm_add_sim(mm_ctx* C, const mm_mesh* mesh, const mm_material* mat, const dou
     for (int i = 0; i < 3; ++i) d.H[i] = mat->H[i];
     d.alpha = mat->alpha; d.gamma = mat->gamma;
     d.dx = mesh->dx; d.dy = mesh->dy; d.dz = mesh->dz;
-    d.flags = (mat->demag ? F_DEMAG : 0) | (mat->dmi_kind == MM_DMI_INTERFACIAL ? F_DMI : 0) |
-              (mat->precession ? F_PREC : 0);
+    d.flags = (mat->demag ? F_DEMAG : 0) | (mat->precession ? F_PREC : 0);
     if (mat->dmi_kind != MM_DMI_NONE && mat->dmi_kind != MM_DMI_INTERFACIAL)
         return fail(C, MM_EINVAL, "unsupported DMI kind");
+    plan_coefficients(d, mat->dmi_kind == MM_DMI_INTERFACIAL);
     d.group_begin = d.group_end = -1;
     d.neb_index = -1;
     d.ms_off = -1;
@@ -436,12 +437,14 @@ int mm_batch_layout(const mm_ctx* C, long long* offsets, long long* total) {
 int mm_set_field(mm_ctx* C, int sim, const double H[3]) {
     if (!C || !H) return MM_EINVAL;
     if (sim < 0 || sim >= (int)C->sims.size()) return fail(C, MM_EINVAL, "bad sim id");
+    SimHost& s = C->sims[sim];
     for (int i = 0; i < 3; ++i) {
-        C->sims[sim].mat.H[i] = H[i];
-        C->sims[sim].d.H[i] = H[i];
+        s.mat.H[i] = H[i];
+        s.d.H[i] = H[i];
     }
+    plan_coefficients(s.d, s.mat.dmi_kind == MM_DMI_INTERFACIAL);
     if (C->finalized) {
-        CK(cudaMemcpyAsync(&C->desc_d[sim].H[0], H, 3 * sizeof(double), cudaMemcpyHostToDevice, C->stream));
+        CK(cudaMemcpyAsync(&C->desc_d[sim], &s.d, sizeof(SimDesc), cudaMemcpyHostToDevice, C->stream));
         CK(cudaStreamSynchronize(C->stream));
     }
     return MM_OK;
@@ -477,8 +480,8 @@ int mm_precompute_demag(mm_ctx* C) {
         if (g.demag) {
             for (SimHost& s : C->sims)
                 if (s.geom == (int)gi) {
-                    g.tens_off = C->tens_elems;
-                    C->tens_elems += (long long)s.d.ncomp * s.d.Pzh * s.d.Pyh * s.d.Kx;
+                    g.tens_off = C->tens_elems;   // a multiple of 4 elements: 16-byte vector loads
+                    C->tens_elems += (plan_tens_elems(s.d) + 3) & ~3LL;
                     break;
                 }
         }
@@ -519,6 +522,7 @@ int mm_precompute_demag(mm_ctx* C) {
     if ((rc = dalloc(C, &C->spec, (size_t)C->spec_elems * 2 * C->esz))) return rc;
     if ((rc = dalloc(C, &C->Msd, (size_t)C->ms_elems * C->esz))) return rc;
     if ((rc = dalloc(C, &C->tens, (size_t)C->tens_elems * C->esz))) return rc;
+    CK(cudaMemsetAsync(C->tens, 0, (size_t)C->tens_elems * C->esz, C->stream));   // padding of blocked tensors
     if ((rc = dalloc(C, (void**)&C->oct, (size_t)C->oct_elems * 8))) return rc;
     if ((rc = dalloc(C, &C->twd, (size_t)MM_LMAX * 16))) return rc;
     if ((rc = dalloc(C, &C->twf, (size_t)MM_LMAX * 8))) return rc;

@@ -85,6 +85,46 @@ __device__ __forceinline__ double inv_norm(double s) {
     return y;
 }
 
+// m <- y / |y| for one cell.  FP64 states: sum of squares and Newton-refined
+// rsqrt in FP64.  FP32 states: the same accuracy from FP32 operations in
+// float-float arithmetic (error-free products and sums, one Newton step on
+// the unevaluated sum hi + lo), since FP64 instructions would bound the
+// kernel on GB300: 1/|y| comes out to ~1e-13 relative and each component is
+// rounded once, as the FP64 form rounds (T)(y_c / |y|).
+__device__ __forceinline__ void project_cell(const double (&y)[3], double (&m)[3]) {
+    const double inv = inv_norm<double>(y[0] * y[0] + y[1] * y[1] + y[2] * y[2]);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) m[c] = y[c] * inv;
+}
+
+__device__ __forceinline__ void project_cell(const float (&y)[3], float (&m)[3]) {
+    float p0, e0, p1, e1, p2, e2, s, t1, t2;
+    two_prod(y[0], y[0], p0, e0);
+    two_prod(y[1], y[1], p1, e1);
+    two_prod(y[2], y[2], p2, e2);
+    two_sum(p0, p1, s, t1);
+    two_sum(s, p2, s, t2);
+    const float lo = __fadd_rn(__fadd_rn(__fadd_rn(e0, e1), __fadd_rn(e2, t1)), t2);   // |y|^2 = s + lo
+    if (!(s > 0.f)) {                      // zero (or non-finite) vector: unchanged, as the FP64 form
+#pragma unroll
+        for (int c = 0; c < 3; ++c) m[c] = y[c];
+        return;
+    }
+    const float r0 = rsqrtf(s);
+    // q = 1 - |y|^2 r0^2 to ~eps^2: r0^2 = a + ae and s a = b + be exactly, 1 - b exact (b ~ 1)
+    float a, ae, b, be;
+    two_prod(r0, r0, a, ae);
+    two_prod(s, a, b, be);
+    const float q = __fsub_rn(__fsub_rn(__fsub_rn(1.f, b), be), __fmaf_rn(s, ae, __fmul_rn(lo, a)));
+    const float rl = __fmul_rn(__fmul_rn(0.5f, r0), q);   // 1/|y| = r0 + rl (one Newton step)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        float pc, ec;
+        two_prod(y[c], r0, pc, ec);
+        m[c] = __fadd_rn(pc, __fmaf_rn(y[c], rl, ec));
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(MM_THREADS) k_project(const SimDesc* __restrict__ desc, const SimState* st,
                                                         const WorkItem* __restrict__ items, T* m, const T* y) {
@@ -99,7 +139,7 @@ __global__ void __launch_bounds__(MM_THREADS) k_project(const SimDesc* __restric
     const int cnt = w.b * d.nx;
     // four cells per thread per pass: all twelve loads in flight before the stores
     for (int b0 = threadIdx.x; b0 < cnt; b0 += 4 * blockDim.x) {
-        double v[4][3];
+        T v[4][3];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int id = b0 + u * blockDim.x;
@@ -112,9 +152,10 @@ __global__ void __launch_bounds__(MM_THREADS) k_project(const SimDesc* __restric
             const int id = b0 + u * blockDim.x;
             if (id >= cnt) continue;
             const long long o = c0 + id;
-            const double inv = inv_norm<T>(v[u][0] * v[u][0] + v[u][1] * v[u][1] + v[u][2] * v[u][2]);
+            T r[3];
+            project_cell(v[u], r);
 #pragma unroll
-            for (int c = 0; c < 3; ++c) m[o + c * N] = (T)(v[u][c] * inv);
+            for (int c = 0; c < 3; ++c) m[o + c * N] = r[c];
         }
     }
 }
@@ -146,9 +187,27 @@ __device__ __forceinline__ double total_energy(const SimState& S) {
     return S.E[0] + S.E[1] + S.E[2] + S.E[3] + S.E[4] + S.E[5];
 }
 
+// Block sum of per-thread compensated sums: warp sums in the context
+// precision (float-float for FP32), the cross-warp sum in FP64.  Result in
+// thread 0.
+template <typename T>
+__device__ __forceinline__ double block_csum(CSum<T> v, double* red) {
+    v.warp_reduce();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[wid] = v.value();
+    __syncthreads();
+    double r = 0.0;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r += red[i];
+    }
+    return r;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(MM_THREADS) k_neb_tangent(NebParams<T> p) {
     __shared__ double red[MM_THREADS / 32];
+    __shared__ T wsh[2];
     const WorkItem w = p.items[blockIdx.x];
     SimState* st = p.state;
     if (st[w.sim].status != 0) return;
@@ -157,28 +216,34 @@ __global__ void __launch_bounds__(MM_THREADS) k_neb_tangent(NebParams<T> p) {
     const int N = d.ncells;
     const bool free_img = i > 0 && i < n - 1;
     const bool has_next = i < n - 1;
-    double wp = 0.0, wm = 0.0;                   // tau = wp * tau+ + wm * tau-
-    if (free_img) {
-        const double Ep = total_energy(st[w.sim + 1]), E0 = total_energy(st[w.sim]),
-                     Em = total_energy(st[w.sim - 1]);
-        if (Ep > E0 && E0 > Em) { wp = 1.0; wm = 0.0; }
-        else if (Ep < E0 && E0 < Em) { wp = 0.0; wm = 1.0; }
-        else {
-            const double dmax = fmax(fabs(Ep - E0), fabs(Em - E0));
-            const double dmin = fmin(fabs(Ep - E0), fabs(Em - E0));
-            if (Ep > Em) { wp = dmax; wm = dmin; } else { wp = dmin; wm = dmax; }
+    if (threadIdx.x == 0) {
+        // tau = wp * tau+ + wm * tau- (energy-weighted upwind tangent), in FP64 once per CTA
+        double wp = 0.0, wm = 0.0;
+        if (free_img) {
+            const double Ep = total_energy(st[w.sim + 1]), E0 = total_energy(st[w.sim]),
+                         Em = total_energy(st[w.sim - 1]);
+            if (Ep > E0 && E0 > Em) { wp = 1.0; wm = 0.0; }
+            else if (Ep < E0 && E0 < Em) { wp = 0.0; wm = 1.0; }
+            else {
+                const double dmax = fmax(fabs(Ep - E0), fabs(Em - E0));
+                const double dmin = fmin(fabs(Ep - E0), fabs(Em - E0));
+                if (Ep > Em) { wp = dmax; wm = dmin; } else { wp = dmin; wm = dmax; }
+            }
+            // only the direction of tau matters (it is normalised per image): scale the
+            // weights to <= 1 so the per-cell products stay in range in FP32
+            const double wn = fmax(wp, wm);
+            if (wn > 0.0) { wp /= wn; wm /= wn; }
         }
-        // only the direction of tau matters (it is normalised per image): scale the
-        // weights to <= 1 so the per-cell products stay in range in FP32
-        const double wn = fmax(wp, wm);
-        if (wn > 0.0) { wp /= wn; wm /= wn; }
+        wsh[0] = (T)wp;
+        wsh[1] = (T)wm;
     }
+    __syncthreads();
     const long long off = d.off;
     const long long offn = has_next ? p.desc[w.sim + 1].off : off;
     const long long offp = free_img ? p.desc[w.sim - 1].off : off;
-    // per-cell geometry in the context precision, sums in FP64
-    double t2 = 0.0, ht = 0.0, th2 = 0.0;
-    const T wpt = (T)wp, wmt = (T)wm;
+    // per-cell geometry in the context precision, compensated per-thread sums, FP64 across threads
+    CSum<T> t2, ht, th2;
+    const T wpt = wsh[0], wmt = wsh[1];
     const long long c0 = (long long)w.a * d.nx;
     const int cnt = w.b * d.nx;
     for (int id = threadIdx.x; id < cnt; id += blockDim.x) {
@@ -194,7 +259,7 @@ __global__ void __launch_bounds__(MM_THREADS) k_neb_tangent(NebParams<T> p) {
             const T cx = m[1] * mn[2] - m[2] * mn[1], cy = m[2] * mn[0] - m[0] * mn[2],
                     cz = m[0] * mn[1] - m[1] * mn[0];
             const T th = atan2(sqrt(cx * cx + cy * cy + cz * cz), m[0] * mn[0] + m[1] * mn[1] + m[2] * mn[2]);
-            th2 += (double)(th * th);
+            th2.add(th * th);
         }
         if (free_img) {
             T t[3];
@@ -210,21 +275,22 @@ __global__ void __launch_bounds__(MM_THREADS) k_neb_tangent(NebParams<T> p) {
                 tt += t[c] * t[c];
                 htc += p.heff[off + c * (long long)N + cell] * t[c];
             }
-            t2 += (double)tt;
-            ht += (double)htc;
+            t2.add(tt);
+            ht.add(htc);
         }
     }
-    const double s0 = block_sum(t2, red);
+    const double s0 = block_csum(t2, red);
     if (threadIdx.x == 0) atomicAdd(&st[w.sim].neb[0], s0);
-    const double s1 = block_sum(ht, red);
+    const double s1 = block_csum(ht, red);
     if (threadIdx.x == 0) atomicAdd(&st[w.sim].neb[1], s1);
-    const double s2 = block_sum(th2, red);
+    const double s2 = block_csum(th2, red);
     if (threadIdx.x == 0) atomicAdd(&st[w.sim].neb[2], s2);
 }
 
 template <typename T>
 __global__ void __launch_bounds__(MM_THREADS) k_neb_force(NebParams<T> p) {
     __shared__ unsigned long long red[MM_THREADS / 32];
+    __shared__ T fsh[3];
     const WorkItem w = p.items[blockIdx.x];
     SimState* st = p.state;
     if (st[w.sim].status != 0) return;
@@ -233,19 +299,25 @@ __global__ void __launch_bounds__(MM_THREADS) k_neb_force(NebParams<T> p) {
     const int N = d.ncells;
     const bool free_img = i > 0 && i < n - 1;
     const bool msarr = (d.flags & F_MSARR) != 0;
-    const double agt = d.alpha * d.gamma / (1.0 + d.alpha * d.alpha);
-    double inv_t = 0.0, Ht = 0.0, spring = 0.0;
-    if (free_img) {
-        const double t2 = st[w.sim].neb[0];
-        inv_t = t2 > 0.0 ? 1.0 / sqrt(t2) : 0.0;
-        Ht = st[w.sim].neb[1] * inv_t;
-        spring = d.k_spring * (sqrt(st[w.sim].neb[2]) - sqrt(st[w.sim - 1].neb[2]));
+    if (threadIdx.x == 0) {
+        // 1/|tau|, H.tau/|tau| and the spring term k (L+ - L-) in FP64 once per CTA
+        double inv_t = 0.0, Ht = 0.0, spring = 0.0;
+        if (free_img) {
+            const double t2 = st[w.sim].neb[0];
+            inv_t = t2 > 0.0 ? 1.0 / sqrt(t2) : 0.0;
+            Ht = st[w.sim].neb[1] * inv_t;
+            spring = d.k_spring * (sqrt(st[w.sim].neb[2]) - sqrt(st[w.sim - 1].neb[2]));
+        }
+        fsh[0] = (T)inv_t;
+        fsh[1] = (T)Ht;
+        fsh[2] = (T)spring;
     }
-    const double hstep = st[w.sim].h;
+    __syncthreads();
     const long long off = d.off;
     const long long c0 = (long long)w.a * d.nx;
     const int cnt = w.b * d.nx;
-    const T inv_tt = (T)inv_t, Htt = (T)Ht, springt = (T)spring, agtt = (T)agt;
+    const T inv_tt = fsh[0], Htt = fsh[1], springt = fsh[2], agtt = coef<T>(d).agt;
+    const T e7 = (T)p.e7;
     unsigned long long vmax = 0ull;
     for (int id = threadIdx.x; id < cnt; id += blockDim.x) {
         const long long cell = c0 + id;
@@ -268,19 +340,22 @@ __global__ void __launch_bounds__(MM_THREADS) k_neb_force(NebParams<T> p) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) p.kout[off + c * (long long)N + cell] = k[c];
         if (p.stage == 1) {
-            const double v = (double)(k[0] * k[0] + k[1] * k[1] + k[2] * k[2]);      // squared norm
-            vmax = umax64(vmax, (unsigned long long)__double_as_longlong(v));
+            vmax = umax64(vmax, obits(k[0] * k[0] + k[1] * k[1] + k[2] * k[2]));      // squared norm
         } else if (p.stage == 7) {
+            // e_7 k_7 added to the prologue's partial sum in one FMA; h after the max
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const double v = fabs(hstep * ((double)p.errp[off + c * (long long)N + cell] + p.e7 * (double)k[c]));
-                vmax = umax64(vmax, (unsigned long long)__double_as_longlong(v));
-            }
+            for (int c = 0; c < 3; ++c)
+                vmax = umax64(vmax, obits(fabs(fma(e7, k[c], p.errp[off + c * (long long)N + cell]))));
         }
     }
     if (p.stage == 1 || p.stage == 7) {
         const unsigned long long r = block_max_u64(vmax, red);
-        if (threadIdx.x == 0) atomicMax(p.stage == 1 ? &st[w.sim].maxk_bits : &st[w.sim].err_bits, r);
+        if (threadIdx.x == 0) {
+            const double v = obits_to_double<T>(r);
+            const double vs = p.stage == 7 ? fabs(st[w.sim].h * v) : v;
+            atomicMax(p.stage == 1 ? &st[w.sim].maxk_bits : &st[w.sim].err_bits,
+                      (unsigned long long)__double_as_longlong(vs));
+        }
     }
 }
 

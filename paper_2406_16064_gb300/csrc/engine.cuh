@@ -77,8 +77,9 @@ void launch_newell_octant(cudaStream_t s, int nx, int ny, int nz, double dx, dou
 void launch_newell_place(cudaStream_t s, const double* oct, int c, int nx, int ny, int nz, int Px, int Py, int Pz,
                          void* buf);
 void launch_fft_axis_f64(cudaStream_t s, void* buf, int Px, int Py, int Pz, int axis, const void* twd);
+// Ty > 0: the blocked layout of the cluster-fused y/z pass with qp values per bin
 void launch_newell_extract(cudaStream_t s, const void* buf, int c, int Px, int Py, int Kx, int Pyh, int Pzh,
-                           double scale, void* out, int is_f32, unsigned long long* maxim,
+                           double scale, void* out, int is_f32, int Ty, int qp, unsigned long long* maxim,
                            unsigned long long* maxre);
 
 }  // namespace mm

@@ -11,7 +11,9 @@
 //          ncomp = 6 (xx yy zz xy xz yz) or 4 when Pz == 1 (xz = yz = 0),
 //          holding -N^(k)/(Px Py Pz); other bins follow from the parities
 //          of the Newell tensor (diagonal even, xy odd in kx and ky, xz odd
-//          in kx and kz, yz odd in ky and kz).
+//          in kx and kz, yz odd in ky and kz).  Geometries of the cluster-fused
+//          y/z pass store it blocked instead: [NBx][Py/2+1][Ty][yzc_qp(Pz)],
+//          entry 6 kz + c, so one column's values for one ky are contiguous.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -28,7 +30,26 @@ constexpr int MM_XTHREADS_MAX = sizeof(T) == 4 ? 1024 : 512;
 #define MM_CHECKED 0
 #endif
 
-enum { F_DEMAG = 1, F_DMI = 2, F_PREC = 4, F_MSARR = 8 };
+// F_DMI: interfacial DMI with D != 0; F_EX / F_UNI / F_CUB: A, Ku, Kc != 0.
+enum { F_DEMAG = 1, F_DMI = 2, F_PREC = 4, F_MSARR = 8, F_EX = 16, F_UNI = 32, F_CUB = 64 };
+
+// Coefficients of the local fields and of the LL torque of one simulation in
+// one precision, computed once on the host (plan_coefficients).  GB300 runs
+// FP64 at a small fraction of its FP32 rate, so the kernels of an FP32
+// context read these instead of dividing and converting FP64 material
+// parameters in every thread.
+template <typename T>
+struct Coef {
+    T Ms;                // uniform saturation magnetisation
+    T mu0;
+    T inv_u;             // 1 / (mu0 Ms) for uniform Ms (0 when Ms = 0)
+    T ex[3];             // 1/dx^2, 1/dy^2, 1/dz^2
+    T dm[2];             // 1/dx, 1/dy
+    T cA, cD, cK, cC;    // 2A, D, 2Ku, 4Kc
+    T u[3], H[3];
+    T gt, agt;           // gamma/(1+alpha^2), alpha gamma/(1+alpha^2)
+    T pad;
+};
 
 struct SimDesc {
     int nx, ny, nz, ncells;
@@ -52,7 +73,13 @@ struct SimDesc {
     double Ms, A, D, Ku, u[3], Kc, H[3], alpha, gamma;
     double dx, dy, dz;
     double k_spring;
+    Coef<double> cd;         // the coefficients in FP64 and in FP32
+    Coef<float> cf;
 };
+
+template <typename T> __host__ __device__ __forceinline__ const Coef<T>& coef(const SimDesc& d);
+template <> __host__ __device__ __forceinline__ const Coef<double>& coef<double>(const SimDesc& d) { return d.cd; }
+template <> __host__ __device__ __forceinline__ const Coef<float>& coef<float>(const SimDesc& d) { return d.cf; }
 
 struct SimState {
     double t, h, t_end, rtol, max_dmdt;
@@ -66,6 +93,11 @@ struct SimState {
 };
 
 struct WorkItem { int sim, a, b, c; };
+
+// Tensor values per (kx, ky) bin in the blocked layout of the cluster-fused
+// y/z pass: the 6 components of the Pz/2+1 kz bins, padded to a multiple of 4
+// for 16-byte vector loads.
+__host__ __device__ constexpr int yzc_qp(int Pz) { return ((6 * (Pz / 2 + 1) + 3) / 4) * 4; }
 
 template <typename T> struct alignas(2 * sizeof(T)) V2 { T x, y; };
 
@@ -394,3 +426,65 @@ struct PassParams {
 };
 
 __device__ __forceinline__ double bits_to_double(unsigned long long b) { return __longlong_as_double((long long)b); }
+
+// Ordered bits of a non-negative value in the context precision: for v >= 0
+// (and NaN, which compares above +inf) integer order is value order, so a max
+// over bits is exact and lets a NaN win.  obits_to_double converts a maximum
+// back to FP64 once per CTA.
+__device__ __forceinline__ unsigned long long obits(float v) { return (unsigned long long)__float_as_uint(v); }
+__device__ __forceinline__ unsigned long long obits(double v) { return (unsigned long long)__double_as_longlong(v); }
+template <typename T> __device__ __forceinline__ double obits_to_double(unsigned long long b);
+template <> __device__ __forceinline__ double obits_to_double<float>(unsigned long long b) {
+    return (double)__uint_as_float((unsigned)b);
+}
+template <> __device__ __forceinline__ double obits_to_double<double>(unsigned long long b) {
+    return __longlong_as_double((long long)b);
+}
+
+// Error-free transformations (Knuth's TwoSum, Dekker's product through an
+// FMA): a + b = s + e and a * b = p + e exactly in binary floating point.
+// The _rn intrinsics keep the compiler from contracting or reordering them.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+    p = __fmul_rn(a, b);
+    e = __fmaf_rn(a, b, -p);
+}
+
+// Per-thread sum with FP64-level accuracy: an FP32 context accumulates a
+// compensated (float-float) sum with FP32 operations, an FP64 context a plain
+// FP64 sum; value() is the FP64 total handed to the FP64 block reduction.
+template <typename T> struct CSum;
+template <> struct CSum<float> {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float v) {
+        float t, e;
+        two_sum(s, v, t, e);
+        s = t;
+        c = __fadd_rn(c, e);
+    }
+    // sum over the warp (float-float additions), result in every lane
+    __device__ __forceinline__ void warp_reduce() {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float so = __shfl_xor_sync(0xffffffffu, s, o), co = __shfl_xor_sync(0xffffffffu, c, o);
+            float t, e;
+            two_sum(s, so, t, e);
+            s = t;
+            c = __fadd_rn(__fadd_rn(c, co), e);
+        }
+    }
+    __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+template <> struct CSum<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double v) { s += v; }
+    __device__ __forceinline__ void warp_reduce() {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    }
+    __device__ __forceinline__ double value() const { return s; }
+};

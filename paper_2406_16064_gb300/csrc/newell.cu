@@ -222,7 +222,7 @@ __global__ void k_fft_axis_f64(double2* buf, int Px, int Py, int Pz, int axis, i
 // out[c][kzh][kyh][kx] = -Re(buf[kzh][kyh][kx]) * scale; tracks max |Im| / max |Re|
 template <typename T>
 __global__ void k_newell_extract(const double2* __restrict__ buf, int c, int Px, int Py, int Kx, int Pyh,
-                                 int Pzh, double scale, T* out, unsigned long long* maxim,
+                                 int Pzh, double scale, T* out, int Ty, int qp, unsigned long long* maxim,
                                  unsigned long long* maxre) {
     const long long tot = (long long)Kx * Pyh * Pzh;
     for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < tot;
@@ -231,16 +231,19 @@ __global__ void k_newell_extract(const double2* __restrict__ buf, int c, int Px,
         const int ky = (int)((id / Kx) % Pyh);
         const int kz = (int)(id / ((long long)Kx * Pyh));
         const double2 v = buf[((long long)kz * Py + ky) * Px + kx];
-        out[(long long)c * tot + id] = (T)(-v.x * scale);
+        // standard [c][kz][ky][kx]; blocked (Ty > 0) [kx / Ty][ky][kx % Ty][6 kz + c]
+        const long long o = Ty > 0 ? (((long long)(kx / Ty) * Pyh + ky) * Ty + kx % Ty) * qp + 6 * kz + c
+                                   : (long long)c * tot + id;
+        out[o] = (T)(-v.x * scale);
         atomicMax(maxim, (unsigned long long)__double_as_longlong(fabs(v.y)));
         atomicMax(maxre, (unsigned long long)__double_as_longlong(fabs(v.x)));
     }
 }
 
 template __global__ void k_newell_extract<float>(const double2*, int, int, int, int, int, int, double, float*,
-                                                  unsigned long long*, unsigned long long*);
+                                                  int, int, unsigned long long*, unsigned long long*);
 template __global__ void k_newell_extract<double>(const double2*, int, int, int, int, int, int, double, double*,
-                                                   unsigned long long*, unsigned long long*);
+                                                   int, int, unsigned long long*, unsigned long long*);
 
 // twiddle tables exp(-2 pi i k / LMAX)
 __global__ void k_twiddles(V2<double>* twd, V2<float>* twf) {
@@ -333,17 +336,17 @@ void launch_fft_axis_f64(cudaStream_t s, void* buf, int Px, int Py, int Pz, int 
 }
 
 void launch_newell_extract(cudaStream_t s, const void* buf, int c, int Px, int Py, int Kx, int Pyh, int Pzh,
-                           double scale, void* out, int is_f32, unsigned long long* maxim,
+                           double scale, void* out, int is_f32, int Ty, int qp, unsigned long long* maxim,
                            unsigned long long* maxre) {
     const long long n = (long long)Kx * Pyh * Pzh;
     const long long blocks = (n + 255) / 256;
     const int g = (int)(blocks < 1048576 ? blocks : 1048576);
     if (is_f32)
         k_newell_extract<float><<<g, 256, 0, s>>>(reinterpret_cast<const double2*>(buf), c, Px, Py, Kx, Pyh, Pzh,
-                                                   scale, reinterpret_cast<float*>(out), maxim, maxre);
+                                                   scale, reinterpret_cast<float*>(out), Ty, qp, maxim, maxre);
     else
         k_newell_extract<double><<<g, 256, 0, s>>>(reinterpret_cast<const double2*>(buf), c, Px, Py, Kx, Pyh, Pzh,
-                                                    scale, reinterpret_cast<double*>(out), maxim, maxre);
+                                                    scale, reinterpret_cast<double*>(out), Ty, qp, maxim, maxre);
 }
 
 }  // namespace mm

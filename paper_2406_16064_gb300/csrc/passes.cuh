@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(MM_XTHREADS_MAX<T>, 1) k_xfwd(PassParams<T> p)
                     }
                 }
                 if (demag) {
-                    const T ms = msarr ? msp[cell] : (T)d.Ms;
+                    const T ms = msarr ? msp[cell] : coef<T>(d).Ms;
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
                         if (h2 == 0) val[c].x = ms * yv[c]; else val[c].y = ms * yv[c];
@@ -330,18 +330,47 @@ __global__ void __launch_bounds__(MM_XTHREADS_MAX<T>, 1) k_zcol(PassParams<T> p)
 }
 
 // ------------------------------------------------ y + z fused, cluster per block
+// QP tensor values of one (column, ky) bin of the blocked layout, as 16-byte loads
+template <int QP>
+__device__ __forceinline__ void load_bin(const float* __restrict__ q, float (&v)[QP]) {
+    const float4* q4 = reinterpret_cast<const float4*>(q);
+#pragma unroll
+    for (int i = 0; i < QP / 4; ++i) {
+        const float4 t = __ldg(q4 + i);
+        v[4 * i] = t.x; v[4 * i + 1] = t.y; v[4 * i + 2] = t.z; v[4 * i + 3] = t.w;
+    }
+}
+template <int QP>
+__device__ __forceinline__ void load_bin(const double* __restrict__ q, double (&v)[QP]) {
+    const double2* q2 = reinterpret_cast<const double2*>(q);
+#pragma unroll
+    for (int i = 0; i < QP / 2; ++i) {
+        const double2 t = __ldg(q2 + i);
+        v[2 * i] = t.x; v[2 * i + 1] = t.y;
+    }
+}
+
 template <typename T, int PZ>
 __device__ void yzc_zstep(const PassParams<T>& p, const SimDesc& d, V2<T>* const (&rem)[8], int rank, int nz,
-                          int es, int kx0, int ncols) {
+                          int es, int b, int ncols) {
+    constexpr int QP = yzc_qp(PZ);
     const int TT = d.Ty, lT = d.lTy, Py = d.Py;
     const int ky_lo = (int)(((long long)rank * Py) / nz);    // share of rows
     const int ky_hi = (int)(((long long)(rank + 1) * Py) / nz);
     const int nwork = (ky_hi - ky_lo) << lT;
+    const T* __restrict__ tb = p.tensor + d.tens_off + (long long)b * d.Pyh * TT * QP;
     for (int id = threadIdx.x; id < nwork; id += blockDim.x) {
         const int col = id & (TT - 1);
         const int r = ky_lo + (id >> lT);              // row of the bit-reversed y spectrum
         const int ky = bitrev(r, d.lPy);
         if (col >= ncols) continue;
+        // tensor of bin (kx0 + col, ky): H = T M per kz; the ky fold (kyh = Py - ky,
+        // xy and yz odd in ky) is per item, the kz fold compile time
+        const bool fy = ky > (Py >> 1);
+        const int kyh = fy ? Py - ky : ky;
+        const T sy = fy ? (T)-1 : (T)1;
+        T tv[QP];
+        load_bin<QP>(tb + ((long long)kyh * TT + col) * QP, tv);
         V2<T> X[3][PZ];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -358,26 +387,17 @@ __device__ void yzc_zstep(const PassParams<T>& p, const SimDesc& d, V2<T>* const
         }
 #pragma unroll
         for (int c = 0; c < 3; ++c) reg_fft<T, PZ, false>(X[c], p.tw);
-        {
-            // H = T M per kz; the ky fold is hoisted, the kz fold is compile time
-            const bool fy = ky > (Py >> 1);
-            const int kyh = fy ? Py - ky : ky;
-            const T sy = fy ? (T)-1 : (T)1;
-            const long long PS = (long long)d.Pyh * d.Kx;            // kz-plane stride
-            const long long CS = (long long)d.Pzh * PS;              // component stride
-            const T* tb = p.tensor + d.tens_off + (long long)kyh * d.Kx + kx0 + col;
 #pragma unroll
-            for (int kz = 0; kz < PZ; ++kz) {
-                const int kzh = kz <= PZ / 2 ? kz : PZ - kz;
-                const T sz = kz <= PZ / 2 ? (T)1 : (T)-1;
-                const T* t = tb + kzh * PS;
-                const T xx = t[0], yy = t[CS], zz = t[2 * CS];
-                const T xy = sy * t[3 * CS], xz = sz * t[4 * CS], yz = sy * sz * t[5 * CS];
-                const V2<T> a = X[0][kz], b = X[1][kz], c = X[2][kz];
-                X[0][kz] = mk<T>(xx * a.x + xy * b.x + xz * c.x, xx * a.y + xy * b.y + xz * c.y);
-                X[1][kz] = mk<T>(xy * a.x + yy * b.x + yz * c.x, xy * a.y + yy * b.y + yz * c.y);
-                X[2][kz] = mk<T>(xz * a.x + yz * b.x + zz * c.x, xz * a.y + yz * b.y + zz * c.y);
-            }
+        for (int kz = 0; kz < PZ; ++kz) {
+            const int kzh = kz <= PZ / 2 ? kz : PZ - kz;
+            const T sz = kz <= PZ / 2 ? (T)1 : (T)-1;
+            const T* t = tv + 6 * kzh;
+            const T xx = t[0], yy = t[1], zz = t[2];
+            const T xy = sy * t[3], xz = sz * t[4], yz = sy * sz * t[5];
+            const V2<T> a = X[0][kz], bb = X[1][kz], c = X[2][kz];
+            X[0][kz] = mk<T>(xx * a.x + xy * bb.x + xz * c.x, xx * a.y + xy * bb.y + xz * c.y);
+            X[1][kz] = mk<T>(xy * a.x + yy * bb.x + yz * c.x, xy * a.y + yy * bb.y + yz * c.y);
+            X[2][kz] = mk<T>(xz * a.x + yz * bb.x + zz * c.x, xz * a.y + yz * bb.y + zz * c.y);
         }
 #pragma unroll
         for (int c = 0; c < 3; ++c) reg_fft<T, PZ, true>(X[c], p.tw);
@@ -437,7 +457,7 @@ __global__ void __launch_bounds__(MM_THREADS, sizeof(T) == 4 ? 2 : 1) k_yzc(Pass
     V2<T>* rem[8];
 #pragma unroll
     for (int zz = 0; zz < 8; ++zz) rem[zz] = zz < nz ? cl.map_shared_rank(sm, zz) : sm;
-    yzc_zstep<T, PZ>(p, d, rem, rank, nz, es, kx0, ncols);   // PZ == d.Pz, fixed by nz per launch
+    yzc_zstep<T, PZ>(p, d, rem, rank, nz, es, b, ncols);   // PZ == d.Pz, fixed by nz per launch
     cl.sync();                                  // every row back in its owner's plane
     fft_dit<T, true>(sm, lL, es, 1, es, p.tw);    // bit-reversed in, natural out
 #pragma unroll
@@ -464,20 +484,6 @@ __device__ __forceinline__ unsigned long long block_max_u64(unsigned long long v
     unsigned long long r = 0;
     if (threadIdx.x == 0) {
         for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r = umax64(r, red[i]);
-    }
-    return r;
-}
-
-__device__ __forceinline__ double block_sum(double v, double* red) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0) red[wid] = v;
-    __syncthreads();
-    double r = 0.0;
-    if (threadIdx.x == 0) {
-        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r += red[i];
     }
     return r;
 }
@@ -558,37 +564,36 @@ __global__ void __launch_bounds__(MM_XTHREADS_MAX<T>, 1) k_xinv(PassParams<T> p,
         Hd = stockham_fft<T, true, (sizeof(T) == 4 ? 4 : 3)>(bufB, bufA, lLh, nseq, SK, p.tw);
     }
 
-    // per-cell local fields and torque
-    const T mu0 = (T)kMu0;
-    const T inv_u = d.Ms > 0.0 ? (T)(1.0 / (kMu0 * d.Ms)) : (T)0;   // 1/(mu0 Ms) for uniform Ms
-    const T ex_x = (T)(1.0 / (d.dx * d.dx)), ex_y = (T)(1.0 / (d.dy * d.dy)), ex_z = (T)(1.0 / (d.dz * d.dz));
-    const T dm_x = (T)(1.0 / d.dx), dm_y = (T)(1.0 / d.dy);
-    const T cA = (T)(2.0 * d.A), cD = (T)d.D, cK = (T)(2.0 * d.Ku), cC = (T)(4.0 * d.Kc);
-    const T ux = (T)d.u[0], uy = (T)d.u[1], uz = (T)d.u[2];
-    const T Hx0 = (T)d.H[0], Hy0 = (T)d.H[1], Hz0 = (T)d.H[2];
-    const T gt = (T)(d.gamma / (1.0 + d.alpha * d.alpha));
-    const T agt = (T)(d.alpha * d.gamma / (1.0 + d.alpha * d.alpha));
+    // per-cell local fields and torque; coefficients precomputed in the context
+    // precision (no FP64 arithmetic per thread in an FP32 context)
+    const Coef<T>& cf = coef<T>(d);
+    const T mu0 = cf.mu0, inv_u = cf.inv_u;
+    const T ex_x = cf.ex[0], ex_y = cf.ex[1], ex_z = cf.ex[2];
+    const T dm_x = cf.dm[0], dm_y = cf.dm[1];
+    const T cA = cf.cA, cD = cf.cD, cK = cf.cK, cC = cf.cC;
+    const T ux = cf.u[0], uy = cf.u[1], uz = cf.u[2];
+    const T Hx0 = cf.H[0], Hy0 = cf.H[1], Hz0 = cf.H[2];
+    const T gt = cf.gt, agt = cf.agt, Msu = cf.Ms;
     const bool prec = (d.flags & F_PREC) != 0;
-    const bool dmi = (d.flags & F_DMI) != 0 && d.D != 0.0;
-    const bool do_ex = d.A != 0.0, do_uni = d.Ku != 0.0, do_cub = d.Kc != 0.0;
+    const bool dmi = (d.flags & F_DMI) != 0;
+    const bool do_ex = (d.flags & F_EX) != 0, do_uni = (d.flags & F_UNI) != 0, do_cub = (d.flags & F_CUB) != 0;
     const bool write_k = !ENERGY;
     const T* __restrict__ m0p = ys + tile;
     const T* __restrict__ m1p = m0p + N;
     const T* __restrict__ m2p = m1p + N;
     const int sz = nx * ny;
     const T* __restrict__ msp = msarr ? p.Ms + d.ms_off + (long long)row0 * nx : nullptr;
-    const double hstep = (p.mode == MODE_RK) ? p.state[w.sim].h : 0.0;
-    const double e7 = p.e[6];
+    const T e7 = (T)dp_e(6);
     const bool red1 = !ENERGY && p.mode == MODE_RK && p.stage == 1;
     const bool red7 = !ENERGY && p.mode == MODE_RK && p.stage == 7;
     unsigned long long vmax = 0ull;
-    double esum[6] = {0, 0, 0, 0, 0, 0};
+    CSum<T> esum[6];
     for (int r = 0; r < nrows; ++r) {
         const int y = y0 + r, z = z0;
         for (int x = threadIdx.x; x < nx; x += blockDim.x) {
             const int cell = r * nx + x;                     // within the tile
             const T m0 = m0p[cell], m1 = m1p[cell], m2 = m2p[cell];
-            const T ms = msarr ? msp[cell] : (T)d.Ms;
+            const T ms = msarr ? msp[cell] : Msu;
             T H0 = 0, H1 = 0, H2 = 0, k0 = 0, k1 = 0, k2 = 0;
             if (ms > (T)0) {
                 const T inv = msarr ? (T)1 / (mu0 * ms) : inv_u;
@@ -653,16 +658,17 @@ __global__ void __launch_bounds__(MM_XTHREADS_MAX<T>, 1) k_xinv(PassParams<T> p,
                 H1 = hd1 + ex1 + dm1 + un1 + cu1 + Hy0;
                 H2 = hd2 + ex2 + dm2 + un2 + cu2 + Hz0;
                 if (ENERGY) {
-                    // per-cell densities in the context precision, summed in FP64; the
-                    // constant factors are applied once per CTA
-                    esum[0] += (double)(ms * (m0 * ex0 + m1 * ex1 + m2 * ex2));
-                    esum[1] += (double)(ms * (m0 * dm0 + m1 * dm1 + m2 * dm2));
+                    // per-cell densities in the context precision, accumulated per
+                    // thread with FP64-level accuracy (CSum) and summed across
+                    // threads in FP64; the constant factors are applied once per CTA
+                    esum[0].add(ms * (m0 * ex0 + m1 * ex1 + m2 * ex2));
+                    esum[1].add(ms * (m0 * dm0 + m1 * dm1 + m2 * dm2));
                     const T mu = m0 * ux + m1 * uy + m2 * uz;
-                    esum[2] += (double)(mu * mu);
+                    esum[2].add(mu * mu);
                     const T q0 = m0 * m0, q1 = m1 * m1, q2 = m2 * m2;
-                    esum[3] += (double)(q0 * q0 + q1 * q1 + q2 * q2);
-                    esum[4] += (double)(ms * (m0 * Hx0 + m1 * Hy0 + m2 * Hz0));
-                    esum[5] += (double)(ms * (m0 * hd0 + m1 * hd1 + m2 * hd2));
+                    esum[3].add(q0 * q0 + q1 * q1 + q2 * q2);
+                    esum[4].add(ms * (m0 * Hx0 + m1 * Hy0 + m2 * Hz0));
+                    esum[5].add(ms * (m0 * hd0 + m1 * hd1 + m2 * hd2));
                 }
                 // LL form: dm/dt = -g~ m x H - alpha g~ m x (m x H)
                 const T c0 = m1 * H2 - m2 * H1, c1 = m2 * H0 - m0 * H2, c2 = m0 * H1 - m1 * H0;
@@ -678,46 +684,49 @@ __global__ void __launch_bounds__(MM_XTHREADS_MAX<T>, 1) k_xinv(PassParams<T> p,
                 p.heff[o] = H0; p.heff[o + N] = H1; p.heff[o + 2 * N] = H2;
             }
             if (red1) {
-                // squared norm (FP32 is exact enough for a threshold / step-size
-                // estimate; the max is taken over ordered bits, sqrt once per simulation)
-                const double v = (double)(k0 * k0 + k1 * k1 + k2 * k2);
-                vmax = umax64(vmax, (unsigned long long)__double_as_longlong(v));
+                // squared norm |dm/dt|^2 (a threshold / step-size estimate); the max
+                // runs over ordered bits in the context precision, sqrt once per simulation
+                vmax = umax64(vmax, obits(k0 * k0 + k1 * k1 + k2 * k2));
             } else if (red7) {
+                // embedded error sum_j e_j k_j: e_1..e_6 part accumulated by the stage-7
+                // prologue, plus e_7 k_7 in one correctly rounded FMA; h is applied
+                // after the max (rounded scaling by h > 0 is monotone, so
+                // max_i h|v_i| = h max_i |v_i| exactly)
                 const T* ep = p.errp + o;
-                const double v0 = fabs(hstep * ((double)ep[0] + e7 * k0));
-                const double v1 = fabs(hstep * ((double)ep[N] + e7 * k1));
-                const double v2 = fabs(hstep * ((double)ep[2 * N] + e7 * k2));
-                vmax = umax64(vmax, (unsigned long long)__double_as_longlong(v0));
-                vmax = umax64(vmax, (unsigned long long)__double_as_longlong(v1));
-                vmax = umax64(vmax, (unsigned long long)__double_as_longlong(v2));
+                vmax = umax64(vmax, obits(fabs(fma(e7, k0, ep[0]))));
+                vmax = umax64(vmax, obits(fabs(fma(e7, k1, ep[N]))));
+                vmax = umax64(vmax, obits(fabs(fma(e7, k2, ep[2 * N]))));
             }
         }
     }
     if (red1 || red7) {
         const unsigned long long rr = block_max_u64(vmax, red_u);
-        if (threadIdx.x == 0) atomicMax(red1 ? &p.state[w.sim].maxk_bits : &p.state[w.sim].err_bits, rr);
+        if (threadIdx.x == 0) {
+            // FP64 from here on: the CTA maximum, scaled by h at stage 7
+            const double v = obits_to_double<T>(rr);
+            const double vs = red7 ? fabs(p.state[w.sim].h * v) : v;
+            atomicMax(red1 ? &p.state[w.sim].maxk_bits : &p.state[w.sim].err_bits,
+                      (unsigned long long)__double_as_longlong(vs));
+        }
     }
     if (ENERGY) {
-        // E_ex, E_dmi, E_d = -mu0/2 V sum Ms m.H;  E_zee = -mu0 V sum Ms m.H_ext;
-        // E_uni = -Ku V sum (m.u)^2;  E_cub = Kc V sum (mx^4 + my^4 + mz^4)
-        const double V = d.dx * d.dy * d.dz;
-        const double scale[6] = {-0.5 * kMu0 * V, -0.5 * kMu0 * V, -d.Ku * V, d.Kc * V, -kMu0 * V,
-                                 -0.5 * kMu0 * V};
         const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
-        for (int t = 0; t < 6; ++t) {
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) esum[t] += __shfl_xor_sync(0xffffffffu, esum[t], o);
-        }
+        for (int t = 0; t < 6; ++t) esum[t].warp_reduce();
         if (lane == 0) {
 #pragma unroll
-            for (int t = 0; t < 6; ++t) red_e[t * 32 + wid] = esum[t];
+            for (int t = 0; t < 6; ++t) red_e[t * 32 + wid] = esum[t].value();
         }
         __syncthreads();
         if (threadIdx.x < 6) {
+            // E_ex, E_dmi, E_d = -mu0/2 V sum Ms m.H;  E_zee = -mu0 V sum Ms m.H_ext;
+            // E_uni = -Ku V sum (m.u)^2;  E_cub = Kc V sum (mx^4 + my^4 + mz^4)
+            const double V = d.dx * d.dy * d.dz;
+            const int t = threadIdx.x;
+            const double scale = t == 2 ? -d.Ku * V : t == 3 ? d.Kc * V : t == 4 ? -kMu0 * V : -0.5 * kMu0 * V;
             double e = 0.0;
-            for (int i = 0; i < (int)(blockDim.x >> 5); ++i) e += red_e[threadIdx.x * 32 + i];
-            atomicAdd(&p.state[w.sim].E[threadIdx.x], e * scale[threadIdx.x]);
+            for (int i = 0; i < (int)(blockDim.x >> 5); ++i) e += red_e[t * 32 + i];
+            atomicAdd(&p.state[w.sim].E[t], e * scale);
         }
     }
 }

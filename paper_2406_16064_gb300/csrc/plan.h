@@ -59,6 +59,53 @@ inline void plan_geometry(SimDesc& d, bool f32) {
     d.NBx = (d.Kx + d.Ty - 1) >> d.lTy;
 }
 
+template <typename T>
+inline void plan_fill_coef(Coef<T>& c, const SimDesc& d) {
+    const double mu0 = 4e-7 * 3.14159265358979323846;
+    c.Ms = (T)d.Ms;
+    c.mu0 = (T)mu0;
+    c.inv_u = d.Ms > 0.0 ? (T)(1.0 / (mu0 * d.Ms)) : (T)0;
+    c.ex[0] = (T)(1.0 / (d.dx * d.dx));
+    c.ex[1] = (T)(1.0 / (d.dy * d.dy));
+    c.ex[2] = (T)(1.0 / (d.dz * d.dz));
+    c.dm[0] = (T)(1.0 / d.dx);
+    c.dm[1] = (T)(1.0 / d.dy);
+    c.cA = (T)(2.0 * d.A);
+    c.cD = (T)d.D;
+    c.cK = (T)(2.0 * d.Ku);
+    c.cC = (T)(4.0 * d.Kc);
+    for (int i = 0; i < 3; ++i) { c.u[i] = (T)d.u[i]; c.H[i] = (T)d.H[i]; }
+    c.gt = (T)(d.gamma / (1.0 + d.alpha * d.alpha));
+    c.agt = (T)(d.alpha * d.gamma / (1.0 + d.alpha * d.alpha));
+    c.pad = (T)0;
+}
+
+// Derive the term flags and both coefficient sets of d from its FP64 material
+// parameters; call again after any parameter (the applied field) changes.
+// dmi_interfacial: the material's DMI kind is interfacial.
+inline void plan_coefficients(SimDesc& d, bool dmi_interfacial) {
+    d.flags &= ~(F_DMI | F_EX | F_UNI | F_CUB);
+    if (dmi_interfacial && d.D != 0.0) d.flags |= F_DMI;
+    if (d.A != 0.0) d.flags |= F_EX;
+    if (d.Ku != 0.0) d.flags |= F_UNI;
+    if (d.Kc != 0.0) d.flags |= F_CUB;
+    plan_fill_coef(d.cd, d);
+    plan_fill_coef(d.cf, d);
+}
+
+// Films with 2..kMaxClusterPlanes planes run the cluster-fused y/z pass, which
+// reads its tensor in a blocked layout (plan_tens_elems).
+inline bool plan_uses_yzc(const SimDesc& d) { return d.Pz > 1 && d.Py > 1 && d.nz <= kMaxClusterPlanes; }
+
+// Elements of a geometry's stored tensor:
+//   standard [ncomp][Pz/2+1][Py/2+1][Kx];
+//   blocked (cluster pass) [NBx][Py/2+1][Ty][qp], entry q = 6 kz + c, so the
+//   values one column of one ky row needs are contiguous.
+inline long long plan_tens_elems(const SimDesc& d) {
+    if (plan_uses_yzc(d)) return (long long)d.NBx * d.Pyh * d.Ty * yzc_qp(d.Pz);
+    return (long long)d.ncomp * d.Pzh * d.Pyh * d.Kx;
+}
+
 inline long long plan_spec_elems(const SimDesc& d) { return 3LL * d.nz * d.NBx * d.Py * d.Ty; }
 
 // x-inverse shared memory: two FFT buffers of 3*Rx padded rows.
@@ -79,7 +126,7 @@ inline void plan_items(const SimDesc& d, int sid, size_t vsz, PlanItems& P) {
     P.smem_x = std::max(P.smem_x, 2 * 3 * (size_t)d.Rx * padded_len(d.Kx) * vsz);
     P.smem_xi = std::max(P.smem_xi, plan_xinv_smem(d, vsz));
     if (!(d.flags & F_DEMAG)) return;
-    if (d.Pz > 1 && d.Py > 1 && d.nz <= kMaxClusterPlanes) {
+    if (plan_uses_yzc(d)) {
         for (int b = 0; b < d.NBx; ++b) P.yzc[d.nz].push_back({sid, 0, b, 0});
         P.smem_yzc = std::max(P.smem_yzc, 3 * (size_t)d.Py * d.Ty * vsz);
     } else if (d.Pz > 1) {

@@ -102,8 +102,8 @@ extern "C" int mm_rhs_eval_static(const mm_mesh* mesh, const mm_material* mat, i
     d.Ms = mat->Ms; d.A = mat->A; d.D = mat->D; d.Ku = mat->Ku; d.Kc = mat->Kc;
     d.alpha = mat->alpha; d.gamma = mat->gamma;
     d.dx = mesh->dx; d.dy = mesh->dy; d.dz = mesh->dz;
-    d.flags = (mat->demag ? F_DEMAG : 0) | (mat->dmi_kind == MM_DMI_INTERFACIAL ? F_DMI : 0) |
-              (mat->precession ? F_PREC : 0);
+    d.flags = (mat->demag ? F_DEMAG : 0) | (mat->precession ? F_PREC : 0);
+    plan_coefficients(d, mat->dmi_kind == MM_DMI_INTERFACIAL);
     d.group_begin = d.group_end = -1;
     d.neb_index = -1;
     d.ms_off = -1;
@@ -132,7 +132,7 @@ extern "C" int mm_rhs_eval_static(const mm_mesh* mesh, const mm_material* mat, i
     const size_t o_z = cv.take(std::max<size_t>(1, P.z.size()) * sizeof(WorkItem));
     const size_t o_y2 = cv.take(std::max<size_t>(1, P.y2.size()) * sizeof(WorkItem));
     const size_t o_yz = cv.take(std::max<size_t>(1, yzv.size()) * sizeof(WorkItem));
-    const long long tens_elems = (long long)d.ncomp * d.Pzh * d.Pyh * d.Kx;
+    const long long tens_elems = plan_tens_elems(d);
     const long long spec_elems = demag ? plan_spec_elems(d) : 0;
     const size_t o_tens = cv.take(demag ? (size_t)tens_elems * e : 16);
     const size_t o_spec = cv.take(demag ? (size_t)spec_elems * vsz : 16);
@@ -169,11 +169,13 @@ extern "C" int mm_rhs_eval_static(const mm_mesh* mesh, const mm_material* mat, i
         launch_newell_octant(s, d.nx, d.ny, d.nz, d.dx, d.dy, d.dz, oct);
         const double scale = 1.0 / ((double)d.Px * d.Py * d.Pz);
         unsigned long long* diag = (unsigned long long*)(base + o_diag);
+        SCK(cudaMemsetAsync(base + o_tens, 0, (size_t)tens_elems * e, s));   // padding of a blocked tensor
+        const int Tyb = plan_uses_yzc(d) ? d.Ty : 0;
         for (int c = 0; c < d.ncomp; ++c) {
             launch_newell_place(s, oct, c, d.nx, d.ny, d.nz, d.Px, d.Py, d.Pz, fftbuf);
             for (int ax = 0; ax < 3; ++ax) launch_fft_axis_f64(s, fftbuf, d.Px, d.Py, d.Pz, ax, base + o_twd);
-            launch_newell_extract(s, fftbuf, c, d.Px, d.Py, d.Kx, d.Pyh, d.Pzh, scale, base + o_tens, f32, diag,
-                                  diag + 1);
+            launch_newell_extract(s, fftbuf, c, d.Px, d.Py, d.Kx, d.Pyh, d.Pzh, scale, base + o_tens, f32, Tyb,
+                                  yzc_qp(d.Pz), diag, diag + 1);
         }
         SCK(cudaGetLastError());
         unsigned long long hb[2];
