@@ -20,6 +20,7 @@ N as RHS cell-updates/s and as Heun-equivalent cells/s (RHS rate / 2).
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -81,7 +82,13 @@ def pad(n, min2=False):
 
 
 def kernel_bytes(w, e):
-    """Compulsory bytes per attempt of each kernel kind ('Roofline')."""
+    """Compulsory bytes per attempt of each kernel kind: every stage vector, state, spectrum
+    row and tensor value a kernel must read or write once (e = bytes of one real value).
+    The x forward pass of stage s reads y_n and the s-1 earlier k's, writes y_s (s > 1) and
+    the partial error vector (s = 7) and the x-transform rows; the column passes read and
+    write the spectrum and read the tensor; the x inverse reads the spectrum rows and the
+    stage state and writes k_s (and reads the partial error at s = 7); the projection reads
+    y and writes m."""
     out = {k: 0.0 for k in ("x_forward", "y_forward", "z_fused", "y_inverse", "y_fused",
                             "x_inverse_epilogue", "project", "yz_cluster")}
     for s in w.sims:
@@ -124,6 +131,40 @@ def step_bytes_survey(w, e):
         T = ncomp * e * (Kx * (Py // 2 + 1) * (Pz // 2 + 1)) / s.mesh.ncells if s.mat.demag else 0.0
         tot += (22.5 * e + T) * s.mesh.ncells * 7
     return tot
+
+
+# ------------------------------------------------------------------ ncu traffic
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic.md")
+
+
+def source_fingerprint():
+    """Hash of every kernel source file: DRAM counters taken on other sources are stale."""
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2406_16064_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        if fn.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, fn), "rb") as f:
+                h.update(fn.encode())
+                h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kind, workload_name):
+    """dram__bytes_read.sum + dram__bytes_write.sum per launch of a kernel kind on a
+    workload, from the committed ncu summary; None unless it was captured on the
+    current kernel sources."""
+    if not os.path.exists(TRAFFIC_FILE):
+        return None
+    fp = source_fingerprint()
+    with open(TRAFFIC_FILE) as f:
+        for line in f:
+            cells = [c.strip() for c in line.strip().strip("|").split("|")]
+            if len(cells) >= 5 and cells[0] == workload_name and cells[1] == kind and cells[3] == fp:
+                try:
+                    return float(cells[4])
+                except ValueError:
+                    return None
+    return None
 
 
 # ------------------------------------------------------------------ clocks
@@ -363,7 +404,8 @@ def run_gpu(args, rank, world, dist):
                          f"(state, 7 stage vectors, spectrum, tensor) vs 129 MB L2"},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm if achieved else None, "peak_kind": f"of {peak_kind}",
-                     "bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_launch_ms, "traffic": None,
+                     "bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_launch_ms,
+                     "traffic": recorded_traffic(dom, w.name), "source_fingerprint": source_fingerprint(),
                      "step_algorithmic_gbs": step_bytes / (step_ms / 1e3) / 1e9,
                      "step_frac": step_bytes / (step_ms / 1e3) / 1e9 / hbm},
         "kernels": rows,

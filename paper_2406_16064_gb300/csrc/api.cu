@@ -524,8 +524,8 @@ int mm_precompute_demag(mm_ctx* C) {
     if ((rc = dalloc(C, &C->tens, (size_t)C->tens_elems * C->esz))) return rc;
     CK(cudaMemsetAsync(C->tens, 0, (size_t)C->tens_elems * C->esz, C->stream));   // padding of blocked tensors
     if ((rc = dalloc(C, (void**)&C->oct, (size_t)C->oct_elems * 8))) return rc;
-    if ((rc = dalloc(C, &C->twd, (size_t)MM_LMAX * 16))) return rc;
-    if ((rc = dalloc(C, &C->twf, (size_t)MM_LMAX * 8))) return rc;
+    if ((rc = dalloc(C, &C->twd, (size_t)MM_TW_ENTRIES * 16))) return rc;
+    if ((rc = dalloc(C, &C->twf, (size_t)MM_TW_ENTRIES * 8))) return rc;
     if ((rc = dalloc(C, (void**)&C->kvec_dev, 7 * sizeof(void*)))) return rc;
     if ((rc = dalloc(C, (void**)&C->desc_d, C->sims.size() * sizeof(SimDesc)))) return rc;
     if ((rc = dalloc(C, (void**)&C->state_d, C->sims.size() * sizeof(SimState)))) return rc;

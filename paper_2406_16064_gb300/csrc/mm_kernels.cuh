@@ -126,6 +126,25 @@ __device__ __forceinline__ V2<T> twid(const V2<T>* __restrict__ tw, int k, int l
     return w;
 }
 
+// Stage twiddle tables, stored after the MM_LMAX-entry table: for radix
+// R = 2^LR (LR = 1..4) and length M = 2^lM (LR <= lM <= MM_LOG2_LMAX), the
+// values W_M^(k r) for r = 1..R-1 and k < M/R at stw_base(LR, lM) + (r-1) M/R + k.
+// Consecutive k are adjacent, so the butterflies of a warp read one contiguous
+// run per r (the MM_LMAX table, read at stride LMAX/M, puts every lane of a
+// warp on its own sector).  (LR = 1, lM) is W_M^k for k < M/2.
+__host__ __device__ constexpr int stw_size(int LR) { return ((1 << LR) - 1) * ((1 << (MM_LOG2_LMAX + 1 - LR)) - 1); }
+__host__ __device__ constexpr int stw_off(int LR) { return LR <= 1 ? 0 : stw_off(LR - 1) + stw_size(LR - 1); }
+__host__ __device__ constexpr int stw_base(int LR, int lM) { return stw_off(LR) + ((1 << LR) - 1) * ((1 << (lM - LR)) - 1); }
+#define MM_STW_ENTRIES (stw_off(5))
+#define MM_TW_ENTRIES (MM_LMAX + MM_STW_ENTRIES)
+
+template <typename T, bool INV>
+__device__ __forceinline__ V2<T> stw_get(const V2<T>* __restrict__ t, int i) {
+    V2<T> w = t[i];
+    if (INV) w.y = -w.y;
+    return w;
+}
+
 // Map a linear butterfly index to (sequence, group).  Sequences stored with
 // unit element stride are walked group-fastest; interleaved sequences
 // (element stride > 1) sequence-fastest, so a warp touches adjacent words.
@@ -206,13 +225,17 @@ __device__ __forceinline__ void reg_fft(V2<T> (&x)[PZ], const V2<T>* __restrict_
 // W_{Ns R}^{(j mod Ns) r}, does an R-point DFT in registers and writes
 // x'[(j / Ns) Ns R + (j mod Ns) + r Ns], Ns = 2^lNs the length already
 // transformed.  Natural order in, natural order out after the last stage.
-template <typename T, bool INV, int R>
+// ZIN (first stage only): the upper half of the input is zero and is not read.
+// HOUT (last stage only): only the lower half of the output is written.
+// tw points at the MM_LMAX table; the stage tables follow it.
+template <typename T, bool INV, int R, bool ZIN, bool HOUT>
 __device__ __forceinline__ void stockham_stage(const V2<T>* src, V2<T>* dst, int lL, int lNs, int nseq, int sstride,
                                                const V2<T>* __restrict__ tw) {
     constexpr int LR = Log2<R>::v;
     const int lnb = lL - LR;
     const int nb = 1 << lnb;
     const int tot = nseq << lnb;
+    const V2<T>* __restrict__ st = tw + MM_LMAX + stw_base(LR, lNs + LR);
     for (int id = threadIdx.x; id < tot; id += blockDim.x) {
         const int seq = id >> lnb, j = id & (nb - 1);
         const V2<T>* s = src + seq * sstride;
@@ -220,34 +243,53 @@ __device__ __forceinline__ void stockham_stage(const V2<T>* src, V2<T>* dst, int
         const int k = j & ((1 << lNs) - 1);
         V2<T> v[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = s[ix<true>(j + (r << lnb), 1)];
-        if (lNs > 0) {
+        for (int r = 0; r < R; ++r)
+            v[r] = (ZIN && r >= R / 2) ? mk<T>((T)0, (T)0) : s[ix<true>(j + (r << lnb), 1)];
+        if (!ZIN && lNs > 0) {
 #pragma unroll
-            for (int r = 1; r < R; ++r) v[r] = cmul(v[r], twid<T, INV>(tw, k * r, lNs + LR));
+            for (int r = 1; r < R; ++r) v[r] = cmul(v[r], stw_get<T, INV>(st, ((r - 1) << lNs) + k));
         }
         reg_fft<T, R, INV>(v, tw);
         const int o = ((j >> lNs) << (lNs + LR)) + k;
 #pragma unroll
-        for (int r = 0; r < R; ++r) d[ix<true>(o + (r << lNs), 1)] = v[r];
+        for (int r = 0; r < (HOUT ? R / 2 : R); ++r) d[ix<true>(o + (r << lNs), 1)] = v[r];
+    }
+}
+
+template <typename T, bool INV, int R, bool ZIN, bool HOUT>
+__device__ __forceinline__ void stockham_pick(const V2<T>* a, V2<T>* b, int lL, int lNs, int nseq, int sstride,
+                                              const V2<T>* __restrict__ tw, bool first, bool last) {
+    if (ZIN && first) {
+        if (HOUT && last) stockham_stage<T, INV, R, true, true>(a, b, lL, lNs, nseq, sstride, tw);
+        else stockham_stage<T, INV, R, true, false>(a, b, lL, lNs, nseq, sstride, tw);
+    } else {
+        if (HOUT && last) stockham_stage<T, INV, R, false, true>(a, b, lL, lNs, nseq, sstride, tw);
+        else stockham_stage<T, INV, R, false, false>(a, b, lL, lNs, nseq, sstride, tw);
     }
 }
 
 // Full unnormalised FFT of nseq padded sequences of length 2^lL (natural
 // order in and out) with Stockham stages of radix up to 2^MAXLR, ping-ponging
 // between a and b.  Returns the buffer that holds the result.  Ends with
-// __syncthreads().
-template <typename T, bool INV, int MAXLR>
+// __syncthreads().  ZIN: the upper half of every input sequence is zero (it
+// need not be stored); HOUT: only the lower half of the result is wanted
+// (the upper half is left undefined).
+template <typename T, bool INV, int MAXLR, bool ZIN = false, bool HOUT = false>
 __device__ V2<T>* stockham_fft(V2<T>* a, V2<T>* b, int lL, int nseq, int sstride, const V2<T>* __restrict__ tw) {
     int lNs = 0;
     while (lNs < lL) {
         const int rem = lL - lNs;
         int lr = rem < MAXLR ? rem : MAXLR;
         if (rem - lr == 1 && lr > 2) lr -= 1;          // avoid a trailing radix-2 stage
+        const bool first = lNs == 0, last = lNs + lr == lL;
         switch (lr) {
-            case 1: stockham_stage<T, INV, 2>(a, b, lL, lNs, nseq, sstride, tw); break;
-            case 2: stockham_stage<T, INV, 4>(a, b, lL, lNs, nseq, sstride, tw); break;
-            case 3: stockham_stage<T, INV, 8>(a, b, lL, lNs, nseq, sstride, tw); break;
-            default: stockham_stage<T, INV, (MAXLR >= 4 ? 16 : 8)>(a, b, lL, lNs, nseq, sstride, tw); break;
+            case 1: stockham_pick<T, INV, 2, ZIN, HOUT>(a, b, lL, lNs, nseq, sstride, tw, first, last); break;
+            case 2: stockham_pick<T, INV, 4, ZIN, HOUT>(a, b, lL, lNs, nseq, sstride, tw, first, last); break;
+            case 3: stockham_pick<T, INV, 8, ZIN, HOUT>(a, b, lL, lNs, nseq, sstride, tw, first, last); break;
+            default:
+                stockham_pick<T, INV, (MAXLR >= 4 ? 16 : 8), ZIN, HOUT>(a, b, lL, lNs, nseq, sstride, tw, first,
+                                                                      last);
+                break;
         }
         __syncthreads();
         V2<T>* t = a; a = b; b = t;
@@ -263,7 +305,9 @@ __device__ V2<T>* stockham_fft(V2<T>* a, V2<T>* b, int lL, int nseq, int sstride
 // stage t for offset u = m mod 2^t is W_{s 2^(t+1)}^r * W_{2^(t+1)}^u (table
 // times compile-time constant).  Checked against numpy's FFT for lengths
 // 1..1024 and every group size.
-template <typename T, bool INV, int G, bool PAD>
+// HOUT (last group only): only the lower half of the sequence is wanted; the
+// last stage skips its differences and the upper half is not stored.
+template <typename T, bool INV, int G, bool PAD, bool HOUT = false>
 __device__ __forceinline__ void dit_group(V2<T>* buf, int lL, int lg, int nseq, int sstride, int estride,
                                           const V2<T>* __restrict__ tw) {
     constexpr int M = 1 << G;
@@ -290,15 +334,17 @@ __device__ __forceinline__ void dit_group(V2<T>* buf, int lL, int lg, int nseq, 
                 const V2<T> w = u ? cmul(wb, small_twid<T, INV>(u, t + 1)) : wb;
                 const V2<T> a = v[m], b = cmul(v[m + h], w);
                 v[m] = a + b;
-                v[m + h] = a - b;
+                if (!(HOUT && t == G - 1)) v[m + h] = a - b;
             }
         }
 #pragma unroll
-        for (int m = 0; m < M; ++m) p[ix<PAD>(base + m * s, estride)] = v[m];
+        for (int m = 0; m < (HOUT ? M / 2 : M); ++m) p[ix<PAD>(base + m * s, estride)] = v[m];
     }
 }
 
-template <typename T, bool INV, int G, bool PAD>
+// ZIN (first group only): the upper half of the sequence is zero; it is not
+// read and the first stage reduces to v[m + M/2] = v[m] w.
+template <typename T, bool INV, int G, bool PAD, bool ZIN = false>
 __device__ __forceinline__ void dif_group(V2<T>* buf, int lL, int lS, int nseq, int sstride, int estride,
                                           const V2<T>* __restrict__ tw) {
     constexpr int M = 1 << G;
@@ -314,7 +360,7 @@ __device__ __forceinline__ void dif_group(V2<T>* buf, int lL, int lS, int nseq, 
         const int base = ((g >> lsm) << (lS + 1)) + r;
         V2<T> v[M];
 #pragma unroll
-        for (int m = 0; m < M; ++m) v[m] = p[ix<PAD>(base + m * sm, estride)];
+        for (int m = 0; m < M; ++m) v[m] = (ZIN && m >= M / 2) ? mk<T>((T)0, (T)0) : p[ix<PAD>(base + m * sm, estride)];
 #pragma unroll
         for (int t = G - 1; t >= 0; --t) {
             const int h = 1 << t;
@@ -324,9 +370,13 @@ __device__ __forceinline__ void dif_group(V2<T>* buf, int lL, int lS, int nseq, 
                 if (m & h) continue;
                 const int u = m & (h - 1);
                 const V2<T> w = u ? cmul(wb, small_twid<T, INV>(u, t + 1)) : wb;
-                const V2<T> a = v[m], b = v[m + h];
-                v[m] = a + b;
-                v[m + h] = cmul(a - b, w);
+                if (ZIN && t == G - 1) {
+                    v[m + h] = cmul(v[m], w);        // b = 0: a + b = a, (a - b) w = a w
+                } else {
+                    const V2<T> a = v[m], b = v[m + h];
+                    v[m] = a + b;
+                    v[m + h] = cmul(a - b, w);
+                }
             }
         }
 #pragma unroll
@@ -337,8 +387,9 @@ __device__ __forceinline__ void dif_group(V2<T>* buf, int lL, int lS, int nseq, 
 // In-place decimation-in-time FFT of nseq sequences of length 2^logL held in
 // shared memory in BIT-REVERSED order; leaves them in natural order.
 // Unnormalised.  Ends with __syncthreads().  PAD: unit-stride sequences
-// stored with pidx() padding (estride ignored).
-template <typename T, bool INV, bool PAD = false>
+// stored with pidx() padding (estride ignored).  HOUT: only the lower half of
+// each result is wanted (the upper half is left undefined).
+template <typename T, bool INV, bool PAD = false, bool HOUT = false>
 __device__ void fft_dit(V2<T>* buf, int logL, int nseq, int sstride, int estride,
                         const V2<T>* __restrict__ tw) {
     constexpr int GM = sizeof(T) == 4 ? 4 : 3;
@@ -346,11 +397,24 @@ __device__ void fft_dit(V2<T>* buf, int logL, int nseq, int sstride, int estride
     while (lg < logL) {
         const int rem = logL - lg;
         const int G = rem < GM ? rem : GM;
+        const bool last = lg + G == logL;
         switch (G) {
-            case 1: dit_group<T, INV, 1, PAD>(buf, logL, lg, nseq, sstride, estride, tw); break;
-            case 2: dit_group<T, INV, 2, PAD>(buf, logL, lg, nseq, sstride, estride, tw); break;
-            case 3: dit_group<T, INV, 3, PAD>(buf, logL, lg, nseq, sstride, estride, tw); break;
-            default: dit_group<T, INV, GM, PAD>(buf, logL, lg, nseq, sstride, estride, tw); break;
+            case 1:
+                if (HOUT && last) dit_group<T, INV, 1, PAD, true>(buf, logL, lg, nseq, sstride, estride, tw);
+                else dit_group<T, INV, 1, PAD>(buf, logL, lg, nseq, sstride, estride, tw);
+                break;
+            case 2:
+                if (HOUT && last) dit_group<T, INV, 2, PAD, true>(buf, logL, lg, nseq, sstride, estride, tw);
+                else dit_group<T, INV, 2, PAD>(buf, logL, lg, nseq, sstride, estride, tw);
+                break;
+            case 3:
+                if (HOUT && last) dit_group<T, INV, 3, PAD, true>(buf, logL, lg, nseq, sstride, estride, tw);
+                else dit_group<T, INV, 3, PAD>(buf, logL, lg, nseq, sstride, estride, tw);
+                break;
+            default:
+                if (HOUT && last) dit_group<T, INV, GM, PAD, true>(buf, logL, lg, nseq, sstride, estride, tw);
+                else dit_group<T, INV, GM, PAD>(buf, logL, lg, nseq, sstride, estride, tw);
+                break;
         }
         __syncthreads();
         lg += G;
@@ -358,19 +422,33 @@ __device__ void fft_dit(V2<T>* buf, int logL, int nseq, int sstride, int estride
 }
 
 // In-place decimation-in-frequency FFT: natural order in, BIT-REVERSED order
-// out.  Unnormalised.  Ends with __syncthreads().
-template <typename T, bool INV, bool PAD = false>
+// out.  Unnormalised.  Ends with __syncthreads().  ZIN: the upper half of each
+// input is zero (it need not be stored).
+template <typename T, bool INV, bool PAD = false, bool ZIN = false>
 __device__ void fft_dif(V2<T>* buf, int logL, int nseq, int sstride, int estride,
                         const V2<T>* __restrict__ tw) {
     constexpr int GM = sizeof(T) == 4 ? 4 : 3;
     int lS = logL - 1;
     while (lS >= 0) {
         const int G = (lS + 1) < GM ? (lS + 1) : GM;
+        const bool first = lS == logL - 1;
         switch (G) {
-            case 1: dif_group<T, INV, 1, PAD>(buf, logL, lS, nseq, sstride, estride, tw); break;
-            case 2: dif_group<T, INV, 2, PAD>(buf, logL, lS, nseq, sstride, estride, tw); break;
-            case 3: dif_group<T, INV, 3, PAD>(buf, logL, lS, nseq, sstride, estride, tw); break;
-            default: dif_group<T, INV, GM, PAD>(buf, logL, lS, nseq, sstride, estride, tw); break;
+            case 1:
+                if (ZIN && first) dif_group<T, INV, 1, PAD, true>(buf, logL, lS, nseq, sstride, estride, tw);
+                else dif_group<T, INV, 1, PAD>(buf, logL, lS, nseq, sstride, estride, tw);
+                break;
+            case 2:
+                if (ZIN && first) dif_group<T, INV, 2, PAD, true>(buf, logL, lS, nseq, sstride, estride, tw);
+                else dif_group<T, INV, 2, PAD>(buf, logL, lS, nseq, sstride, estride, tw);
+                break;
+            case 3:
+                if (ZIN && first) dif_group<T, INV, 3, PAD, true>(buf, logL, lS, nseq, sstride, estride, tw);
+                else dif_group<T, INV, 3, PAD>(buf, logL, lS, nseq, sstride, estride, tw);
+                break;
+            default:
+                if (ZIN && first) dif_group<T, INV, GM, PAD, true>(buf, logL, lS, nseq, sstride, estride, tw);
+                else dif_group<T, INV, GM, PAD>(buf, logL, lS, nseq, sstride, estride, tw);
+                break;
         }
         __syncthreads();
         lS -= G;

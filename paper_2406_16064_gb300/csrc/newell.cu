@@ -245,13 +245,31 @@ template __global__ void k_newell_extract<float>(const double2*, int, int, int, 
 template __global__ void k_newell_extract<double>(const double2*, int, int, int, int, int, int, double, double*,
                                                    int, int, unsigned long long*, unsigned long long*);
 
-// twiddle tables exp(-2 pi i k / LMAX)
+// twiddle tables: exp(-2 pi i k / LMAX) for k < LMAX, then the stage tables
+// W_M^(k r) (layout: stw_base in mm_kernels.cuh), all from FP64 sincospi of the
+// exact fraction 2 (k r mod M) / M
 __global__ void k_twiddles(V2<double>* twd, V2<float>* twf) {
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < MM_LMAX; k += gridDim.x * blockDim.x) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < MM_TW_ENTRIES; i += gridDim.x * blockDim.x) {
+        long long num;
+        int lM;
+        if (i < MM_LMAX) {
+            num = i;
+            lM = MM_LOG2_LMAX;
+        } else {
+            int rem = i - MM_LMAX, LR = 1;
+            while (LR < 4 && rem >= stw_off(LR + 1)) ++LR;
+            rem -= stw_off(LR);
+            const int R1 = (1 << LR) - 1;
+            lM = LR;
+            while (rem >= R1 * (1 << (lM - LR))) { rem -= R1 * (1 << (lM - LR)); ++lM; }
+            const int ns = 1 << (lM - LR);
+            const int r = rem / ns + 1, k = rem - (r - 1) * ns;
+            num = ((long long)k * r) & ((1LL << lM) - 1);
+        }
         double s, c;
-        sincospi(2.0 * k / MM_LMAX, &s, &c);
-        twd[k].x = c; twd[k].y = -s;
-        twf[k].x = (float)c; twf[k].y = (float)-s;
+        sincospi(2.0 * (double)num / (double)(1LL << lM), &s, &c);
+        twd[i].x = c; twd[i].y = -s;
+        twf[i].x = (float)c; twf[i].y = (float)-s;
     }
 }
 

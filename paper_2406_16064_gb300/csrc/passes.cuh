@@ -99,9 +99,12 @@ __global__ void __launch_bounds__(MM_XTHREADS_MAX<T>, 1) k_xfwd(PassParams<T> p)
     const bool msarr = (d.flags & F_MSARR) != 0;
     const T hstep = (T)((p.mode == MODE_RK || p.mode == MODE_NEB) ? p.state[w.sim].h : 0.0);
     const T* __restrict__ msp = msarr ? p.Ms + d.ms_off + (long long)row0 * nx : nullptr;
-    const int tot = nrows << lLh;
+    // z[n] = M[2n] + i M[2n+1] is non-zero for n < ceil(nx/2) <= Lh/2 (Lh >= nx): only the
+    // lower half of each sequence is stored, the first FFT stage does not read the upper half
+    const int lhalf = lLh > 0 ? lLh - 1 : 0;
+    const int tot = nrows << lhalf;
     for (int id = threadIdx.x; id < tot; id += blockDim.x) {
-        const int r = id >> lLh, n = id & (Lh - 1);
+        const int r = id >> lhalf, n = id & ((1 << lhalf) - 1);
         V2<T> val[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) val[c] = mk<T>((T)0, (T)0);
@@ -160,7 +163,8 @@ __global__ void __launch_bounds__(MM_XTHREADS_MAX<T>, 1) k_xfwd(PassParams<T> p)
     }
     if (!demag) return;
     __syncthreads();
-    const V2<T>* Z = stockham_fft<T, false, (sizeof(T) == 4 ? 4 : 3)>(bufA, bufB, lLh, nseq, SL, p.tw);
+    const V2<T>* Z = stockham_fft<T, false, (sizeof(T) == 4 ? 4 : 3), true, false>(bufA, bufB, lLh, nseq, SL, p.tw);
+    const V2<T>* __restrict__ wsplit = p.tw + MM_LMAX + stw_base(1, d.lPx);   // W_Px^k, k < Lh
     // split the half-length transform into X_k, k = 0..Lh, and store in the kx-blocked layout
     const int z0 = row0 / ny, y0 = row0 - z0 * ny;       // a tile never crosses a plane
     V2<T>* sp = p.spec + d.spec_off;
@@ -179,7 +183,7 @@ __global__ void __launch_bounds__(MM_XTHREADS_MAX<T>, 1) k_xfwd(PassParams<T> p)
         const V2<T> Dd = Zk - Zm;
         const V2<T> O = mk<T>(Dd.y * (T)0.5, -Dd.x * (T)0.5);
         const int o = (c * d.nz + z) * plane + (((k >> lT) * d.Py + y) << lT) + (k & (TT - 1));
-        sp[o] = E + cmul(twid<T, false>(p.tw, k, d.lPx), O);
+        sp[o] = E + cmul(k < Lh ? wsplit[k] : mk<T>((T)-1, (T)0), O);
     }
 }
 
@@ -233,13 +237,13 @@ __global__ void __launch_bounds__(MM_XTHREADS_MAX<T>, 1) k_ycol(PassParams<T> p)
     }
     __syncthreads();
     if (YMODE == 0) {
-        fft_dif<T, false>(sm, lL, es, 1, es, p.tw);
+        fft_dif<T, false, false, true>(sm, lL, es, 1, es, p.tw);
         for (int id = threadIdx.x; id < (L << lT); id += blockDim.x)
             p.spec[gb[0] + id] = sm[id];             // NC == 1: row stride Ty
         return;
     }
     if (YMODE == 2) {
-        fft_dif<T, false>(sm, lL, es, 1, es, p.tw);
+        fft_dif<T, false, false, true>(sm, lL, es, 1, es, p.tw);
         for (int id = threadIdx.x; id < (L << lT); id += blockDim.x) {
             const int col = id & (TT - 1), r = id >> lT;
             if (col < ncols) {
@@ -251,7 +255,7 @@ __global__ void __launch_bounds__(MM_XTHREADS_MAX<T>, 1) k_ycol(PassParams<T> p)
         }
         __syncthreads();
     }
-    fft_dit<T, true>(sm, lL, es, 1, es, p.tw);
+    fft_dit<T, true, false, true>(sm, lL, es, 1, es, p.tw);
 #pragma unroll
     for (int cc = 0; cc < NC; ++cc) {
         for (int id = threadIdx.x; id < (ny << lT); id += blockDim.x) {
@@ -306,7 +310,7 @@ __global__ void __launch_bounds__(MM_XTHREADS_MAX<T>, 1) k_zcol(PassParams<T> p)
         }
     }
     __syncthreads();
-    fft_dif<T, false>(sm, lL, es, 1, es, p.tw);
+    fft_dif<T, false, false, true>(sm, lL, es, 1, es, p.tw);
     for (int id = threadIdx.x; id < (L << lT); id += blockDim.x) {
         const int col = id & (TT - 1);
         const int r = id >> lT;
@@ -318,7 +322,7 @@ __global__ void __launch_bounds__(MM_XTHREADS_MAX<T>, 1) k_zcol(PassParams<T> p)
         }
     }
     __syncthreads();
-    fft_dit<T, true>(sm, lL, es, 1, es, p.tw);
+    fft_dit<T, true, false, true>(sm, lL, es, 1, es, p.tw);
     const int tot3 = (nz * 3) << lT;
     for (int id = threadIdx.x; id < tot3; id += blockDim.x) {
         const int col = id & (TT - 1);
@@ -452,14 +456,14 @@ __global__ void __launch_bounds__(MM_THREADS, sizeof(T) == 4 ? 2 : 1) k_yzc(Pass
         }
     }
     __syncthreads();
-    fft_dif<T, false>(sm, lL, es, 1, es, p.tw);   // rows leave in bit-reversed order
+    fft_dif<T, false, false, true>(sm, lL, es, 1, es, p.tw);   // rows leave in bit-reversed order
     cl.sync();                                  // every plane transformed along y
     V2<T>* rem[8];
 #pragma unroll
     for (int zz = 0; zz < 8; ++zz) rem[zz] = zz < nz ? cl.map_shared_rank(sm, zz) : sm;
     yzc_zstep<T, PZ>(p, d, rem, rank, nz, es, b, ncols);   // PZ == d.Pz, fixed by nz per launch
     cl.sync();                                  // every row back in its owner's plane
-    fft_dit<T, true>(sm, lL, es, 1, es, p.tw);    // bit-reversed in, natural out
+    fft_dit<T, true, false, true>(sm, lL, es, 1, es, p.tw);    // bit-reversed in, natural out
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         for (int id = threadIdx.x; id < (ny << lT); id += blockDim.x) {
@@ -552,16 +556,19 @@ __global__ void __launch_bounds__(MM_XTHREADS_MAX<T>, 1) k_xinv(PassParams<T> p,
             __syncthreads();
         }
         // Hermitian split into B: Z_k = (X_k + X*_{Lh-k}) + i W^{-k} (X_k - X*_{Lh-k}), k < Lh
+        const V2<T>* __restrict__ wsplit = p.tw + MM_LMAX + stw_base(1, d.lPx);   // W_Px^k, k < Lh
         for (int id = threadIdx.x; id < tot1; id += blockDim.x) {
             const int q = id >> lLh, k = id & (Lh - 1);
             const V2<T>* s = bufA + q * SK;
             const V2<T> Xa = s[ix<true>(k, 1)], Xb = cconj(s[ix<true>(Lh - k, 1)]);
             const V2<T> e = Xa + Xb;
-            const V2<T> t = cmul(twid<T, true>(p.tw, k, d.lPx), Xa - Xb);
+            const V2<T> t = cmul(stw_get<T, true>(wsplit, k), Xa - Xb);
             bufB[q * SK + ix<true>(k, 1)] = mk<T>(e.x - t.y, e.y + t.x);
         }
         __syncthreads();
-        Hd = stockham_fft<T, true, (sizeof(T) == 4 ? 4 : 3)>(bufB, bufA, lLh, nseq, SK, p.tw);
+        // only z[n], n < ceil(nx/2) <= Lh/2, is read by the epilogue: the last stage
+        // writes the lower half of each sequence
+        Hd = stockham_fft<T, true, (sizeof(T) == 4 ? 4 : 3), false, true>(bufB, bufA, lLh, nseq, SK, p.tw);
     }
 
     // per-cell local fields and torque; coefficients precomputed in the context

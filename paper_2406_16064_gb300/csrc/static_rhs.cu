@@ -122,8 +122,8 @@ extern "C" int mm_rhs_eval_static(const mm_mesh* mesh, const mm_material* mat, i
 
     // carve the static array
     Carve cv;
-    const size_t o_twd = cv.take((size_t)MM_LMAX * 16);
-    const size_t o_twf = cv.take((size_t)MM_LMAX * 8);
+    const size_t o_twd = cv.take((size_t)MM_TW_ENTRIES * 16);
+    const size_t o_twf = cv.take((size_t)MM_TW_ENTRIES * 8);
     const size_t o_desc = cv.take(sizeof(SimDesc));
     const size_t o_state = cv.take(sizeof(SimState));
     const size_t o_diag = cv.take(2 * sizeof(unsigned long long));

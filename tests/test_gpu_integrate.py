@@ -98,6 +98,27 @@ def test_norm_and_energy_decay_on_gpu():
         E0 = E1
 
 
+def test_norm_and_energy_decay_on_gpu_f32():
+    """FP32 states: the projection (float-float norm) leaves every |m| within two
+    FP32 ulps of 1 (one rounding per component); the energy does not grow beyond
+    the controller's tolerance."""
+    mesh = synth.Mesh(24, 16, 2, 2e-9, 2e-9, 2e-9)
+    mat = synth.Material(Ms=8e5, A=1.3e-11, Ku=2e5, alpha=0.5, H=(1e4, 0, 0))
+    sim = synth.Sim(mesh, mat, synth.random_state(2, mesh))
+    ctx = make_ctx("f32", [sim])
+    ctx.set_m(sim.m0.ravel())
+    ctx.reset_time()
+    ctx.rk45_setup(1e-5)
+    E0 = ctx.energy(0)["total"]
+    for _ in range(10):
+        ctx.rk45_step()
+        m = ctx.get_m(0).reshape(3, -1)
+        assert np.abs(np.sqrt((m ** 2).sum(0)) - 1).max() < 2 * 2.0 ** -23
+        E1 = ctx.energy(0)["total"]
+        assert E1 <= E0 + 1e-5 * abs(E0)
+        E0 = E1
+
+
 def test_stoner_wohlfarth_switching_on_gpu():
     mesh = synth.Mesh(4, 4, 4, 2e-9, 2e-9, 2e-9)
     Ms0, Ku = 1e6, 5e4
