@@ -172,21 +172,28 @@ __host__ __device__ constexpr int brev_ct(int v) {
     return r;
 }
 
-// cos(2 pi r / 16) and sin(2 pi r / 16), r = 0..3 (the rest by symmetry)
-__device__ __forceinline__ double w16c(int r) {
-    return r == 0 ? 1.0 : r == 1 ? 0.92387953251128675613 : r == 2 ? 0.70710678118654752440 : 0.38268343236508977173;
+// cos(2 pi k / 32), k = 0..7 (the rest of the circle by symmetry)
+__device__ __forceinline__ double w32c(int k) {
+    return k == 0 ? 1.0
+         : k == 1 ? 0.9807852804032304491261822
+         : k == 2 ? 0.9238795325112867561281832
+         : k == 3 ? 0.8314696123025452370787884
+         : k == 4 ? 0.7071067811865475244008444
+         : k == 5 ? 0.5555702330196022247428308
+         : k == 6 ? 0.3826834323650897717284600
+         : 0.1950903220161282678482849;
 }
 
-// W_M^r = exp(-+2 pi i r / M) for M <= 16, from compile-time constants
+// W_M^r = exp(-+2 pi i r / M) for M <= 32, from compile-time constants
 template <typename T, bool INV>
 __device__ __forceinline__ V2<T> small_twid(int r, int logM) {
-    const int q = r << (4 - logM);              // in sixteenths of a turn, 0..15
-    const int qm = q & 3;
-    const T c = (T)w16c(qm), s = (T)w16c(4 - qm == 4 ? 0 : 4 - qm);   // cos, sin of qm/16 turn
-    const T sn = qm == 0 ? (T)0 : s;
-    // rotate by the quarter turns in q >> 2: (c, -sn) * (-i)^(q>>2)
+    const int q = r << (5 - logM);              // in 32nds of a turn, 0..31
+    const int qm = q & 7;
+    const T c = (T)w32c(qm);                    // cos and sin of qm/32 turn
+    const T sn = qm == 0 ? (T)0 : (T)w32c(8 - qm);
+    // rotate by the quarter turns in q >> 3: (c, -sn) * (-i)^(q>>3)
     V2<T> w;
-    switch (q >> 2) {
+    switch (q >> 3) {
         case 0: w = mk<T>(c, -sn); break;
         case 1: w = mk<T>(-sn, -c); break;
         case 2: w = mk<T>(-c, sn); break;
@@ -384,36 +391,56 @@ __device__ __forceinline__ void dif_group(V2<T>* buf, int lL, int lS, int nseq, 
     }
 }
 
+// Stages per register group: logL stages in ceil(logL / GM) groups of
+// near-equal size (a trailing group of one or two stages costs almost as
+// much per element as a full one).  Group i of the schedule:
+__device__ __forceinline__ int group_size(int logL, int GM, int i) {
+    const int ng = (logL + GM - 1) / GM;
+    const int b = logL / ng;
+    return b + (i < logL - b * ng ? 1 : 0);
+}
+
+template <typename T, bool INV, int G, bool PAD, bool HOUT>
+__device__ __forceinline__ void dit_pick(V2<T>* buf, int logL, int lg, int nseq, int sstride, int estride,
+                                         const V2<T>* __restrict__ tw, bool last) {
+    if (HOUT && last) dit_group<T, INV, G, PAD, true>(buf, logL, lg, nseq, sstride, estride, tw);
+    else dit_group<T, INV, G, PAD, false>(buf, logL, lg, nseq, sstride, estride, tw);
+}
+
+template <typename T, bool INV, int G, bool PAD, bool ZIN>
+__device__ __forceinline__ void dif_pick(V2<T>* buf, int logL, int lS, int nseq, int sstride, int estride,
+                                         const V2<T>* __restrict__ tw, bool first) {
+    if (ZIN && first) dif_group<T, INV, G, PAD, true>(buf, logL, lS, nseq, sstride, estride, tw);
+    else dif_group<T, INV, G, PAD, false>(buf, logL, lS, nseq, sstride, estride, tw);
+}
+
+// Default largest group: 16 points (FP32) / 8 (FP64) in registers; kernels
+// with a larger register budget pass GM = 5.
+template <typename T>
+constexpr int kGroupMax = sizeof(T) == 4 ? 4 : 3;
+
 // In-place decimation-in-time FFT of nseq sequences of length 2^logL held in
 // shared memory in BIT-REVERSED order; leaves them in natural order.
 // Unnormalised.  Ends with __syncthreads().  PAD: unit-stride sequences
 // stored with pidx() padding (estride ignored).  HOUT: only the lower half of
-// each result is wanted (the upper half is left undefined).
-template <typename T, bool INV, bool PAD = false, bool HOUT = false>
+// each result is wanted (the upper half is left undefined).  GM: largest
+// group (log2 of the points held in registers).
+template <typename T, bool INV, bool PAD = false, bool HOUT = false, int GM = kGroupMax<T>>
 __device__ void fft_dit(V2<T>* buf, int logL, int nseq, int sstride, int estride,
                         const V2<T>* __restrict__ tw) {
-    constexpr int GM = sizeof(T) == 4 ? 4 : 3;
     int lg = 0;
-    while (lg < logL) {
-        const int rem = logL - lg;
-        const int G = rem < GM ? rem : GM;
+    for (int i = 0; lg < logL; ++i) {
+        const int G = group_size(logL, GM, i);
         const bool last = lg + G == logL;
         switch (G) {
-            case 1:
-                if (HOUT && last) dit_group<T, INV, 1, PAD, true>(buf, logL, lg, nseq, sstride, estride, tw);
-                else dit_group<T, INV, 1, PAD>(buf, logL, lg, nseq, sstride, estride, tw);
-                break;
-            case 2:
-                if (HOUT && last) dit_group<T, INV, 2, PAD, true>(buf, logL, lg, nseq, sstride, estride, tw);
-                else dit_group<T, INV, 2, PAD>(buf, logL, lg, nseq, sstride, estride, tw);
-                break;
-            case 3:
-                if (HOUT && last) dit_group<T, INV, 3, PAD, true>(buf, logL, lg, nseq, sstride, estride, tw);
-                else dit_group<T, INV, 3, PAD>(buf, logL, lg, nseq, sstride, estride, tw);
+            case 1: dit_pick<T, INV, 1, PAD, HOUT>(buf, logL, lg, nseq, sstride, estride, tw, last); break;
+            case 2: dit_pick<T, INV, 2, PAD, HOUT>(buf, logL, lg, nseq, sstride, estride, tw, last); break;
+            case 3: dit_pick<T, INV, 3, PAD, HOUT>(buf, logL, lg, nseq, sstride, estride, tw, last); break;
+            case 4:
+                if constexpr (GM >= 4) dit_pick<T, INV, 4, PAD, HOUT>(buf, logL, lg, nseq, sstride, estride, tw, last);
                 break;
             default:
-                if (HOUT && last) dit_group<T, INV, GM, PAD, true>(buf, logL, lg, nseq, sstride, estride, tw);
-                else dit_group<T, INV, GM, PAD>(buf, logL, lg, nseq, sstride, estride, tw);
+                if constexpr (GM >= 5) dit_pick<T, INV, 5, PAD, HOUT>(buf, logL, lg, nseq, sstride, estride, tw, last);
                 break;
         }
         __syncthreads();
@@ -423,31 +450,23 @@ __device__ void fft_dit(V2<T>* buf, int logL, int nseq, int sstride, int estride
 
 // In-place decimation-in-frequency FFT: natural order in, BIT-REVERSED order
 // out.  Unnormalised.  Ends with __syncthreads().  ZIN: the upper half of each
-// input is zero (it need not be stored).
-template <typename T, bool INV, bool PAD = false, bool ZIN = false>
+// input is zero (it need not be stored).  GM as for fft_dit.
+template <typename T, bool INV, bool PAD = false, bool ZIN = false, int GM = kGroupMax<T>>
 __device__ void fft_dif(V2<T>* buf, int logL, int nseq, int sstride, int estride,
                         const V2<T>* __restrict__ tw) {
-    constexpr int GM = sizeof(T) == 4 ? 4 : 3;
     int lS = logL - 1;
-    while (lS >= 0) {
-        const int G = (lS + 1) < GM ? (lS + 1) : GM;
-        const bool first = lS == logL - 1;
+    for (int i = 0; lS >= 0; ++i) {
+        const int G = group_size(logL, GM, i);
+        const bool first = i == 0;
         switch (G) {
-            case 1:
-                if (ZIN && first) dif_group<T, INV, 1, PAD, true>(buf, logL, lS, nseq, sstride, estride, tw);
-                else dif_group<T, INV, 1, PAD>(buf, logL, lS, nseq, sstride, estride, tw);
-                break;
-            case 2:
-                if (ZIN && first) dif_group<T, INV, 2, PAD, true>(buf, logL, lS, nseq, sstride, estride, tw);
-                else dif_group<T, INV, 2, PAD>(buf, logL, lS, nseq, sstride, estride, tw);
-                break;
-            case 3:
-                if (ZIN && first) dif_group<T, INV, 3, PAD, true>(buf, logL, lS, nseq, sstride, estride, tw);
-                else dif_group<T, INV, 3, PAD>(buf, logL, lS, nseq, sstride, estride, tw);
+            case 1: dif_pick<T, INV, 1, PAD, ZIN>(buf, logL, lS, nseq, sstride, estride, tw, first); break;
+            case 2: dif_pick<T, INV, 2, PAD, ZIN>(buf, logL, lS, nseq, sstride, estride, tw, first); break;
+            case 3: dif_pick<T, INV, 3, PAD, ZIN>(buf, logL, lS, nseq, sstride, estride, tw, first); break;
+            case 4:
+                if constexpr (GM >= 4) dif_pick<T, INV, 4, PAD, ZIN>(buf, logL, lS, nseq, sstride, estride, tw, first);
                 break;
             default:
-                if (ZIN && first) dif_group<T, INV, GM, PAD, true>(buf, logL, lS, nseq, sstride, estride, tw);
-                else dif_group<T, INV, GM, PAD>(buf, logL, lS, nseq, sstride, estride, tw);
+                if constexpr (GM >= 5) dif_pick<T, INV, 5, PAD, ZIN>(buf, logL, lS, nseq, sstride, estride, tw, first);
                 break;
         }
         __syncthreads();

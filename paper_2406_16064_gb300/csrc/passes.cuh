@@ -456,14 +456,16 @@ __global__ void __launch_bounds__(MM_THREADS, sizeof(T) == 4 ? 2 : 1) k_yzc(Pass
         }
     }
     __syncthreads();
-    fft_dif<T, false, false, true>(sm, lL, es, 1, es, p.tw);   // rows leave in bit-reversed order
+    // 32-point register groups in FP32 (this kernel has 128 registers a thread)
+    constexpr int GMC = sizeof(T) == 4 ? 5 : kGroupMax<T>;
+    fft_dif<T, false, false, true, GMC>(sm, lL, es, 1, es, p.tw);   // rows leave in bit-reversed order
     cl.sync();                                  // every plane transformed along y
     V2<T>* rem[8];
 #pragma unroll
     for (int zz = 0; zz < 8; ++zz) rem[zz] = zz < nz ? cl.map_shared_rank(sm, zz) : sm;
     yzc_zstep<T, PZ>(p, d, rem, rank, nz, es, b, ncols);   // PZ == d.Pz, fixed by nz per launch
     cl.sync();                                  // every row back in its owner's plane
-    fft_dit<T, true, false, true>(sm, lL, es, 1, es, p.tw);    // bit-reversed in, natural out
+    fft_dit<T, true, false, true, GMC>(sm, lL, es, 1, es, p.tw);    // bit-reversed in, natural out
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         for (int id = threadIdx.x; id < (ny << lT); id += blockDim.x) {
