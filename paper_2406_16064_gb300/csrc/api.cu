@@ -61,10 +61,11 @@ struct mm_ctx {
     SimDesc* desc_d = nullptr;
     SimState* state_d = nullptr;
     WorkItem *xi = nullptr, *y13i = nullptr, *zi = nullptr, *y2i = nullptr;
-    WorkItem* yzci[kMaxClusterPlanes + 1] = {};
+    WorkItem* yzci[2 * kYzcLists] = {};
     PlanItems plan;
-    // per simulation: first item and item count in each list (the yzc list is the one of its nz)
-    std::vector<int> xb, xc, y13b, y13c, zb, zc, y2b, y2c, yzcb, yzcc;
+    // per simulation: first item and item count in each list (the yzc list is the
+    // one of its plane count and group width, yzcl)
+    std::vector<int> xb, xc, y13b, y13c, zb, zc, y2b, y2c, yzcb, yzcc, yzcl;
     int *flag_d = nullptr, *status_d = nullptr;
     unsigned long long* diag_d = nullptr;
     cudaGraphExec_t rk_exec = nullptr;
@@ -120,9 +121,9 @@ Launch make_launch(mm_ctx* C, int sim) {
     set(L.y13, C->y13i, C->y13b, C->y13c, P.y13);
     set(L.z, C->zi, C->zb, C->zc, P.z);
     set(L.y2, C->y2i, C->y2b, C->y2c, P.y2);
-    for (int nz = 2; nz <= kMaxClusterPlanes; ++nz) {
-        if (sim < 0) L.yzc[nz] = {C->yzci[nz], (int)P.yzc[nz].size()};
-        else if (C->sims[sim].d.nz == nz) L.yzc[nz] = {C->yzci[nz] + C->yzcb[sim], C->yzcc[sim]};
+    for (int li = 0; li < 2 * kYzcLists; ++li) {
+        if (sim < 0) L.yzc[li] = {C->yzci[li], (int)P.yzc[li].size()};
+        else if (C->yzcl[sim] == li) L.yzc[li] = {C->yzci[li] + C->yzcb[sim], C->yzcc[sim]};
     }
     L.smem_x = P.smem_x;
     L.smem_xi = P.smem_xi;
@@ -187,10 +188,12 @@ int validate_items(mm_ctx* C) {
         if (w.a < 0 || w.a >= d.Py || w.b < 0 || w.b >= d.NBx) return fail(C, MM_EBOUNDS, "z item range");
         if (3ULL * d.Pz * d.Ty * vsz > P.smem_z) return fail(C, MM_EBOUNDS, "z item smem");
     }
-    for (int nz = 2; nz <= kMaxClusterPlanes; ++nz) {
-        for (const WorkItem& w : P.yzc[nz]) {
+    for (int li = 0; li < 2 * kYzcLists; ++li) {
+        const int nz = li % kYzcLists;
+        for (const WorkItem& w : P.yzc[li]) {
             const SimDesc& d = C->sims[w.sim].d;
-            if (d.nz != nz || d.Py < 2 || w.b < 0 || w.b >= d.NBx || d.Pz != plan_pad_len(nz, false))
+            if (d.nz != nz || d.Py < 2 || w.b < 0 || w.b >= d.NBx || d.Pz != plan_pad_len(nz, false) ||
+                plan_yzc_list(d, C->precision == MM_F32) != li)
                 return fail(C, MM_EBOUNDS, "yz item range");
             if (3ULL * d.Py * d.Ty * vsz > P.smem_yzc) return fail(C, MM_EBOUNDS, "yz item smem");
         }
@@ -371,7 +374,7 @@ int mm_destroy(mm_ctx* C) {
                     C->zi, C->y2i, C->flag_d, C->status_d, C->diag_d};
     for (void* p : ptrs) if (p) cudaFree(p);
     for (int j = 0; j < 7; ++j) if (C->k[j]) cudaFree(C->k[j]);
-    for (int nz = 0; nz <= kMaxClusterPlanes; ++nz) if (C->yzci[nz]) cudaFree(C->yzci[nz]);
+    for (int li = 0; li < 2 * kYzcLists; ++li) if (C->yzci[li]) cudaFree(C->yzci[li]);
     if (C->own_stream) cudaStreamDestroy(C->stream);
     delete C;
     return MM_OK;
@@ -496,9 +499,14 @@ int mm_precompute_demag(mm_ctx* C) {
         C->total_elems += 3LL * d.ncells;
         d.tens_off = C->geoms[s.geom].tens_off;
         if (d.flags & F_MSARR) { d.ms_off = C->ms_elems; C->ms_elems += d.ncells; }
-        if (d.flags & F_DEMAG) { d.spec_off = C->spec_elems; C->spec_elems += plan_spec_elems(d); }
+        if (d.flags & F_DEMAG) {
+            // 4-element (32-byte) aligned, so every Ty-wide run of Ty >= 2 values takes 16-byte copies
+            d.spec_off = (C->spec_elems + 3) & ~3LL;
+            C->spec_elems = d.spec_off + plan_spec_elems(d);
+        }
         else d.spec_off = 0;
-        const int g = std::min(d.nz, kMaxClusterPlanes);
+        const int g = plan_uses_yzc(d) ? plan_yzc_list(d, C->precision == MM_F32) : 0;
+        C->yzcl.push_back(g);
         C->xb.push_back((int)P.x.size());
         C->y13b.push_back((int)P.y13.size());
         C->zb.push_back((int)P.z.size());
@@ -543,8 +551,8 @@ int mm_precompute_demag(mm_ctx* C) {
     if ((rc = up_items(&C->y13i, P.y13))) return rc;
     if ((rc = up_items(&C->zi, P.z))) return rc;
     if ((rc = up_items(&C->y2i, P.y2))) return rc;
-    for (int nz = 2; nz <= kMaxClusterPlanes; ++nz)
-        if ((rc = up_items(&C->yzci[nz], P.yzc[nz]))) return rc;
+    for (int li = 0; li < 2 * kYzcLists; ++li)
+        if ((rc = up_items(&C->yzci[li], P.yzc[li]))) return rc;
     CK(cudaMemcpyAsync(C->kvec_dev, C->k, 7 * sizeof(void*), cudaMemcpyHostToDevice, C->stream));
     CK(cudaMemsetAsync(C->spec, 0, (size_t)C->spec_elems * 2 * C->esz, C->stream));
     CK(cudaMemsetAsync(C->m, 0, sb, C->stream));

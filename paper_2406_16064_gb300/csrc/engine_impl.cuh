@@ -69,11 +69,13 @@ static void issue_passes(const Launch& L, PassParams<T> p, const T* ys, bool inc
         if (hk) hk->mark(KIND_YINV);
         ++n;
     }
-    for (int nz = 2; nz <= 8; ++nz) {
-        if (!L.yzc[nz].count) continue;
-        p.items = L.yzc[nz].dev;
+    for (int li = 0; li < 18; ++li) {
+        if (!L.yzc[li].count) continue;
+        const int nz = li % 9;
+        const bool wide = li >= 9;
+        p.items = L.yzc[li].dev;
         cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3((unsigned)(L.yzc[nz].count * nz), 1, 1);
+        cfg.gridDim = dim3((unsigned)(L.yzc[li].count * nz), 1, 1);
         cfg.blockDim = dim3(MM_THREADS, 1, 1);
         cfg.dynamicSmemBytes = L.smem_yzc;
         cfg.stream = s;
@@ -84,10 +86,10 @@ static void issue_passes(const Launch& L, PassParams<T> p, const T* ys, bool inc
         attr[0].val.clusterDim.z = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        // padded z length: the power of two >= 2 nz - 1
-        if (nz == 2) cudaLaunchKernelEx(&cfg, k_yzc<T, 4>, p);
-        else if (nz <= 4) cudaLaunchKernelEx(&cfg, k_yzc<T, 8>, p);
-        else cudaLaunchKernelEx(&cfg, k_yzc<T, 16>, p);
+        // padded z length: the power of two >= 2 nz - 1; wide: 32-point column groups
+        if (nz == 2) cudaLaunchKernelEx(&cfg, wide ? k_yzc<T, 4, true> : k_yzc<T, 4, false>, p);
+        else if (nz <= 4) cudaLaunchKernelEx(&cfg, wide ? k_yzc<T, 8, true> : k_yzc<T, 8, false>, p);
+        else cudaLaunchKernelEx(&cfg, wide ? k_yzc<T, 16, true> : k_yzc<T, 16, false>, p);
         if (hk) hk->mark(KIND_YZC);
         ++n;
     }
@@ -219,9 +221,12 @@ static void set_attrs() {
     cudaFuncSetAttribute(k_ycol<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     cudaFuncSetAttribute(k_ycol<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     cudaFuncSetAttribute(k_zcol<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    cudaFuncSetAttribute(k_yzc<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    cudaFuncSetAttribute(k_yzc<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    cudaFuncSetAttribute(k_yzc<T, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_yzc<T, 4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_yzc<T, 8, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_yzc<T, 16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_yzc<T, 4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_yzc<T, 8, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_yzc<T, 16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
 }
 
 }  // namespace mm

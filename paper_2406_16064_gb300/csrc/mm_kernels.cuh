@@ -522,6 +522,17 @@ struct PassParams {
     int* errflag;           // set by checked builds on an out-of-range index
 };
 
+// Asynchronous 16-byte global -> shared copies (cp.async, L2 only): a CTA
+// issues all its tile loads without holding them in registers, then waits for
+// its own copies once.
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
 __device__ __forceinline__ double bits_to_double(unsigned long long b) { return __longlong_as_double((long long)b); }
 
 // Ordered bits of a non-negative value in the context precision: for v >= 0

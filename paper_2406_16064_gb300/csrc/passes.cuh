@@ -215,23 +215,38 @@ __global__ void __launch_bounds__(MM_XTHREADS_MAX<T>, 1) k_ycol(PassParams<T> p)
 #pragma unroll
     for (int cc = 0; cc < NC; ++cc) gb[cc] = spec_block<T>(d, c0 + cc, z, b);
     const int nload = (YMODE == 1) ? L : ny;
-    for (int b0 = threadIdx.x; b0 < (L << lT); b0 += 4 * blockDim.x) {   // 4 NC loads in flight
-        V2<T> v[NC][4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int id = b0 + u * blockDim.x;
-            const int y = id >> lT;
-#pragma unroll
-            for (int cc = 0; cc < NC; ++cc)
-                v[cc][u] = (id < (L << lT) && y < nload) ? p.spec[gb[cc] + id] : mk<T>((T)0, (T)0);
+    constexpr int VPC = 16 / (int)sizeof(V2<T>);                 // complex values per 16-byte copy
+    if ((TT % VPC) == 0) {
+        // rows y < nload as 16-byte async copies; rows nload <= y < L/2 zeroed (the
+        // forward's first group does not read the upper half; the inverse loads all rows)
+        const int cpr = TT / VPC, ncp = NC * nload * cpr;
+        for (int i = threadIdx.x; i < ncp; i += blockDim.x) {
+            const int q = i % cpr, yc = i / cpr;
+            const int cc = yc % NC, y = yc / NC;
+            cp_async16(sm + y * es + cc * TT + q * VPC, p.spec + gb[cc] + ((long long)y << lT) + q * VPC);
         }
+        const int zrows = (YMODE == 1) ? 0 : (L >> 1) - nload;
+        for (int i = threadIdx.x; i < zrows * es; i += blockDim.x) sm[nload * es + i] = mk<T>((T)0, (T)0);
+        cp_async_wait_all();
+    } else {
+        for (int b0 = threadIdx.x; b0 < (L << lT); b0 += 4 * blockDim.x) {   // 4 NC loads in flight
+            V2<T> v[NC][4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int id = b0 + u * blockDim.x;
-            if (id < (L << lT)) {
-                const int col = id & (TT - 1), y = id >> lT;
+            for (int u = 0; u < 4; ++u) {
+                const int id = b0 + u * blockDim.x;
+                const int y = id >> lT;
 #pragma unroll
-                for (int cc = 0; cc < NC; ++cc) sm[y * es + cc * TT + col] = v[cc][u];
+                for (int cc = 0; cc < NC; ++cc)
+                    v[cc][u] = (id < (L << lT) && y < nload) ? p.spec[gb[cc] + id] : mk<T>((T)0, (T)0);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int id = b0 + u * blockDim.x;
+                if (id < (L << lT)) {
+                    const int col = id & (TT - 1), y = id >> lT;
+#pragma unroll
+                    for (int cc = 0; cc < NC; ++cc) sm[y * es + cc * TT + col] = v[cc][u];
+                }
             }
         }
     }
@@ -284,28 +299,43 @@ __global__ void __launch_bounds__(MM_XTHREADS_MAX<T>, 1) k_zcol(PassParams<T> p)
     const int kx0 = b << lT;
     const int ncols = min(TT, d.Kx - kx0);
     const int es = 3 * TT;
-    const int tot = (L * 3) << lT;
-    for (int b0 = threadIdx.x; b0 < tot; b0 += 4 * blockDim.x) {   // four loads in flight
-        V2<T> v[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int id = b0 + u * blockDim.x;
-            const int col = id & (TT - 1);
-            const int rest = id >> lT;
-            const int c = rest % 3;
-            const int z = rest / 3;
-            v[u] = (id < tot && z < nz) ? p.spec[spec_block<T>(d, c, z, b) + ((long long)row << lT) + col]
-                                        : mk<T>((T)0, (T)0);
+    constexpr int VPC = 16 / (int)sizeof(V2<T>);                 // complex values per 16-byte copy
+    if ((TT % VPC) == 0) {
+        // planes z < nz: one Ty-wide run per (z, c) as 16-byte async copies; planes
+        // nz <= z < L/2 zeroed (the forward's first group does not read the upper half)
+        const int cpr = TT / VPC, ncp = nz * 3 * cpr;
+        for (int i = threadIdx.x; i < ncp; i += blockDim.x) {
+            const int q = i % cpr, zc = i / cpr;
+            const int c = zc % 3, z = zc / 3;
+            cp_async16(sm + z * es + c * TT + q * VPC,
+                       p.spec + spec_block<T>(d, c, z, b) + ((long long)row << lT) + q * VPC);
         }
+        for (int i = threadIdx.x; i < ((L >> 1) - nz) * es; i += blockDim.x) sm[nz * es + i] = mk<T>((T)0, (T)0);
+        cp_async_wait_all();
+    } else {
+        const int tot = (L * 3) << lT;
+        for (int b0 = threadIdx.x; b0 < tot; b0 += 4 * blockDim.x) {   // four loads in flight
+            V2<T> v[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int id = b0 + u * blockDim.x;
-            if (id < tot) {
+            for (int u = 0; u < 4; ++u) {
+                const int id = b0 + u * blockDim.x;
                 const int col = id & (TT - 1);
                 const int rest = id >> lT;
                 const int c = rest % 3;
                 const int z = rest / 3;
-                sm[z * es + c * TT + col] = v[u];
+                v[u] = (id < tot && z < nz) ? p.spec[spec_block<T>(d, c, z, b) + ((long long)row << lT) + col]
+                                            : mk<T>((T)0, (T)0);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int id = b0 + u * blockDim.x;
+                if (id < tot) {
+                    const int col = id & (TT - 1);
+                    const int rest = id >> lT;
+                    const int c = rest % 3;
+                    const int z = rest / 3;
+                    sm[z * es + c * TT + col] = v[u];
+                }
             }
         }
     }
@@ -416,7 +446,8 @@ __device__ void yzc_zstep(const PassParams<T>& p, const SimDesc& d, V2<T>* const
 }
 
 // FP32: two clusters' CTAs per SM (128 registers); FP64 keeps the registers it needs.
-template <typename T, int PZ>
+// WIDE: 32-point register groups for the y columns (FP32; see plan_yzc_list).
+template <typename T, int PZ, bool WIDE>
 __global__ void __launch_bounds__(MM_THREADS, sizeof(T) == 4 ? 2 : 1) k_yzc(PassParams<T> p) {
     namespace cg = cooperative_groups;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -456,8 +487,7 @@ __global__ void __launch_bounds__(MM_THREADS, sizeof(T) == 4 ? 2 : 1) k_yzc(Pass
         }
     }
     __syncthreads();
-    // 32-point register groups in FP32 (this kernel has 128 registers a thread)
-    constexpr int GMC = sizeof(T) == 4 ? 5 : kGroupMax<T>;
+    constexpr int GMC = (WIDE && sizeof(T) == 4) ? 5 : kGroupMax<T>;
     fft_dif<T, false, false, true, GMC>(sm, lL, es, 1, es, p.tw);   // rows leave in bit-reversed order
     cl.sync();                                  // every plane transformed along y
     V2<T>* rem[8];

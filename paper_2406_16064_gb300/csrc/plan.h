@@ -97,6 +97,19 @@ inline void plan_coefficients(SimDesc& d, bool dmi_interfacial) {
 // reads its tensor in a blocked layout (plan_tens_elems).
 inline bool plan_uses_yzc(const SimDesc& d) { return d.Pz > 1 && d.Py > 1 && d.nz <= kMaxClusterPlanes; }
 
+// Cluster-pass work lists, one per (plane count nz, register-group width):
+// list nz + kYzcLists * wide.  FP32 columns of 2^5, 2^9 or 2^13 points run
+// with 32-point register groups (their schedule then holds exactly one
+// 32-point group: (5), (5,4), (5,4,4)); every other length with 16-point
+// groups, whose schedule is the same or better (two unrolled 32-point groups
+// per direction no longer fit the instruction cache: 1024-point columns
+// measured faster as (4,3,3) than as (5,5)).
+constexpr int kYzcLists = kMaxClusterPlanes + 1;
+inline int plan_yzc_list(const SimDesc& d, bool f32) {
+    const bool wide = f32 && (d.lPy == 5 || d.lPy == 9 || d.lPy == 13);
+    return d.nz + kYzcLists * (wide ? 1 : 0);
+}
+
 // Elements of a geometry's stored tensor:
 //   standard [ncomp][Pz/2+1][Py/2+1][Kx];
 //   blocked (cluster pass) [NBx][Py/2+1][Ty][qp], entry q = 6 kz + c, so the
@@ -114,7 +127,7 @@ inline size_t plan_xinv_smem(const SimDesc& d, size_t vsz) {
 }
 
 struct PlanItems {
-    std::vector<WorkItem> x, y13, z, y2, yzc[kMaxClusterPlanes + 1];
+    std::vector<WorkItem> x, y13, z, y2, yzc[2 * kYzcLists];
     size_t smem_x = 0, smem_xi = 0, smem_y13 = 0, smem_z = 0, smem_y2 = 0, smem_yzc = 0;
 };
 
@@ -127,7 +140,8 @@ inline void plan_items(const SimDesc& d, int sid, size_t vsz, PlanItems& P) {
     P.smem_xi = std::max(P.smem_xi, plan_xinv_smem(d, vsz));
     if (!(d.flags & F_DEMAG)) return;
     if (plan_uses_yzc(d)) {
-        for (int b = 0; b < d.NBx; ++b) P.yzc[d.nz].push_back({sid, 0, b, 0});
+        const int li = plan_yzc_list(d, vsz == 2 * sizeof(float));
+        for (int b = 0; b < d.NBx; ++b) P.yzc[li].push_back({sid, 0, b, 0});
         P.smem_yzc = std::max(P.smem_yzc, 3 * (size_t)d.Py * d.Ty * vsz);
     } else if (d.Pz > 1) {
         if (d.Py > 1) {

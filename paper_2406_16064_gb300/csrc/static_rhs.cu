@@ -114,7 +114,8 @@ extern "C" int mm_rhs_eval_static(const mm_mesh* mesh, const mm_material* mat, i
     const size_t vsz = 2 * e;
     PlanItems P;
     plan_items(d, 0, vsz, P);
-    const std::vector<WorkItem>& yzv = P.yzc[std::min(d.nz, kMaxClusterPlanes)];
+    const int yzl = plan_uses_yzc(d) ? plan_yzc_list(d, f32) : 0;
+    const std::vector<WorkItem>& yzv = P.yzc[yzl];
     const size_t cap = 227 * 1024;
     if (P.smem_x > cap - 4096 || P.smem_xi > cap - 4096 || P.smem_y13 > cap || P.smem_y2 > cap ||
         P.smem_z > cap || P.smem_yzc > cap)
@@ -196,7 +197,7 @@ extern "C" int mm_rhs_eval_static(const mm_mesh* mesh, const mm_material* mat, i
     L.y13 = {(const WorkItem*)(base + o_y13), (int)P.y13.size()};
     L.z = {(const WorkItem*)(base + o_z), (int)P.z.size()};
     L.y2 = {(const WorkItem*)(base + o_y2), (int)P.y2.size()};
-    if (!yzv.empty()) L.yzc[d.nz] = {(const WorkItem*)(base + o_yz), (int)yzv.size()};
+    if (!yzv.empty()) L.yzc[yzl] = {(const WorkItem*)(base + o_yz), (int)yzv.size()};
     L.smem_x = P.smem_x;
     L.smem_xi = P.smem_xi;
     L.smem_y13 = P.smem_y13;
