@@ -203,6 +203,34 @@ __device__ __forceinline__ V2<T> small_twid(int r, int logM) {
     return w;
 }
 
+// a * (-i)^m (forward) or (+i)^m (INV): swaps and sign flips only
+template <typename T, bool INV>
+__device__ __forceinline__ V2<T> rot_quarter(V2<T> a, int m) {
+    switch (m & 3) {
+        case 0: return a;
+        case 1: return INV ? mk<T>(-a.y, a.x) : mk<T>(a.y, -a.x);
+        case 2: return mk<T>(-a.x, -a.y);
+        default: return INV ? mk<T>(a.y, -a.x) : mk<T>(-a.y, a.x);
+    }
+}
+
+// a * W_32^q (INV: conjugate) for q fixed at compile time after unrolling:
+// quarter turns cost no arithmetic, odd eighth turns two adds and two
+// multiplies by sqrt(1/2), the rest a full complex product.  (IEEE rules keep
+// the compiler from folding the zero and unit parts of a general product, and
+// FP64 arithmetic is scarce on GB300.)
+template <typename T, bool INV>
+__device__ __forceinline__ V2<T> cmul_tw32(V2<T> a, int q) {
+    q &= 31;
+    if ((q & 7) == 0) return rot_quarter<T, INV>(a, q >> 3);
+    if ((q & 3) == 0) {
+        const T h = (T)0.7071067811865475244008444;
+        const V2<T> b = INV ? mk<T>(h * (a.x - a.y), h * (a.x + a.y)) : mk<T>(h * (a.x + a.y), h * (a.y - a.x));
+        return rot_quarter<T, INV>(b, q >> 3);
+    }
+    return cmul(a, small_twid<T, INV>(q, 5));
+}
+
 template <typename T, int PZ, bool INV>
 __device__ __forceinline__ void reg_fft(V2<T> (&x)[PZ], const V2<T>* __restrict__ tw) {
     constexpr int LG = Log2<PZ>::v;
@@ -216,8 +244,8 @@ __device__ __forceinline__ void reg_fft(V2<T> (&x)[PZ], const V2<T>* __restrict_
         for (int base = 0; base < PZ; base += 2 * s) {
 #pragma unroll
             for (int r = 0; r < s; ++r) {
-                const V2<T> w = small_twid<T, INV>(r, lg + 1);
-                const V2<T> a = y[base + r], b = r == 0 ? y[base + r + s] : cmul(y[base + r + s], w);
+                // W_{2s}^r = W_32^(r 32 / 2s)
+                const V2<T> a = y[base + r], b = cmul_tw32<T, INV>(y[base + r + s], r << (4 - lg));
                 y[base + r] = a + b;
                 y[base + r + s] = a - b;
             }
@@ -338,7 +366,7 @@ __device__ __forceinline__ void dit_group(V2<T>* buf, int lL, int lg, int nseq, 
             for (int m = 0; m < M; ++m) {
                 if (m & h) continue;
                 const int u = m & (h - 1);
-                const V2<T> w = u ? cmul(wb, small_twid<T, INV>(u, t + 1)) : wb;
+                const V2<T> w = u ? cmul_tw32<T, INV>(wb, u << (4 - t)) : wb;   // wb W_{2^(t+1)}^u
                 const V2<T> a = v[m], b = cmul(v[m + h], w);
                 v[m] = a + b;
                 if (!(HOUT && t == G - 1)) v[m + h] = a - b;
@@ -376,7 +404,7 @@ __device__ __forceinline__ void dif_group(V2<T>* buf, int lL, int lS, int nseq, 
             for (int m = 0; m < M; ++m) {
                 if (m & h) continue;
                 const int u = m & (h - 1);
-                const V2<T> w = u ? cmul(wb, small_twid<T, INV>(u, t + 1)) : wb;
+                const V2<T> w = u ? cmul_tw32<T, INV>(wb, u << (4 - t)) : wb;   // wb W_{2^(t+1)}^u
                 if (ZIN && t == G - 1) {
                     v[m + h] = cmul(v[m], w);        // b = 0: a + b = a, (a - b) w = a w
                 } else {
