@@ -81,6 +81,20 @@ def pad(n, min2=False):
     return p
 
 
+def tensor_bytes(s, e):
+    """Bytes of the stored demag tensor one right-hand side reads.  Films of 2..8 planes
+    (cluster pass) convolve along z directly: xx, yy, zz, xy at dz = 0..nz-1 and xz, yz
+    at dz = 1..nz-1 per (kx, ky >= 0) bin; other meshes: ncomp components at the kz <= Pz/2
+    bins."""
+    nx, ny, nz = s.mesh.nx, s.mesh.ny, s.mesh.nz
+    Px, Py, Pz = pad(nx, True), pad(ny), pad(nz)
+    Kx = Px // 2 + 1
+    if Pz > 1 and Py > 1 and nz <= 8:
+        return (4 * nz + 2 * (nz - 1)) * (Py // 2 + 1) * Kx * e
+    ncomp = 6 if Pz > 1 else 4
+    return ncomp * (Pz // 2 + 1) * (Py // 2 + 1) * Kx * e
+
+
 def kernel_bytes(w, e):
     """Compulsory bytes per attempt of each kernel kind: every stage vector, state, spectrum
     row and tensor value a kernel must read or write once (e = bytes of one real value).
@@ -99,8 +113,7 @@ def kernel_bytes(w, e):
         c = 2 * e                                    # one complex value
         spec_rows = 3 * nz * ny * Kx * c             # x-transform rows (ny of Py)
         spec_full = 3 * nz * Py * Kx * c             # all Py rows
-        ncomp = 6 if Pz > 1 else 4
-        tens = ncomp * (Pz // 2 + 1) * (Py // 2 + 1) * Kx * e
+        tens = tensor_bytes(s, e)
         demag = s.mat.demag
         for st in range(1, 8):
             out["x_forward"] += 3 * e * n * st + (3 * e * n if st > 1 else 0) + (3 * e * n if st == 7 else 0)
@@ -126,9 +139,7 @@ def step_bytes_survey(w, e):
     for s in w.sims:
         nx, ny, nz = s.mesh.nx, s.mesh.ny, s.mesh.nz
         Px, Py, Pz = pad(nx, True), pad(ny), pad(nz)
-        Kx = Px // 2 + 1
-        ncomp = 6 if Pz > 1 else 4
-        T = ncomp * e * (Kx * (Py // 2 + 1) * (Pz // 2 + 1)) / s.mesh.ncells if s.mat.demag else 0.0
+        T = tensor_bytes(s, e) / s.mesh.ncells if s.mat.demag else 0.0
         tot += (22.5 * e + T) * s.mesh.ncells * 7
     return tot
 

@@ -236,19 +236,22 @@ int precompute_geometry(mm_ctx* C, Geom& g, const SimDesc& d) {
     const size_t bytes = (size_t)d.Px * d.Py * d.Pz * 16;
     int rc = dalloc(C, &buf, bytes);
     if (rc) return rc;
-    const double scale = 1.0 / ((double)d.Px * d.Py * d.Pz);
-    // the spectrum of an even/odd real tensor is real: compare the largest imaginary
-    // part of any component with the largest real part of all of them
+    // films of the cluster pass convolve along z directly: their tensor is transformed
+    // along x and y only, one value per dz = 0..nz-1 (plan_tens_elems)
+    const bool blocked = plan_uses_yzc(d);
+    const double scale = blocked ? 1.0 / ((double)d.Px * d.Py) : 1.0 / ((double)d.Px * d.Py * d.Pz);
+    // the spectrum of an even/odd real tensor is real (along x, y only: xz, yz are
+    // imaginary): compare the largest discarded part with the largest kept part
     CK(cudaMemsetAsync(C->diag_d, 0, 2 * sizeof(unsigned long long), C->stream));
     for (int c = 0; c < d.ncomp; ++c) {
         launch_newell_place(C->stream, C->oct + g.oct_off, c, g.nx, g.ny, g.nz, d.Px, d.Py, d.Pz, buf);
-        for (int ax = 0; ax < 3; ++ax) launch_fft_axis_f64(C->stream, buf, d.Px, d.Py, d.Pz, ax, C->twd);
+        for (int ax = 0; ax < (blocked ? 2 : 3); ++ax)
+            launch_fft_axis_f64(C->stream, buf, d.Px, d.Py, d.Pz, ax, C->twd);
         char* out = (char*)C->tens + (size_t)g.tens_off * C->esz;
-        const bool blocked = plan_uses_yzc(d);
-        launch_newell_extract(C->stream, buf, c, d.Px, d.Py, d.Kx, d.Pyh, d.Pzh, scale, out,
-                              C->precision == MM_F32, blocked ? d.Ty : 0, yzc_qp(d.Pz), C->diag_d,
-                              C->diag_d + 1);
-        C->launches += 5;
+        launch_newell_extract(C->stream, buf, c, d.Px, d.Py, d.Kx, d.Pyh, blocked ? d.nz : d.Pzh, scale, out,
+                              C->precision == MM_F32, blocked ? d.Ty : 0, yzc_qp(d.nz), blocked ? 1 : 0,
+                              C->diag_d, C->diag_d + 1);
+        C->launches += blocked ? 4 : 5;
         CK(cudaGetLastError());
     }
     unsigned long long hb[2];

@@ -77,9 +77,11 @@ void launch_newell_octant(cudaStream_t s, int nx, int ny, int nz, double dx, dou
 void launch_newell_place(cudaStream_t s, const double* oct, int c, int nx, int ny, int nz, int Px, int Py, int Pz,
                          void* buf);
 void launch_fft_axis_f64(cudaStream_t s, void* buf, int Px, int Py, int Pz, int axis, const void* twd);
-// Ty > 0: the blocked layout of the cluster-fused y/z pass with qp values per bin
-void launch_newell_extract(cudaStream_t s, const void* buf, int c, int Px, int Py, int Kx, int Pyh, int Pzh,
-                           double scale, void* out, int is_f32, int Ty, int qp, unsigned long long* maxim,
-                           unsigned long long* maxre);
+// Ty > 0: the blocked layout of the cluster-fused y/z pass with qp values per bin;
+// nk: kz bins (Pz/2+1) or, for the cluster pass, the nz dz planes of an x-y
+// transformed buffer (imag_xz: xz and yz are imaginary there)
+void launch_newell_extract(cudaStream_t s, const void* buf, int c, int Px, int Py, int Kx, int Pyh, int nk,
+                           double scale, void* out, int is_f32, int Ty, int qp, int imag_xz,
+                           unsigned long long* maxim, unsigned long long* maxre);
 
 }  // namespace mm

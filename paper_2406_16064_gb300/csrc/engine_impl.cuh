@@ -33,6 +33,20 @@ static int wide_threads(size_t smem) {
     return nt < MM_THREADS ? MM_THREADS : nt;
 }
 
+// The cluster kernel for nz planes (2..8) and the column group width.
+template <typename T>
+static void (*yzc_kernel(int nz, bool wide))(PassParams<T>) {
+    switch (nz) {
+        case 2: return wide ? k_yzc<T, 2, true> : k_yzc<T, 2, false>;
+        case 3: return wide ? k_yzc<T, 3, true> : k_yzc<T, 3, false>;
+        case 4: return wide ? k_yzc<T, 4, true> : k_yzc<T, 4, false>;
+        case 5: return wide ? k_yzc<T, 5, true> : k_yzc<T, 5, false>;
+        case 6: return wide ? k_yzc<T, 6, true> : k_yzc<T, 6, false>;
+        case 7: return wide ? k_yzc<T, 7, true> : k_yzc<T, 7, false>;
+        default: return wide ? k_yzc<T, 8, true> : k_yzc<T, 8, false>;
+    }
+}
+
 template <typename T>
 static void issue_passes(const Launch& L, PassParams<T> p, const T* ys, bool include_xinv = true) {
     if (L.x.count == 0) return;
@@ -86,10 +100,8 @@ static void issue_passes(const Launch& L, PassParams<T> p, const T* ys, bool inc
         attr[0].val.clusterDim.z = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        // padded z length: the power of two >= 2 nz - 1; wide: 32-point column groups
-        if (nz == 2) cudaLaunchKernelEx(&cfg, wide ? k_yzc<T, 4, true> : k_yzc<T, 4, false>, p);
-        else if (nz <= 4) cudaLaunchKernelEx(&cfg, wide ? k_yzc<T, 8, true> : k_yzc<T, 8, false>, p);
-        else cudaLaunchKernelEx(&cfg, wide ? k_yzc<T, 16, true> : k_yzc<T, 16, false>, p);
+        // one instantiation per plane count; wide: 32-point column groups
+        cudaLaunchKernelEx(&cfg, yzc_kernel<T>(nz, wide), p);
         if (hk) hk->mark(KIND_YZC);
         ++n;
     }
@@ -221,12 +233,10 @@ static void set_attrs() {
     cudaFuncSetAttribute(k_ycol<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     cudaFuncSetAttribute(k_ycol<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     cudaFuncSetAttribute(k_zcol<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    cudaFuncSetAttribute(k_yzc<T, 4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    cudaFuncSetAttribute(k_yzc<T, 8, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    cudaFuncSetAttribute(k_yzc<T, 16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    cudaFuncSetAttribute(k_yzc<T, 4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    cudaFuncSetAttribute(k_yzc<T, 8, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    cudaFuncSetAttribute(k_yzc<T, 16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    for (int nz = 2; nz <= 8; ++nz) {
+        cudaFuncSetAttribute(yzc_kernel<T>(nz, false), cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        cudaFuncSetAttribute(yzc_kernel<T>(nz, true), cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    }
 }
 
 }  // namespace mm

@@ -11,9 +11,12 @@
 //          ncomp = 6 (xx yy zz xy xz yz) or 4 when Pz == 1 (xz = yz = 0),
 //          holding -N^(k)/(Px Py Pz); other bins follow from the parities
 //          of the Newell tensor (diagonal even, xy odd in kx and ky, xz odd
-//          in kx and kz, yz odd in ky and kz).  Geometries of the cluster-fused
-//          y/z pass store it blocked instead: [NBx][Py/2+1][Ty][yzc_qp(Pz)],
-//          entry 6 kz + c, so one column's values for one ky are contiguous.
+//          in kx and kz, yz odd in ky and kz).  Films of the cluster-fused y/z
+//          pass (2..8 planes) convolve along z directly and store the tensor
+//          transformed along x and y only, blocked: [NBx][Py/2+1][Ty][yzc_qp(nz)],
+//          entry 6 dz + c for dz = 0..nz-1 (-N^/(Px Py); xz and yz, odd in one of
+//          x, y, are imaginary there and stored as their imaginary parts; negative
+//          dz by the z parities), so one column's values for one ky are contiguous.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -95,9 +98,9 @@ struct SimState {
 struct WorkItem { int sim, a, b, c; };
 
 // Tensor values per (kx, ky) bin in the blocked layout of the cluster-fused
-// y/z pass: the 6 components of the Pz/2+1 kz bins, padded to a multiple of 4
-// for 16-byte vector loads.
-__host__ __device__ constexpr int yzc_qp(int Pz) { return ((6 * (Pz / 2 + 1) + 3) / 4) * 4; }
+// y/z pass: the 6 components at the dz = 0..nz-1 plane offsets, padded to a
+// multiple of 4 for 16-byte vector loads.
+__host__ __device__ constexpr int yzc_qp(int nz) { return ((6 * nz + 3) / 4) * 4; }
 
 template <typename T> struct alignas(2 * sizeof(T)) V2 { T x, y; };
 

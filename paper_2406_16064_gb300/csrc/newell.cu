@@ -219,31 +219,39 @@ __global__ void k_fft_axis_f64(double2* buf, int Px, int Py, int Pz, int axis, i
     }
 }
 
-// out[c][kzh][kyh][kx] = -Re(buf[kzh][kyh][kx]) * scale; tracks max |Im| / max |Re|
+// Stored tensor values of component c from the transformed buffer:
+//   3-D (Ty = 0 or imag_xz = 0 and nk = Pz/2+1): -Re(buf[kz][ky][kx]) * scale for the
+//   kz <= Pz/2 bins (the spectrum of an even/odd real tensor is real);
+//   films of the cluster pass (nk = nz planes, x and y transformed only):
+//   -Re * scale for xx, yy, zz, xy (even in x and y, or odd in both: real) and
+//   -Im * scale for xz, yz when imag_xz (odd in exactly one of x, y: imaginary),
+//   one value per dz = kz < nz.
+// Layout: standard [c][kz][ky][kx]; blocked (Ty > 0) [kx / Ty][ky][kx % Ty][6 kz + c].
+// maxim / maxre track the largest discarded and kept parts.
 template <typename T>
 __global__ void k_newell_extract(const double2* __restrict__ buf, int c, int Px, int Py, int Kx, int Pyh,
-                                 int Pzh, double scale, T* out, int Ty, int qp, unsigned long long* maxim,
-                                 unsigned long long* maxre) {
-    const long long tot = (long long)Kx * Pyh * Pzh;
+                                 int nk, double scale, T* out, int Ty, int qp, int imag_xz,
+                                 unsigned long long* maxim, unsigned long long* maxre) {
+    const long long tot = (long long)Kx * Pyh * nk;
+    const bool im = imag_xz && (c == 4 || c == 5);
     for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < tot;
          id += (long long)gridDim.x * blockDim.x) {
         const int kx = (int)(id % Kx);
         const int ky = (int)((id / Kx) % Pyh);
         const int kz = (int)(id / ((long long)Kx * Pyh));
         const double2 v = buf[((long long)kz * Py + ky) * Px + kx];
-        // standard [c][kz][ky][kx]; blocked (Ty > 0) [kx / Ty][ky][kx % Ty][6 kz + c]
+        const double keep = im ? v.y : v.x, drop = im ? v.x : v.y;
         const long long o = Ty > 0 ? (((long long)(kx / Ty) * Pyh + ky) * Ty + kx % Ty) * qp + 6 * kz + c
                                    : (long long)c * tot + id;
-        out[o] = (T)(-v.x * scale);
-        atomicMax(maxim, (unsigned long long)__double_as_longlong(fabs(v.y)));
-        atomicMax(maxre, (unsigned long long)__double_as_longlong(fabs(v.x)));
+        out[o] = (T)(-keep * scale);
+        atomicMax(maxim, (unsigned long long)__double_as_longlong(fabs(drop)));
+        atomicMax(maxre, (unsigned long long)__double_as_longlong(fabs(keep)));
     }
 }
-
 template __global__ void k_newell_extract<float>(const double2*, int, int, int, int, int, int, double, float*,
-                                                  int, int, unsigned long long*, unsigned long long*);
+                                                  int, int, int, unsigned long long*, unsigned long long*);
 template __global__ void k_newell_extract<double>(const double2*, int, int, int, int, int, int, double, double*,
-                                                   int, int, unsigned long long*, unsigned long long*);
+                                                   int, int, int, unsigned long long*, unsigned long long*);
 
 // twiddle tables: exp(-2 pi i k / LMAX) for k < LMAX, then the stage tables
 // W_M^(k r) (layout: stw_base in mm_kernels.cuh), all from FP64 sincospi of the
@@ -353,18 +361,20 @@ void launch_fft_axis_f64(cudaStream_t s, void* buf, int Px, int Py, int Pz, int 
                                                        reinterpret_cast<const V2<double>*>(twd));
 }
 
-void launch_newell_extract(cudaStream_t s, const void* buf, int c, int Px, int Py, int Kx, int Pyh, int Pzh,
-                           double scale, void* out, int is_f32, int Ty, int qp, unsigned long long* maxim,
-                           unsigned long long* maxre) {
-    const long long n = (long long)Kx * Pyh * Pzh;
+void launch_newell_extract(cudaStream_t s, const void* buf, int c, int Px, int Py, int Kx, int Pyh, int nk,
+                           double scale, void* out, int is_f32, int Ty, int qp, int imag_xz,
+                           unsigned long long* maxim, unsigned long long* maxre) {
+    const long long n = (long long)Kx * Pyh * nk;
     const long long blocks = (n + 255) / 256;
     const int g = (int)(blocks < 1048576 ? blocks : 1048576);
     if (is_f32)
-        k_newell_extract<float><<<g, 256, 0, s>>>(reinterpret_cast<const double2*>(buf), c, Px, Py, Kx, Pyh, Pzh,
-                                                   scale, reinterpret_cast<float*>(out), Ty, qp, maxim, maxre);
+        k_newell_extract<float><<<g, 256, 0, s>>>(reinterpret_cast<const double2*>(buf), c, Px, Py, Kx, Pyh, nk,
+                                                   scale, reinterpret_cast<float*>(out), Ty, qp, imag_xz, maxim,
+                                                   maxre);
     else
-        k_newell_extract<double><<<g, 256, 0, s>>>(reinterpret_cast<const double2*>(buf), c, Px, Py, Kx, Pyh, Pzh,
-                                                    scale, reinterpret_cast<double*>(out), Ty, qp, maxim, maxre);
+        k_newell_extract<double><<<g, 256, 0, s>>>(reinterpret_cast<const double2*>(buf), c, Px, Py, Kx, Pyh, nk,
+                                                    scale, reinterpret_cast<double*>(out), Ty, qp, imag_xz, maxim,
+                                                    maxre);
 }
 
 }  // namespace mm

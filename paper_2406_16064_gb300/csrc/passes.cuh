@@ -384,13 +384,21 @@ __device__ __forceinline__ void load_bin(const double* __restrict__ q, double (&
     }
 }
 
-template <typename T, int PZ>
-__device__ void yzc_zstep(const PassParams<T>& p, const SimDesc& d, V2<T>* const (&rem)[8], int rank, int nz,
-                          int es, int b, int ncols) {
-    constexpr int QP = yzc_qp(PZ);
+// z step of the cluster pass: for every (ky row, kx column) of this CTA's
+// share, gather the NZ planes' values from the cluster's shared memories and
+// convolve along z directly, H(z) = sum_z' N^(kx, ky, z - z') M(z') (Eq. 8 with
+// the z sum written out: for NZ <= 8 planes this costs fewer operations than a
+// zero-padded length-2 NZ FFT pair plus the product), then scatter H back.
+// The stored tensor holds dz >= 0; negative offsets follow from the z parities
+// (xz, yz odd); xz and yz are imaginary in (kx, ky, dz) and stored as t with
+// N^ = i t; the ky fold flips xy and yz.
+template <typename T, int NZ>
+__device__ void yzc_zstep(const PassParams<T>& p, const SimDesc& d, V2<T>* const (&rem)[8], int rank, int es,
+                          int b, int ncols) {
+    constexpr int QP = yzc_qp(NZ);
     const int TT = d.Ty, lT = d.lTy, Py = d.Py;
-    const int ky_lo = (int)(((long long)rank * Py) / nz);    // share of rows
-    const int ky_hi = (int)(((long long)(rank + 1) * Py) / nz);
+    const int ky_lo = (int)(((long long)rank * Py) / NZ);    // share of rows
+    const int ky_hi = (int)(((long long)(rank + 1) * Py) / NZ);
     const int nwork = (ky_hi - ky_lo) << lT;
     const T* __restrict__ tb = p.tensor + d.tens_off + (long long)b * d.Pyh * TT * QP;
     for (int id = threadIdx.x; id < nwork; id += blockDim.x) {
@@ -398,56 +406,86 @@ __device__ void yzc_zstep(const PassParams<T>& p, const SimDesc& d, V2<T>* const
         const int r = ky_lo + (id >> lT);              // row of the bit-reversed y spectrum
         const int ky = bitrev(r, d.lPy);
         if (col >= ncols) continue;
-        // tensor of bin (kx0 + col, ky): H = T M per kz; the ky fold (kyh = Py - ky,
-        // xy and yz odd in ky) is per item, the kz fold compile time
         const bool fy = ky > (Py >> 1);
         const int kyh = fy ? Py - ky : ky;
         const T sy = fy ? (T)-1 : (T)1;
-        T tv[QP];
-        load_bin<QP>(tb + ((long long)kyh * TT + col) * QP, tv);
-        V2<T> X[3][PZ];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-#pragma unroll
-            for (int k = 0; k < PZ; ++k) X[c][k] = mk<T>((T)0, (T)0);
-        }
         const int o = r * es + col;
+        const T* __restrict__ tq = tb + ((long long)kyh * TT + col) * QP;
+        V2<T> M[NZ][3];
 #pragma unroll
-        for (int zz = 0; zz < 8; ++zz) {
-            if (zz < nz && zz < PZ) {
+        for (int z = 0; z < NZ; ++z) {
 #pragma unroll
-                for (int c = 0; c < 3; ++c) X[c][zz] = rem[zz][o + c * TT];
-            }
+            for (int c = 0; c < 3; ++c) M[z][c] = rem[z][o + c * TT];
         }
+        if constexpr (NZ >= 6) {
+            // many planes: offsets dz outermost, so only one offset's six tensor
+            // values are live next to the NZ accumulators
+            V2<T> H[NZ][3];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) reg_fft<T, PZ, false>(X[c], p.tw);
+            for (int z = 0; z < NZ; ++z) {
 #pragma unroll
-        for (int kz = 0; kz < PZ; ++kz) {
-            const int kzh = kz <= PZ / 2 ? kz : PZ - kz;
-            const T sz = kz <= PZ / 2 ? (T)1 : (T)-1;
-            const T* t = tv + 6 * kzh;
-            const T xx = t[0], yy = t[1], zz = t[2];
-            const T xy = sy * t[3], xz = sz * t[4], yz = sy * sz * t[5];
-            const V2<T> a = X[0][kz], bb = X[1][kz], c = X[2][kz];
-            X[0][kz] = mk<T>(xx * a.x + xy * bb.x + xz * c.x, xx * a.y + xy * bb.y + xz * c.y);
-            X[1][kz] = mk<T>(xy * a.x + yy * bb.x + yz * c.x, xy * a.y + yy * bb.y + yz * c.y);
-            X[2][kz] = mk<T>(xz * a.x + yz * bb.x + zz * c.x, xz * a.y + yz * bb.y + zz * c.y);
-        }
-#pragma unroll
-        for (int c = 0; c < 3; ++c) reg_fft<T, PZ, true>(X[c], p.tw);
-#pragma unroll
-        for (int zz = 0; zz < 8; ++zz) {
-            if (zz < nz && zz < PZ) {
-#pragma unroll
-                for (int c = 0; c < 3; ++c) rem[zz][o + c * TT] = X[c][zz];
+                for (int c = 0; c < 3; ++c) H[z][c] = mk<T>((T)0, (T)0);
             }
+#pragma unroll
+            for (int dz = 0; dz < NZ; ++dz) {
+                const T* t = tq + 6 * dz;
+                const T xx = t[0], yy = t[1], zz = t[2], xy = sy * t[3], xzp = t[4], yzp = sy * t[5];
+#pragma unroll
+                for (int sgn = 0; sgn < 2; ++sgn) {
+                    if (sgn == 1 && dz == 0) continue;
+                    const T xz = sgn ? -xzp : xzp, yz = sgn ? -yzp : yzp;   // odd in z
+#pragma unroll
+                    for (int z2 = 0; z2 + dz < NZ; ++z2) {
+                        // sgn 0: z = z2 + dz (offset +dz); sgn 1: z = z2, source z2 + dz (offset -dz)
+                        const int z = sgn ? z2 : z2 + dz, zs = sgn ? z2 + dz : z2;
+                        const V2<T> a = M[zs][0], bb = M[zs][1], c = M[zs][2];
+                        H[z][0].x += xx * a.x + xy * bb.x - xz * c.y;
+                        H[z][0].y += xx * a.y + xy * bb.y + xz * c.x;
+                        H[z][1].x += xy * a.x + yy * bb.x - yz * c.y;
+                        H[z][1].y += xy * a.y + yy * bb.y + yz * c.x;
+                        H[z][2].x += zz * c.x - xz * a.y - yz * bb.y;
+                        H[z][2].y += zz * c.y + xz * a.x + yz * bb.x;
+                    }
+                }
+            }
+#pragma unroll
+            for (int z = 0; z < NZ; ++z) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) rem[z][o + c * TT] = H[z][c];
+            }
+            continue;
+        }
+        T tv[QP];
+        load_bin<QP>(tq, tv);
+#pragma unroll
+        for (int z = 0; z < NZ; ++z) {
+            V2<T> H0 = mk<T>((T)0, (T)0), H1 = H0, H2 = H0;
+#pragma unroll
+            for (int z2 = 0; z2 < NZ; ++z2) {
+                const int dz = z - z2 >= 0 ? z - z2 : z2 - z;
+                const T so = z - z2 >= 0 ? (T)1 : (T)-1;        // xz, yz odd in z
+                const T* t = tv + 6 * dz;
+                const T xx = t[0], yy = t[1], zz = t[2], xy = sy * t[3];
+                const T xz = so * t[4], yz = so * sy * t[5];     // N^xz = i xz, N^yz = i yz
+                const V2<T> a = M[z2][0], bb = M[z2][1], c = M[z2][2];
+                H0.x += xx * a.x + xy * bb.x - xz * c.y;
+                H0.y += xx * a.y + xy * bb.y + xz * c.x;
+                H1.x += xy * a.x + yy * bb.x - yz * c.y;
+                H1.y += xy * a.y + yy * bb.y + yz * c.x;
+                H2.x += zz * c.x - xz * a.y - yz * bb.y;
+                H2.y += zz * c.y + xz * a.x + yz * bb.x;
+            }
+            rem[z][o] = H0;
+            rem[z][o + TT] = H1;
+            rem[z][o + 2 * TT] = H2;
         }
     }
 }
 
 // FP32: two clusters' CTAs per SM (128 registers); FP64 keeps the registers it needs.
-// WIDE: 32-point register groups for the y columns (FP32; see plan_yzc_list).
-template <typename T, int PZ, bool WIDE>
+// NZ: planes (= cluster size); WIDE: 32-point register groups for the y columns
+// (FP32; see plan_yzc_list).
+template <typename T, int NZ, bool WIDE>
 __global__ void __launch_bounds__(MM_THREADS, sizeof(T) == 4 ? 2 : 1) k_yzc(PassParams<T> p) {
     namespace cg = cooperative_groups;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -493,7 +531,7 @@ __global__ void __launch_bounds__(MM_THREADS, sizeof(T) == 4 ? 2 : 1) k_yzc(Pass
     V2<T>* rem[8];
 #pragma unroll
     for (int zz = 0; zz < 8; ++zz) rem[zz] = zz < nz ? cl.map_shared_rank(sm, zz) : sm;
-    yzc_zstep<T, PZ>(p, d, rem, rank, nz, es, b, ncols);   // PZ == d.Pz, fixed by nz per launch
+    yzc_zstep<T, NZ>(p, d, rem, rank, es, b, ncols);   // NZ == d.nz, fixed per launch
     cl.sync();                                  // every row back in its owner's plane
     fft_dit<T, true, false, true, GMC>(sm, lL, es, 1, es, p.tw);    // bit-reversed in, natural out
 #pragma unroll

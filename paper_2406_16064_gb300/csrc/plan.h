@@ -112,10 +112,11 @@ inline int plan_yzc_list(const SimDesc& d, bool f32) {
 
 // Elements of a geometry's stored tensor:
 //   standard [ncomp][Pz/2+1][Py/2+1][Kx];
-//   blocked (cluster pass) [NBx][Py/2+1][Ty][qp], entry q = 6 kz + c, so the
-//   values one column of one ky row needs are contiguous.
+//   blocked (cluster pass) [NBx][Py/2+1][Ty][qp], entry q = 6 dz + c for the
+//   plane offsets dz = 0..nz-1, so the values one column of one ky row needs
+//   are contiguous.
 inline long long plan_tens_elems(const SimDesc& d) {
-    if (plan_uses_yzc(d)) return (long long)d.NBx * d.Pyh * d.Ty * yzc_qp(d.Pz);
+    if (plan_uses_yzc(d)) return (long long)d.NBx * d.Pyh * d.Ty * yzc_qp(d.nz);
     return (long long)d.ncomp * d.Pzh * d.Pyh * d.Kx;
 }
 

@@ -168,15 +168,16 @@ extern "C" int mm_rhs_eval_static(const mm_mesh* mesh, const mm_material* mat, i
         double* oct = (double*)(base + o_oct);
         void* fftbuf = base + o_fft;
         launch_newell_octant(s, d.nx, d.ny, d.nz, d.dx, d.dy, d.dz, oct);
-        const double scale = 1.0 / ((double)d.Px * d.Py * d.Pz);
+        const int Tyb = plan_uses_yzc(d) ? d.Ty : 0;   // cluster-pass film: x-y transform, dz planes
+        const double scale = Tyb ? 1.0 / ((double)d.Px * d.Py) : 1.0 / ((double)d.Px * d.Py * d.Pz);
         unsigned long long* diag = (unsigned long long*)(base + o_diag);
         SCK(cudaMemsetAsync(base + o_tens, 0, (size_t)tens_elems * e, s));   // padding of a blocked tensor
-        const int Tyb = plan_uses_yzc(d) ? d.Ty : 0;
         for (int c = 0; c < d.ncomp; ++c) {
             launch_newell_place(s, oct, c, d.nx, d.ny, d.nz, d.Px, d.Py, d.Pz, fftbuf);
-            for (int ax = 0; ax < 3; ++ax) launch_fft_axis_f64(s, fftbuf, d.Px, d.Py, d.Pz, ax, base + o_twd);
-            launch_newell_extract(s, fftbuf, c, d.Px, d.Py, d.Kx, d.Pyh, d.Pzh, scale, base + o_tens, f32, Tyb,
-                                  yzc_qp(d.Pz), diag, diag + 1);
+            for (int ax = 0; ax < (Tyb ? 2 : 3); ++ax)
+                launch_fft_axis_f64(s, fftbuf, d.Px, d.Py, d.Pz, ax, base + o_twd);
+            launch_newell_extract(s, fftbuf, c, d.Px, d.Py, d.Kx, d.Pyh, Tyb ? d.nz : d.Pzh, scale, base + o_tens,
+                                  f32, Tyb, yzc_qp(d.nz), Tyb ? 1 : 0, diag, diag + 1);
         }
         SCK(cudaGetLastError());
         unsigned long long hb[2];
