@@ -17,16 +17,18 @@
 //            kx block, CTA z owning plane z.  Each CTA transforms its plane
 //            along y; after a cluster barrier every CTA takes a share of the
 //            ky rows, gathers the nz planes from its peers' shared memory
-//            (distributed shared memory), does the zero-padded z FFT in
-//            registers, the tensor product and the inverse z FFT, and scatters
-//            the nz planes back; after a second barrier each CTA inverts its
-//            plane along y.  Replaces y forward + z + y inverse.
+//            (distributed shared memory), convolves them along z directly
+//            with the tensor of the x-y transformed Newell kernel (Eq. 8 with
+//            the z sum written out), and scatters the nz planes back; after a
+//            second barrier each CTA inverts its plane along y.  Replaces
+//            y forward + z + y inverse.
 //   k_xinv   complex-to-real inverse FFT along x (only the nx outputs), then
 //            per cell: exchange (Eq. 5), interfacial DMI (Eq. 14), uniaxial
 //            and cubic anisotropy, Zeeman, the LL torque (LL form of the
 //            LLG equation), optional H_eff, the stage-1 max|dm/dt| and the
-//            stage-7 embedded error norm (FP64 ordered-bit max reductions),
-//            or the energies (FP64 sums) in energy mode.
+//            stage-7 embedded error norm (ordered-bit max reductions, scaled
+//            and combined in FP64), or the energies (compensated per-thread
+//            sums, FP64 across threads) in energy mode.
 #pragma once
 #include <cooperative_groups.h>
 
