@@ -15,6 +15,8 @@ It is plain, slow and written to be checked by eye against the paper
              cubic anisotropy, Zeeman, energies, LL right-hand side
   integrate  adaptive Dormand-Prince RK45 with projection to |m|=1
   neb        geodesic nudged elastic band (Sec. "Miscellaneous")
+  minimize   steepest descent with Barzilai-Borwein steps (Sec. "Steepest
+             descent energy minimization")
 
 All arithmetic is float64.  Parity status of every function is listed in
 its module header.
