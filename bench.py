@@ -11,7 +11,10 @@ perpendicular anisotropy, ~200 reversed disks (FP32 path; the FP64 path is
 measured on the same workload and reported beside it).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                  [--workload film|film_relax_32|cube|neb|batch|sweep]
+                  [--workload film|film_relax_32|cube|neb|batch|sweep] [--driver rk45|sd]
+
+`--driver sd` times steepest-descent steps (one effective-field evaluation and
+the Barzilai-Borwein update each) instead of RK45 attempts.
 
 `--workload sweep` times the N x N x 1 family of the paper's throughput
 comparison (demag + exchange + Zeeman, N = 128 ... 4096, FP32) and reports each
@@ -148,13 +151,20 @@ def step_bytes_survey(w, e):
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic.md")
 
 
+# The sources that define (and instantiate) the kernels of the right-hand side
+# and of the RK45 attempt, whose DRAM counters profiles/dram_traffic.md records.
+KERNEL_SOURCES = ("control.cuh", "engine.cuh", "engine_f32.cu", "engine_f64.cu", "engine_impl.cuh",
+                  "mm_kernels.cuh", "passes.cuh", "plan.h")
+
+
 def source_fingerprint():
-    """Hash of every kernel source file: DRAM counters taken on other sources are stale."""
+    """Hash of the pass-kernel sources: DRAM counters taken on other sources are stale."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2406_16064_gb300", "csrc")
-    for fn in sorted(os.listdir(csrc)):
-        if fn.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(csrc, fn), "rb") as f:
+    for fn in KERNEL_SOURCES:
+        path = os.path.join(csrc, fn)
+        if os.path.exists(path):
+            with open(path, "rb") as f:
                 h.update(fn.encode())
                 h.update(f.read())
     return h.hexdigest()[:16]
@@ -445,6 +455,46 @@ def run_gpu(args, rank, world, dist):
     return line
 
 
+def run_sd(args, rank, world, dist):
+    """Steepest-descent steps (one effective-field evaluation each) on the workload."""
+    import torch
+    from paper_2406_16064_gb300 import mm
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream()
+    w = workload(args.workload, world)
+    if w.neb:
+        raise SystemExit("--driver sd: the NEB workload has its own driver")
+    prec = args.precision or ("f64" if args.workload == "film_relax_32" else "f32")
+    ctx = mm.Context(prec, stream=stream.cuda_stream)
+    for s in w.sims:
+        ctx.add_sim(s.mesh, s.mat, s.Ms_cells)
+    ctx.precompute()
+    m0 = np.concatenate([s.m0.ravel() for s in w.sims])
+    ctx.set_m(m0)
+    ctx.minimize(0.0, max_steps=args.warmup, sync_every=args.warmup)
+    ctx.set_m(m0)
+    n0 = ctx.launches()
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    with Clocks(dev) as clk:
+        start.record(stream)
+        ctx.minimize(0.0, max_steps=args.steps, sync_every=args.steps)
+        end.record(stream)
+        end.synchronize()
+    ms = start.elapsed_time(end)
+    ncell = cells(w)
+    line = {"metric": METRIC, "value": world * ncell * args.steps / (ms / 1e3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": prec, "data": "synthetic",
+            "config": {"workload": w.name, "cells": ncell, "driver": "steepest_descent (1 field evaluation a step)",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "clocks": clk.summary(), "gpu_launches": ctx.launches() - n0}
+    ctx.close()
+    return line
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -456,6 +506,7 @@ def main():
     ap.add_argument("--no-f64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--sweep-n", default=None, help="comma-separated N for --workload sweep")
+    ap.add_argument("--driver", default="rk45", help="rk45 (default) or sd (steepest-descent steps)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -469,7 +520,10 @@ def main():
             import torch.distributed as dist
             torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
             dist.init_process_group("nccl")
-        line = (run_sweep if args.workload == "sweep" else run_gpu)(args, rank, world, dist)
+        if args.driver == "sd":
+            line = run_sd(args, rank, world, dist)
+        else:
+            line = (run_sweep if args.workload == "sweep" else run_gpu)(args, rank, world, dist)
         if dist:
             dist.destroy_process_group()
     if rank == 0 and line is not None:

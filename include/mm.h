@@ -169,6 +169,30 @@ int mm_neb_setup(mm_ctx *ctx, int first_sim, int n_images, double k_spring);
  * host) receives the energy of every simulation afterwards. */
 int mm_neb_relax(mm_ctx *ctx, double rtol, long long n_steps, double *energies_out);
 
+/* Steepest-descent energy minimisation of every simulation (Sec. "Steepest
+ * descent energy minimization"): per cell, with f = m x H_eff and
+ * g = m x (m x H_eff), m_{k+1} = ((1 - a) m_k - tau_k g_k) / (1 + a),
+ * a = tau_k^2 |f|^2 / 4 (the paper's explicit form of its norm-preserving
+ * midpoint step), and Barzilai-Borwein step sizes from the sums over a
+ * simulation's cells, tau^1 = s.s / s.y on odd steps and tau^2 = s.y / y.y on
+ * even ones (s = m_k - m_{k-1}, y = g_k - g_{k-1}); tau_0 = 0.01 / max|g|; a
+ * rule that is not positive keeps the previous tau.  Starts from the current m
+ * (mm_set_m) with no history; a simulation stops once max|dm/dt| of its LL
+ * right-hand side (material alpha, gamma, precession flag) falls below
+ * max_dmdt rad/s (0: never).  Runs at most max_steps steps, checking every
+ * sync_every steps; steps_done (nullable) receives the largest step count,
+ * converged (nullable) 1 if every simulation stopped on the criterion.  The
+ * step sums are FP64 (compensated per thread in FP32 contexts), tau is FP64,
+ * the update runs in the context precision and is followed by the projection
+ * onto |m| = 1 (the update keeps |m| only in exact arithmetic).  Returns
+ * MM_ENAN on a non-finite field and MM_EINVAL in a context with NEB chains.
+ * Leaves the RK45 state (t, h) untouched. */
+int mm_minimize(mm_ctx *ctx, double max_dmdt, long long max_steps, int sync_every, long long *steps_done,
+                int *converged);
+/* Last minimiser state of one simulation: steps taken, tau (m/A), max|dm/dt|
+ * (rad/s) at the last step's m, status (0 running, 2 converged, -4 NaN). */
+int mm_minimize_info(mm_ctx *ctx, int sim_id, long long *steps, double *tau, double *max_dmdt, int *status);
+
 /* Profiling aid: runs `reps` RK45 attempts (NEB attempts in a context with
  * chains) with direct launches (no graph) and a CUDA event recorded on the
  * context stream after every kernel kind.

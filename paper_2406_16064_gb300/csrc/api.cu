@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "engine.cuh"
+#include "minimize.h"
 #include "mm.h"
 #include "plan.h"
 
@@ -70,6 +71,11 @@ struct mm_ctx {
     unsigned long long* diag_d = nullptr;
     cudaGraphExec_t rk_exec = nullptr;
     bool rk_exec_neb = false;
+    // steepest-descent minimiser: buffers, per-simulation state, one captured step
+    void *sd_H = nullptr, *sd_mprev = nullptr, *sd_g = nullptr;
+    SdState* sd_d = nullptr;
+    cudaGraphExec_t sd_exec = nullptr;
+    long long sd_graph_kernels = 0;
     long long graph_kernels = 0;
     long long launches = 0;
     bool neb = false;
@@ -323,6 +329,41 @@ int launch_attempts(mm_ctx* C, long long n) {
     return MM_OK;
 }
 
+// Buffers of the minimiser and one captured step (the step reads everything it
+// needs from device memory, so the graph stays valid for every call).
+int sd_prepare(mm_ctx* C) {
+    int rc;
+    const size_t sb = (size_t)C->total_elems * C->esz;
+    if (!C->sd_H) {
+        if ((rc = ensure_scratch(C))) return rc;
+        if ((rc = dalloc(C, &C->sd_H, sb))) return rc;
+        if ((rc = dalloc(C, &C->sd_mprev, sb))) return rc;
+        if ((rc = dalloc(C, &C->sd_g, sb))) return rc;
+        if ((rc = dalloc(C, (void**)&C->sd_d, C->sims.size() * sizeof(SdState)))) return rc;
+    }
+    if (C->sd_exec) return MM_OK;
+    Launch L = make_launch(C, -1);
+    SdBuffers B;
+    B.m = C->m;
+    B.H = C->sd_H;
+    B.dmdt = C->sc_out;
+    B.mprev = C->sd_mprev;
+    B.gprev = C->sd_g;
+    B.sd = C->sd_d;
+    const long long before = C->launches;
+    cudaGraph_t g;
+    CK(cudaStreamBeginCapture(C->stream, cudaStreamCaptureModeThreadLocal));
+    if (C->precision == MM_F32) sd_step<float>(L, B); else sd_step<double>(L, B);
+    cudaError_t e = cudaStreamEndCapture(C->stream, &g);
+    if (e != cudaSuccess) return fail(C, MM_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&C->sd_exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(C, MM_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    C->sd_graph_kernels = C->launches - before;
+    C->launches = before;
+    return MM_OK;
+}
+
 int first_error(mm_ctx* C, const std::vector<SimState>& st) {
     for (size_t i = 0; i < st.size(); ++i) {
         if (st[i].status < 0) {
@@ -372,9 +413,11 @@ int mm_destroy(mm_ctx* C) {
     cudaSetDevice(C->device);
     if (C->stream) cudaStreamSynchronize(C->stream);
     if (C->rk_exec) cudaGraphExecDestroy(C->rk_exec);
+    if (C->sd_exec) cudaGraphExecDestroy(C->sd_exec);
     void* ptrs[] = {C->m, C->ybuf, C->errp, C->spec, C->Msd, C->tens, C->twd, C->twf, C->sc_in, C->sc_out,
                     C->sc_h, C->heff, C->tau, C->kvec_dev, C->oct, C->desc_d, C->state_d, C->xi, C->y13i,
-                    C->zi, C->y2i, C->flag_d, C->status_d, C->diag_d};
+                    C->zi, C->y2i, C->flag_d, C->status_d, C->diag_d, C->sd_H, C->sd_mprev, C->sd_g,
+                    C->sd_d};
     for (void* p : ptrs) if (p) cudaFree(p);
     for (int j = 0; j < 7; ++j) if (C->k[j]) cudaFree(C->k[j]);
     for (int li = 0; li < 2 * kYzcLists; ++li) if (C->yzci[li]) cudaFree(C->yzci[li]);
@@ -788,6 +831,70 @@ int mm_relax(mm_ctx* C, double rtol, double t_end, double max_dmdt, long long ma
         if (!live) break;
     }
     if (done) *done = att;
+    return MM_OK;
+}
+
+int mm_minimize(mm_ctx* C, double max_dmdt, long long max_steps, int sync_every, long long* steps_done,
+                int* converged) {
+    int rc = check_ready(C);
+    if (rc) return rc;
+    if (C->neb) return fail(C, MM_EINVAL, "mm_minimize: not in a context with NEB chains");
+    if (!(max_dmdt >= 0.0) || max_steps < 0) return fail(C, MM_EINVAL, "mm_minimize: bad arguments");
+    if (sync_every < 1) sync_every = 1;
+    if ((rc = sd_prepare(C))) return rc;
+    // fresh state: tau_0 at the first step, zero history
+    std::vector<SdState> h(C->sims.size());
+    for (size_t i = 0; i < C->sims.size(); ++i) {
+        const mm_material& mt = C->sims[i].mat;
+        SdState z;
+        memset(&z, 0, sizeof(z));
+        const double gt = mt.gamma / (1.0 + mt.alpha * mt.alpha);
+        z.dmdt_scale = gt * (mt.precession ? std::sqrt(1.0 + mt.alpha * mt.alpha) : mt.alpha);
+        z.stop_dmdt = max_dmdt;
+        z.max_dmdt = HUGE_VAL;
+        h[i] = z;
+    }
+    const size_t sb = (size_t)C->total_elems * C->esz;
+    CK(cudaMemcpyAsync(C->sd_d, h.data(), h.size() * sizeof(SdState), cudaMemcpyHostToDevice, C->stream));
+    CK(cudaMemsetAsync(C->sd_mprev, 0, sb, C->stream));
+    CK(cudaMemsetAsync(C->sd_g, 0, sb, C->stream));
+    long long done = 0;
+    while (done < max_steps) {
+        const long long n = std::min<long long>(sync_every, max_steps - done);
+        for (long long i = 0; i < n; ++i) CK(cudaGraphLaunch(C->sd_exec, C->stream));
+        C->launches += n * C->sd_graph_kernels;
+        done += n;
+        CK(cudaMemcpyAsync(h.data(), C->sd_d, h.size() * sizeof(SdState), cudaMemcpyDeviceToHost, C->stream));
+        CK(cudaStreamSynchronize(C->stream));
+        bool live = false;
+        for (size_t i = 0; i < h.size(); ++i) {
+            if (h[i].status < 0) return fail(C, MM_ENAN, "mm_minimize: simulation %zu: non-finite field", i);
+            live |= h[i].status == 0;
+        }
+        if (!live) break;
+    }
+    long long kmax = 0;
+    bool all = true;
+    for (const SdState& s : h) {
+        kmax = std::max(kmax, s.k);
+        all &= s.status == 2;
+    }
+    if (steps_done) *steps_done = kmax;
+    if (converged) *converged = all ? 1 : 0;
+    return MM_OK;
+}
+
+int mm_minimize_info(mm_ctx* C, int sim, long long* steps, double* tau, double* max_dmdt, int* status) {
+    if (!C) return MM_EINVAL;
+    if (sim < 0 || sim >= (int)C->sims.size()) return fail(C, MM_EINVAL, "bad sim id");
+    if (!C->sd_d) return fail(C, MM_EINVAL, "mm_minimize_info: mm_minimize has not run");
+    SdState s;
+    CK(cudaMemcpyAsync(&s, C->sd_d + sim, sizeof(s), cudaMemcpyDeviceToHost, C->stream));
+    CK(cudaStreamSynchronize(C->stream));
+    if (steps) *steps = s.k;
+    if (tau) *tau = s.tau;
+    if (max_dmdt) *max_dmdt = s.max_dmdt;
+    if (status) *status = s.status;
     return MM_OK;
 }
 

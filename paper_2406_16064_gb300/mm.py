@@ -65,6 +65,9 @@ SIGNATURES = {
     "mm_energy": (C.c_int, [_P, C.c_int, _D]),
     "mm_neb_setup": (C.c_int, [_P, C.c_int, C.c_int, C.c_double]),
     "mm_neb_relax": (C.c_int, [_P, C.c_double, C.c_longlong, _D]),
+    "mm_minimize": (C.c_int, [_P, C.c_double, C.c_longlong, C.c_int, C.POINTER(C.c_longlong),
+                              C.POINTER(C.c_int)]),
+    "mm_minimize_info": (C.c_int, [_P, C.c_int, C.POINTER(C.c_longlong), _D, _D, C.POINTER(C.c_int)]),
     "mm_profile_attempts": (C.c_int, [_P, C.c_int, _D, C.POINTER(C.c_longlong)]),
     "mm_debug_bounded_wait": (C.c_int, [_P, C.c_longlong]),
     "mm_kernel_launches": (C.c_longlong, [_P]),
@@ -230,6 +233,20 @@ class Context:
         E = np.zeros(7)
         self._check(self.L.mm_energy(self.h, sim, _dptr(E)))
         return dict(zip(ENERGY_TERMS, E))
+
+    # ---- steepest descent
+    def minimize(self, max_dmdt, max_steps=10 ** 6, sync_every=32):
+        """Steepest descent with Barzilai-Borwein steps; returns (steps, converged)."""
+        done = C.c_longlong()
+        conv = C.c_int()
+        self._check(self.L.mm_minimize(self.h, max_dmdt, max_steps, sync_every, C.byref(done), C.byref(conv)))
+        return done.value, bool(conv.value)
+
+    def minimize_info(self, sim):
+        k, st = C.c_longlong(), C.c_int()
+        tau, mx = C.c_double(), C.c_double()
+        self._check(self.L.mm_minimize_info(self.h, sim, C.byref(k), C.byref(tau), C.byref(mx), C.byref(st)))
+        return {"steps": k.value, "tau": tau.value, "max_dmdt": mx.value, "status": st.value}
 
     # ---- NEB
     def neb_setup(self, first, n, k_spring):

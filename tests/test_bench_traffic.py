@@ -17,9 +17,13 @@ def test_traffic_row_needs_matching_fingerprint(tmp_path, monkeypatch):
 def test_fingerprint_changes_with_any_kernel_source(tmp_path, monkeypatch):
     csrc = tmp_path / "paper_2406_16064_gb300" / "csrc"
     csrc.mkdir(parents=True)
-    (csrc / "a.cuh").write_text("x")
+    for fn in bench.KERNEL_SOURCES:
+        (csrc / fn).write_text("x")
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     f1 = bench.source_fingerprint()
-    (csrc / "a.cuh").write_text("y")
-    assert bench.source_fingerprint() != f1
-    assert os.path.exists(str(csrc / "a.cuh"))
+    for fn in bench.KERNEL_SOURCES:
+        (csrc / fn).write_text("y" + fn)
+        f2 = bench.source_fingerprint()
+        assert f2 != f1
+        f1 = f2
+    assert os.path.exists(str(csrc / "passes.cuh"))
