@@ -14,7 +14,9 @@ measured on the same workload and reported beside it).
                   [--workload film|film_relax_32|cube|neb|batch|sweep] [--driver rk45|sd]
 
 `--driver sd` times steepest-descent steps (one effective-field evaluation and
-the Barzilai-Borwein update each) instead of RK45 attempts.
+the Barzilai-Borwein update each) instead of RK45 attempts; `--driver
+relax-compare` relaxes the workload from its start below --max-dmdt with RK45
+and with steepest descent and reports both wall times.
 
 `--workload sweep` times the N x N x 1 family of the paper's throughput
 comparison (demag + exchange + Zeeman, N = 128 ... 4096, FP32) and reports each
@@ -495,6 +497,47 @@ def run_sd(args, rank, world, dist):
     return line
 
 
+def run_relax_compare(args, rank, world, dist):
+    """Wall time to relax the workload from its start below --max-dmdt (rad/s): RK45
+    (mm_relax, the workload's rtol) against steepest descent (mm_minimize)."""
+    import torch
+    from paper_2406_16064_gb300 import mm
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    w = workload(args.workload, world)
+    prec = args.precision or ("f64" if args.workload == "film_relax_32" else "f32")
+    ctx = mm.Context(prec)
+    for s in w.sims:
+        ctx.add_sim(s.mesh, s.mat, s.Ms_cells)
+    ctx.precompute()
+    m0 = np.concatenate([s.m0.ravel() for s in w.sims])
+    out = {}
+    for drv in ("rk45", "sd"):
+        ctx.set_m(m0)
+        ctx.reset_time()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        if drv == "rk45":
+            n = ctx.relax(w.rtol, t_end=0.0, max_dmdt=args.max_dmdt, max_steps=args.steps, sync_every=64)
+            st = [ctx.status(i) for i in range(len(w.sims))]
+            conv = all(x["status"] == 2 for x in st)
+            rhs = 7 * n
+        else:
+            n, conv = ctx.minimize(args.max_dmdt, max_steps=args.steps, sync_every=16)
+            rhs = n
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        E = sum(ctx.energy(i)["total"] for i in range(len(w.sims)))
+        out[drv] = {"seconds": dt, "steps": n, "field_evaluations": rhs, "converged": bool(conv), "energy_J": E}
+    ctx.close()
+    return {"metric": "relaxation wall time below max|dm/dt|, RK45 vs steepest descent", "unit": "s",
+            "higher_is_better": False, "n_gpus": world, "dtype": prec, "data": "synthetic",
+            "config": {"workload": w.name, "cells": cells(w), "max_dmdt_rad_per_s": args.max_dmdt,
+                       "rtol_rk45": w.rtol, "max_steps": args.steps},
+            "value": out["sd"]["seconds"], "rk45": out["rk45"], "sd": out["sd"],
+            "speedup": out["rk45"]["seconds"] / out["sd"]["seconds"]}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -506,7 +549,9 @@ def main():
     ap.add_argument("--no-f64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--sweep-n", default=None, help="comma-separated N for --workload sweep")
-    ap.add_argument("--driver", default="rk45", help="rk45 (default) or sd (steepest-descent steps)")
+    ap.add_argument("--driver", default="rk45",
+                    help="rk45 (default), sd (steepest-descent steps) or relax-compare")
+    ap.add_argument("--max-dmdt", type=float, default=1e7, help="relax-compare threshold, rad/s")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -522,6 +567,8 @@ def main():
             dist.init_process_group("nccl")
         if args.driver == "sd":
             line = run_sd(args, rank, world, dist)
+        elif args.driver == "relax-compare":
+            line = run_relax_compare(args, rank, world, dist) if rank == 0 else None
         else:
             line = (run_sweep if args.workload == "sweep" else run_gpu)(args, rank, world, dist)
         if dist:
