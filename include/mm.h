@@ -176,7 +176,9 @@ int mm_neb_relax(mm_ctx *ctx, double rtol, long long n_steps, double *energies_o
  * midpoint step), and Barzilai-Borwein step sizes from the sums over a
  * simulation's cells, tau^1 = s.s / s.y on odd steps and tau^2 = s.y / y.y on
  * even ones (s = m_k - m_{k-1}, y = g_k - g_{k-1}); tau_0 = 0.01 / max|g|; a
- * rule that is not positive keeps the previous tau.  Starts from the current m
+ * rule that is not positive falls back to 0.01 / max|g|, and every step is
+ * capped at tau <= 1 / max|g| (no cell turns by more than about one radian).
+ * Starts from the current m
  * (mm_set_m) with no history; a simulation stops once max|dm/dt| of its LL
  * right-hand side (material alpha, gamma, precession flag) falls below
  * max_dmdt rad/s (0: never).  Runs at most max_steps steps, checking every

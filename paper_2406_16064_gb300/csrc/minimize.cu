@@ -6,8 +6,11 @@
 // (s = m_k - m_{k-1}, y = g_k - g_{k-1}, sums over one simulation's cells).
 // Readings where the paper is silent: the rules alternate (tau^1 on odd steps,
 // tau^2 on even ones), tau_0 = 0.01 / max |g|, a rule that is not positive and
-// finite keeps the previous tau, and a simulation stops once the max |dm/dt| of
-// its LL right-hand side at m_k drops below the threshold.
+// finite (negative curvature along the last step) falls back to 0.01 / max |g|,
+// every step is capped at tau <= 1 / max |g| (no cell turns by more than about
+// one radian; without the cap random starts never settle), and a simulation
+// stops once the max |dm/dt| of its LL right-hand side at m_k drops below the
+// threshold.
 //
 // One step of a batch = the effective-field passes of the right-hand side
 // (H_eff written) and three kernels:
@@ -94,12 +97,14 @@ static __global__ void k_sd_tau(SdState* sd, int nsims) {
     S.max_dmdt = maxg * S.dmdt_scale;
     if (!(maxg == maxg) || isinf(maxg)) { S.status = -4; return; }
     if (S.stop_dmdt > 0.0 && S.max_dmdt < S.stop_dmdt) { S.status = 2; return; }
+    const double safe = maxg > 0.0 ? 0.01 / maxg : 0.0;
     if (S.k == 0) {
-        S.tau = maxg > 0.0 ? 0.01 / maxg : 0.0;
+        S.tau = safe;
     } else {
         const double cand = (S.k & 1) ? S.ss / S.sy : S.sy / S.yy;
-        if (cand > 0.0 && !isinf(cand)) S.tau = cand;   // false for NaN too
+        S.tau = (cand > 0.0 && !isinf(cand)) ? cand : safe;   // NaN takes the safe step too
     }
+    if (maxg > 0.0) S.tau = fmin(S.tau, 1.0 / maxg);         // at most ~1 rad a step
     S.k += 1;
     S.ss = 0.0;
     S.sy = 0.0;

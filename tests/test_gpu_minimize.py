@@ -106,6 +106,28 @@ def test_uneven_batch_each_simulation_reaches_its_own_minimum():
         assert ctx.minimize_info(i)["status"] == 2
 
 
+def test_random_start_reaches_the_rk45_minimum_f64():
+    """The 32x32x1 film of random directions: steepest descent converges (step cap)
+    to the energy the damped RK45 relaxation reaches, in far fewer field evaluations."""
+    w = synth.film_relax_32()
+    sim = w.sims[0]
+    ctx = make_ctx("f64", [sim])
+    ctx.set_m(sim.m0.ravel())
+    steps, conv = ctx.minimize(1e7, max_steps=5000)
+    assert conv and steps < 2000, (steps, ctx.minimize_info(0))
+    E_sd = ctx.energy(0)["total"]
+    ctx.set_m(sim.m0.ravel())
+    ctx.reset_time()
+    attempts = ctx.relax(w.rtol, max_dmdt=1e7, max_steps=20000, sync_every=64)
+    assert ctx.status(0)["status"] == 2
+    E_rk = ctx.energy(0)["total"]
+    # both stop at the first state below 1e7 rad/s (RK45 at rtol 1e-6 cannot resolve much
+    # lower: its error-controller noise is ~2e6 rad/s here), so they agree to the energy
+    # error of that threshold, not to rounding (2.5e-6 measured)
+    assert abs(E_sd - E_rk) <= 1e-5 * abs(E_rk), (E_sd, E_rk)
+    assert steps < 7 * attempts / 5
+
+
 def test_masked_cells_stay_fixed_on_gpu():
     mesh = synth.Mesh(6, 5, 1, 2e-9, 2e-9, 2e-9)
     mat = synth.Material(Ms=8e5, A=1.3e-11, Ku=2e5, H=(3e4, 0, 0), precession=0, demag=1)
