@@ -10,6 +10,7 @@
 #include <cstring>
 #include <map>
 #include <string>
+#include <thread>
 #include <tuple>
 #include <vector>
 
@@ -76,6 +77,9 @@ struct mm_ctx {
     SdState* sd_d = nullptr;
     cudaGraphExec_t sd_exec = nullptr;
     long long sd_graph_kernels = 0;
+    // pinned host staging buffer for the host-side state transfers of FP32 contexts
+    void* host_stage = nullptr;
+    size_t host_stage_bytes = 0;
     long long graph_kernels = 0;
     long long launches = 0;
     bool neb = false;
@@ -278,6 +282,39 @@ void to_prec(const double* src, T* dst, size_t n) {
     for (size_t i = 0; i < n; ++i) dst[i] = (T)src[i];
 }
 
+// Element-wise conversion of a large host array on several host threads.
+template <typename A, typename B>
+void convert_host(const A* src, B* dst, long long n) {
+    const unsigned hc = std::thread::hardware_concurrency();
+    const int nt = n < (1LL << 18) ? 1 : (int)std::min(8u, std::max(1u, hc));
+    if (nt == 1) {
+        for (long long i = 0; i < n; ++i) dst[i] = (B)src[i];
+        return;
+    }
+    std::vector<std::thread> th;
+    const long long chunk = (n + nt - 1) / nt;
+    for (int t = 0; t < nt; ++t) {
+        const long long lo = t * chunk, hi = std::min(n, lo + chunk);
+        th.emplace_back([=] { for (long long i = lo; i < hi; ++i) dst[i] = (B)src[i]; });
+    }
+    for (auto& x : th) x.join();
+}
+
+// The pinned staging buffer, grown to at least `bytes` (reused by every host transfer).
+int ensure_host_stage(mm_ctx* C, size_t bytes) {
+    if (C->host_stage_bytes >= bytes) return MM_OK;
+    if (C->host_stage) cudaFreeHost(C->host_stage);
+    C->host_stage = nullptr;
+    C->host_stage_bytes = 0;
+    const cudaError_t e = cudaMallocHost(&C->host_stage, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(C, MM_ENOMEM, "cudaMallocHost(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
+    }
+    C->host_stage_bytes = bytes;
+    return MM_OK;
+}
+
 int ensure_scratch(mm_ctx* C) {
     if (C->sc_in) return MM_OK;
     const size_t b = (size_t)C->total_elems * C->esz;
@@ -419,6 +456,7 @@ int mm_destroy(mm_ctx* C) {
                     C->zi, C->y2i, C->flag_d, C->status_d, C->diag_d, C->sd_H, C->sd_mprev, C->sd_g,
                     C->sd_d};
     for (void* p : ptrs) if (p) cudaFree(p);
+    if (C->host_stage) cudaFreeHost(C->host_stage);
     for (int j = 0; j < 7; ++j) if (C->k[j]) cudaFree(C->k[j]);
     for (int li = 0; li < 2 * kYzcLists; ++li) if (C->yzci[li]) cudaFree(C->yzci[li]);
     if (C->own_stream) cudaStreamDestroy(C->stream);
@@ -673,9 +711,10 @@ int mm_set_m(mm_ctx* C, int sim, const void* m, int where) {
     if (where == MM_DEVICE) {
         CK(cudaMemcpyAsync(dst, m, n * C->esz, cudaMemcpyDeviceToDevice, C->stream));
     } else if (C->precision == MM_F32) {
-        std::vector<float> f(n);
-        to_prec((const double*)m, f.data(), n);
-        CK(cudaMemcpyAsync(dst, f.data(), n * 4, cudaMemcpyHostToDevice, C->stream));
+        if ((rc = ensure_host_stage(C, (size_t)n * 4))) return rc;
+        float* f = (float*)C->host_stage;
+        convert_host((const double*)m, f, n);
+        CK(cudaMemcpyAsync(dst, f, n * 4, cudaMemcpyHostToDevice, C->stream));
     } else {
         CK(cudaMemcpyAsync(dst, m, n * 8, cudaMemcpyHostToDevice, C->stream));
     }
@@ -693,10 +732,11 @@ int mm_get_m(mm_ctx* C, int sim, void* m, int where) {
     if (where == MM_DEVICE) {
         CK(cudaMemcpyAsync(m, src, n * C->esz, cudaMemcpyDeviceToDevice, C->stream));
     } else if (C->precision == MM_F32) {
-        std::vector<float> f(n);
-        CK(cudaMemcpyAsync(f.data(), src, n * 4, cudaMemcpyDeviceToHost, C->stream));
+        if ((rc = ensure_host_stage(C, (size_t)n * 4))) return rc;
+        float* f = (float*)C->host_stage;
+        CK(cudaMemcpyAsync(f, src, n * 4, cudaMemcpyDeviceToHost, C->stream));
         CK(cudaStreamSynchronize(C->stream));
-        for (long long i = 0; i < n; ++i) ((double*)m)[i] = f[i];
+        convert_host(f, (double*)m, n);
     } else {
         CK(cudaMemcpyAsync(m, src, n * 8, cudaMemcpyDeviceToHost, C->stream));
     }
