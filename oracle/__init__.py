@@ -17,6 +17,8 @@ It is plain, slow and written to be checked by eye against the paper
   neb        geodesic nudged elastic band (Sec. "Miscellaneous")
   minimize   steepest descent with Barzilai-Borwein steps (Sec. "Steepest
              descent energy minimization")
+  cayley     fixed-step classical Runge-Kutta with projection and on the
+             Cayley-transform variable (Sec. "Cayley transform")
 
 All arithmetic is float64.  Parity status of every function is listed in
 its module header.
