@@ -11,12 +11,17 @@ perpendicular anisotropy, ~200 reversed disks (FP32 path; the FP64 path is
 measured on the same workload and reported beside it).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                  [--workload film|film_relax_32|cube|neb|batch|sweep] [--driver rk45|sd]
+                  [--workload film|film_relax_32|cube|neb|batch|sweep] [--driver rk45|sd|rk4-cayley|rk4-proj|...]
 
 `--driver sd` times steepest-descent steps (one effective-field evaluation and
 the Barzilai-Borwein update each) instead of RK45 attempts; `--driver
 relax-compare` relaxes the workload from its start below --max-dmdt with RK45
 and with steepest descent and reports both wall times.
+
+`--driver rk4-cayley` / `--driver rk4-proj` time fixed classical RK4 steps
+(four right-hand sides each) on the Cayley-transform variable or with
+projection; `--driver cayley-error` runs the paper's macrospin comparison of the
+two schemes (error against the closed form at 1 ns over a range of h).
 
 `--workload sweep` times the N x N x 1 family of the paper's throughput
 comparison (demag + exchange + Zeeman, N = 128 ... 4096, FP32) and reports each
@@ -497,6 +502,91 @@ def run_sd(args, rank, world, dist):
     return line
 
 
+def run_rk4(args, rank, world, dist, cayley):
+    """Fixed RK4 steps (four right-hand sides each) on the workload, h = 1e-14 s."""
+    import torch
+    from paper_2406_16064_gb300 import mm
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream()
+    w = workload(args.workload, world)
+    if w.neb:
+        raise SystemExit("--driver rk4-*: the NEB workload has its own driver")
+    prec = args.precision or ("f64" if args.workload == "film_relax_32" else "f32")
+    ctx = mm.Context(prec, stream=stream.cuda_stream)
+    for s in w.sims:
+        ctx.add_sim(s.mesh, s.mat, s.Ms_cells)
+    ctx.precompute()
+    m0 = np.concatenate([s.m0.ravel() for s in w.sims])
+    ctx.set_m(m0)
+    h = 1e-14
+    ctx.rk4(h, args.warmup, cayley)
+    ctx.set_m(m0)
+    if dist:
+        dist.barrier()
+    n0 = ctx.launches()
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    with Clocks(dev) as clk:
+        start.record(stream)
+        ctx.rk4(h, args.steps, cayley)
+        end.record(stream)
+        end.synchronize()
+    ms = start.elapsed_time(end)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    m = ctx.get_m(0).reshape(3, -1)
+    ncell = cells(w)
+    line = {"metric": METRIC, "value": world * ncell * 4 * args.steps / (ms / 1e3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": prec, "data": "synthetic",
+            "config": {"workload": w.name, "cells": ncell, "h_s": h,
+                       "driver": ("rk4 on the Cayley variable" if cayley else "rk4 with projection")
+                       + " (4 right-hand sides a step)",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "max_norm_error": float(np.abs(np.sqrt((m.astype(np.float64) ** 2).sum(0)) - 1).max()),
+            "clocks": clk.summary(), "gpu_launches": ctx.launches() - n0}
+    ctx.close()
+    return line
+
+
+def run_cayley_error(args, rank, world, dist):
+    """The paper's macrospin comparison (Sec. "Cayley transform"): alpha = 0.05,
+    H = 1e5 A/m along z, m(0) = x; max-norm error of m(1 ns) against the closed
+    form for RK4 with projection and RK4 on the Cayley variable, FP64 on the GPU."""
+    import torch
+    import synth
+    from paper_2406_16064_gb300 import mm
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    alpha, gamma, Hz, t_end = 0.05, 2.21e5, 1e5, 1e-9
+    mesh = synth.Mesh(1, 1, 1, 2e-9, 2e-9, 2e-9)
+    mat = synth.Material(Ms=8e5, H=(0.0, 0.0, Hz), alpha=alpha, gamma=gamma, demag=0)
+    m0 = synth.uniform_state(mesh, (1.0, 0.0, 0.0))
+    ph = gamma / (1 + alpha ** 2) * Hz * t_end
+    exact = np.array([math.cos(ph) / math.cosh(alpha * ph), math.sin(ph) / math.cosh(alpha * ph),
+                      math.tanh(alpha * ph)])
+    rows = []
+    for n in (250, 500, 1000, 2000, 4000, 8000):
+        row = {"h_s": t_end / n, "steps": n}
+        for name, cay in (("cayley", True), ("projection", False)):
+            ctx = mm.Context("f64")
+            ctx.add_sim(mesh, mat, None)
+            ctx.precompute()
+            ctx.set_m(m0.ravel())
+            ctx.rk4(t_end / n, n, cay)
+            row[name] = float(np.abs(ctx.get_m(0) - exact).max())
+            ctx.close()
+        rows.append(row)
+    order = {k: math.log2(rows[0][k] / rows[1][k]) for k in ("cayley", "projection")}
+    return {"metric": "macrospin max-norm error at 1 ns, RK4 with projection vs RK4 on the Cayley variable",
+            "unit": "1", "higher_is_better": False, "n_gpus": 1, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "macrospin alpha=0.05 Hz=1e5 A/m t=1 ns"},
+            "value": rows[2]["cayley"], "rows": rows, "order_coarsest": order}
+
+
 def run_relax_compare(args, rank, world, dist):
     """Wall time to relax the workload from its start below --max-dmdt (rad/s): RK45
     (mm_relax, the workload's rtol) against steepest descent (mm_minimize)."""
@@ -550,7 +640,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--sweep-n", default=None, help="comma-separated N for --workload sweep")
     ap.add_argument("--driver", default="rk45",
-                    help="rk45 (default), sd (steepest-descent steps) or relax-compare")
+                    help="rk45 (default), sd (steepest-descent steps), relax-compare, rk4-cayley, "
+                         "rk4-proj or cayley-error")
     ap.add_argument("--max-dmdt", type=float, default=1e7, help="relax-compare threshold, rad/s")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
@@ -567,6 +658,10 @@ def main():
             dist.init_process_group("nccl")
         if args.driver == "sd":
             line = run_sd(args, rank, world, dist)
+        elif args.driver in ("rk4-cayley", "rk4-proj"):
+            line = run_rk4(args, rank, world, dist, args.driver == "rk4-cayley")
+        elif args.driver == "cayley-error":
+            line = run_cayley_error(args, rank, world, dist) if rank == 0 else None
         elif args.driver == "relax-compare":
             line = run_relax_compare(args, rank, world, dist) if rank == 0 else None
         else:

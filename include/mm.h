@@ -195,6 +195,20 @@ int mm_minimize(mm_ctx *ctx, double max_dmdt, long long max_steps, int sync_ever
  * (rad/s) at the last step's m, status (0 running, 2 converged, -4 NaN). */
 int mm_minimize_info(mm_ctx *ctx, int sim_id, long long *steps, double *tau, double *max_dmdt, int *status);
 
+/* n_steps fixed steps of size h (seconds) of classical four-stage Runge-Kutta
+ * on every simulation (Sec. "Cayley transform"), from the current m, in the
+ * context precision.  cayley = 0: RK4 on the LL right-hand side dm/dt, then
+ * m <- m / |m| after each step.  cayley = 1: with dm/dt = f x m,
+ * f = gamma (H + alpha m x H) / (1 + alpha^2) (only the alpha term without
+ * precession), RK4 on d omega/dt = f - omega x f / 2 + (omega . f) omega / 4
+ * from omega = 0 and m_{n+1} = Q(omega_{n+1}) m_n with the Cayley transform
+ * Q = (I - Omega/2)^-1 (I + Omega/2), Omega x = omega x x (a rotation: |m|
+ * is kept to rounding).  Cells with Ms = 0 do not move.  Each simulation's
+ * time advances by n_steps * h; its RK45 step size and status are untouched.
+ * There is no error control and no check of the values.  Returns MM_EINVAL
+ * for h not positive and finite, n_steps < 0, or a context with NEB chains. */
+int mm_rk4(mm_ctx *ctx, double h, long long n_steps, int cayley);
+
 /* Profiling aid: runs `reps` RK45 attempts (NEB attempts in a context with
  * chains) with direct launches (no graph) and a CUDA event recorded on the
  * context stream after every kernel kind.

@@ -14,6 +14,7 @@
 #include <tuple>
 #include <vector>
 
+#include "cayley.h"
 #include "engine.cuh"
 #include "minimize.h"
 #include "mm.h"
@@ -77,6 +78,11 @@ struct mm_ctx {
     SdState* sd_d = nullptr;
     cudaGraphExec_t sd_exec = nullptr;
     long long sd_graph_kernels = 0;
+    // fixed-step RK4 (projected or Cayley): one captured step for the last (h, scheme)
+    cudaGraphExec_t c4_exec = nullptr;
+    double c4_h = 0.0;
+    int c4_cay = -1;
+    long long c4_graph_kernels = 0;
     // pinned host staging buffer for the host-side state transfers of FP32 contexts
     void* host_stage = nullptr;
     size_t host_stage_bytes = 0;
@@ -401,6 +407,38 @@ int sd_prepare(mm_ctx* C) {
     return MM_OK;
 }
 
+// One captured RK4 step; the step size is a kernel argument, so a call with
+// another h or scheme captures again.  Stage slopes live in the RK45 stage
+// buffers, the stage state in its stage-state buffer (neither carries state
+// from one RK45 attempt to the next).
+int c4_prepare(mm_ctx* C, double h, int cay) {
+    int rc;
+    if ((rc = ensure_scratch(C))) return rc;
+    if (C->c4_exec && C->c4_h == h && C->c4_cay == cay) return MM_OK;
+    if (C->c4_exec) { cudaGraphExecDestroy(C->c4_exec); C->c4_exec = nullptr; }
+    Launch L = make_launch(C, -1);
+    Rk4Buffers B;
+    B.m = C->m;
+    B.ys = C->ybuf;
+    B.H = C->sc_h;
+    B.dmdt = C->sc_out;
+    for (int j = 0; j < 4; ++j) B.k[j] = C->k[j];
+    const long long before = C->launches;
+    cudaGraph_t g;
+    CK(cudaStreamBeginCapture(C->stream, cudaStreamCaptureModeThreadLocal));
+    if (C->precision == MM_F32) rk4_step<float>(L, B, h, cay != 0); else rk4_step<double>(L, B, h, cay != 0);
+    cudaError_t e = cudaStreamEndCapture(C->stream, &g);
+    if (e != cudaSuccess) return fail(C, MM_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&C->c4_exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(C, MM_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    C->c4_graph_kernels = C->launches - before;
+    C->launches = before;
+    C->c4_h = h;
+    C->c4_cay = cay;
+    return MM_OK;
+}
+
 int first_error(mm_ctx* C, const std::vector<SimState>& st) {
     for (size_t i = 0; i < st.size(); ++i) {
         if (st[i].status < 0) {
@@ -451,6 +489,7 @@ int mm_destroy(mm_ctx* C) {
     if (C->stream) cudaStreamSynchronize(C->stream);
     if (C->rk_exec) cudaGraphExecDestroy(C->rk_exec);
     if (C->sd_exec) cudaGraphExecDestroy(C->sd_exec);
+    if (C->c4_exec) cudaGraphExecDestroy(C->c4_exec);
     void* ptrs[] = {C->m, C->ybuf, C->errp, C->spec, C->Msd, C->tens, C->twd, C->twf, C->sc_in, C->sc_out,
                     C->sc_h, C->heff, C->tau, C->kvec_dev, C->oct, C->desc_d, C->state_d, C->xi, C->y13i,
                     C->zi, C->y2i, C->flag_d, C->status_d, C->diag_d, C->sd_H, C->sd_mprev, C->sd_g,
@@ -921,6 +960,19 @@ int mm_minimize(mm_ctx* C, double max_dmdt, long long max_steps, int sync_every,
     }
     if (steps_done) *steps_done = kmax;
     if (converged) *converged = all ? 1 : 0;
+    return MM_OK;
+}
+
+int mm_rk4(mm_ctx* C, double h, long long n_steps, int cayley) {
+    int rc = check_ready(C);
+    if (rc) return rc;
+    if (C->neb) return fail(C, MM_EINVAL, "mm_rk4: not in a context with NEB chains");
+    if (!(h > 0.0) || std::isinf(h) || n_steps < 0 || (cayley != 0 && cayley != 1))
+        return fail(C, MM_EINVAL, "mm_rk4: bad arguments");
+    if ((rc = c4_prepare(C, h, cayley))) return rc;
+    for (long long i = 0; i < n_steps; ++i) CK(cudaGraphLaunch(C->c4_exec, C->stream));
+    C->launches += n_steps * C->c4_graph_kernels;
+    CK(cudaStreamSynchronize(C->stream));
     return MM_OK;
 }
 

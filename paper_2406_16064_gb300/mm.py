@@ -68,6 +68,7 @@ SIGNATURES = {
     "mm_minimize": (C.c_int, [_P, C.c_double, C.c_longlong, C.c_int, C.POINTER(C.c_longlong),
                               C.POINTER(C.c_int)]),
     "mm_minimize_info": (C.c_int, [_P, C.c_int, C.POINTER(C.c_longlong), _D, _D, C.POINTER(C.c_int)]),
+    "mm_rk4": (C.c_int, [_P, C.c_double, C.c_longlong, C.c_int]),
     "mm_profile_attempts": (C.c_int, [_P, C.c_int, _D, C.POINTER(C.c_longlong)]),
     "mm_debug_bounded_wait": (C.c_int, [_P, C.c_longlong]),
     "mm_kernel_launches": (C.c_longlong, [_P]),
@@ -247,6 +248,11 @@ class Context:
         tau, mx = C.c_double(), C.c_double()
         self._check(self.L.mm_minimize_info(self.h, sim, C.byref(k), C.byref(tau), C.byref(mx), C.byref(st)))
         return {"steps": k.value, "tau": tau.value, "max_dmdt": mx.value, "status": st.value}
+
+    def rk4(self, h, n_steps, cayley=True):
+        """n_steps fixed classical RK4 steps of size h on the Cayley variable
+        (cayley=True) or on dm/dt with projection onto |m| = 1."""
+        self._check(self.L.mm_rk4(self.h, float(h), int(n_steps), 1 if cayley else 0))
 
     # ---- NEB
     def neb_setup(self, first, n, k_spring):
