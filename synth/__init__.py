@@ -87,7 +87,7 @@ class Material:
     Ms: float
     A: float = 0.0
     D: float = 0.0
-    dmi: int = 0                  # 0 none, 1 interfacial (C_nv)
+    dmi: int = 0                  # 0 none, 1 interfacial (C_nv), 2 bulk (T, O), 3 D_2d
     Ku: float = 0.0
     u: tuple = (0.0, 0.0, 1.0)
     Kc: float = 0.0               # cubic, energy density Kc*(mx^4+my^4+mz^4)
@@ -96,6 +96,16 @@ class Material:
     gamma: float = 2.211e5
     precession: int = 1
     demag: int = 1
+    # per-cell exchange / DMI constants (nz, ny, nx), None for the uniform A / D
+    A_cells: Optional[np.ndarray] = None
+    D_cells: Optional[np.ndarray] = None
+    # spin-transfer torque (Zhang-Li): drift velocity u (m/s), non-adiabaticity beta
+    u_stt: tuple = (0.0, 0.0, 0.0)
+    beta: float = 0.0
+    # Slonczewski / spin-orbit torque: a_J, b_J (1/s) and polarisation p
+    aJ: float = 0.0
+    bJ: float = 0.0
+    p: tuple = (0.0, 0.0, 1.0)
 
 
 @dataclass
