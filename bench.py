@@ -161,7 +161,7 @@ TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic.md")
 # The sources that define (and instantiate) the kernels of the right-hand side
 # and of the RK45 attempt, whose DRAM counters profiles/dram_traffic.md records.
 KERNEL_SOURCES = ("control.cuh", "engine.cuh", "engine_f32.cu", "engine_f64.cu", "engine_impl.cuh",
-                  "mm_kernels.cuh", "passes.cuh", "plan.h")
+                  "ext_terms.cuh", "mm_kernels.cuh", "passes.cuh", "plan.h")
 
 
 def source_fingerprint():

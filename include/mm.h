@@ -58,7 +58,11 @@ enum {
 
 enum { MM_F64 = 0, MM_F32 = 1 };          /* context precision */
 enum { MM_HOST = 0, MM_DEVICE = 1 };      /* where a buffer lives */
-enum { MM_DMI_NONE = 0, MM_DMI_INTERFACIAL = 1 };
+/* DMI symmetry class (Sec. "Dzyaloshinskii-Moriya Energy"): DMI vectors e_ij
+ * for the neighbours (-x, +x, -y, +y, -z, +z): interfacial (C_nv)
+ * (-e_y, e_y, e_x, -e_x, 0, 0); bulk (T, O) r_ij = (-e_x, e_x, -e_y, e_y, -e_z,
+ * e_z); D_2d (e_x, -e_x, -e_y, e_y, 0, 0). */
+enum { MM_DMI_NONE = 0, MM_DMI_INTERFACIAL = 1, MM_DMI_BULK = 2, MM_DMI_D2D = 3 };
 
 typedef struct mm_ctx mm_ctx;             /* opaque */
 
@@ -107,6 +111,31 @@ int mm_num_sims(const mm_ctx *ctx);
 
 /* Applied field of one simulation (field sweeps, Listing 2), A/m. */
 int mm_set_field(mm_ctx *ctx, int sim_id, const double H[3]);
+
+/* Cell-based exchange and DMI constants of one simulation (host double arrays
+ * of nx*ny*nz values, J/m and J/m^2; NULL keeps that constant uniform, both
+ * NULL return to uniform A and D).  Neighbours couple with the harmonic means
+ * A_ij = 2 A_i A_j / (A_i + A_j) and D_ij = 2 D_i D_j / (D_i + D_j), 0 where
+ * the two values sum to 0 (Sec. "Exchange energy", Sec. "Dzyaloshinskii-
+ * Moriya Energy").  Must precede mm_precompute_demag; MM_EINVAL for a
+ * non-finite value.  The arrays are copied. */
+int mm_set_cell_params(mm_ctx *ctx, int sim_id, const double *A_cells, const double *D_cells);
+
+/* Spin torques of one simulation (Sec. "Spin transfer torques"), added to
+ * the implicit LLG equation dm/dt = -gamma m x H + alpha m x dm/dt + T with
+ *   T = m x (m x (u.grad)m) + beta m x (u.grad)m      (Zhang-Li, u in m/s)
+ *       - a_J m x (m x p) - b_J m x p                 (Slonczewski / spin-orbit,
+ *                                                       a_J, b_J in 1/s)
+ * and solved for dm/dt: the right-hand side gains (T + alpha m x T)/(1 + alpha^2).
+ * (u.grad)m is the central difference (m_+ - m_-)/(2 Delta) along each axis,
+ * a neighbour outside the mesh or with Ms = 0 taken as the cell itself; p is
+ * normalised (it must be non-zero when a_J or b_J is).  The torques act with
+ * and without the precession term, enter the RK45 attempts, relax, rhs_eval
+ * and mm_rk4 with cayley = 0 (mm_rk4 with cayley = 1 returns MM_EINVAL), and
+ * not the minimiser or the energies, which use H_eff only.  May be called at
+ * any time; zeros switch the torques off.  MM_EINVAL for a non-finite value. */
+int mm_set_spin_torque(mm_ctx *ctx, int sim_id, const double u[3], double beta, double a_J, double b_J,
+                       const double p[3]);
 
 /* Finalise the batch: allocate device state, compute the Newell tensor in
  * FP64 for every distinct (mesh, cell) geometry (Eq. 7, Newell 1993; closed
@@ -206,7 +235,8 @@ int mm_minimize_info(mm_ctx *ctx, int sim_id, long long *steps, double *tau, dou
  * is kept to rounding).  Cells with Ms = 0 do not move.  Each simulation's
  * time advances by n_steps * h; its RK45 step size and status are untouched.
  * There is no error control and no check of the values.  Returns MM_EINVAL
- * for h not positive and finite, n_steps < 0, or a context with NEB chains. */
+ * for h not positive and finite, n_steps < 0, a context with NEB chains, or
+ * cayley = 1 with spin torques set (f is built from H_eff). */
 int mm_rk4(mm_ctx *ctx, double h, long long n_steps, int cayley);
 
 /* Profiling aid: runs `reps` RK45 attempts (NEB attempts in a context with
@@ -236,7 +266,8 @@ long long mm_kernel_launches(const mm_ctx *ctx);
  * outputs dmdt_dev and heff_dev (nullable), [3][nz][ny][nx] each in the given
  * precision (MM_F64: double, MM_F32: float), and a cudaStream_t (NULL = the
  * default stream); the result equals mm_rhs_eval's for the same simulation
- * (uniform Ms only).  Everything else -- twiddle tables, the FP64 Newell
+ * (uniform Ms, A and D, no or interfacial DMI, no spin torques; another DMI
+ * class returns MM_EINVAL).  Everything else -- twiddle tables, the FP64 Newell
  * tensor and its spectrum (recomputed on every call), the demag spectrum,
  * descriptors and work lists -- lives in one static device array of 32 MiB
  * that every GPU loading libmm holds until the process exits.  A mesh whose

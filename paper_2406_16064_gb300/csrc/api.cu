@@ -31,6 +31,7 @@ struct SimHost {
     mm_mesh mesh;
     mm_material mat;
     std::vector<double> Ms;
+    std::vector<double> AD;     // per-cell A then D (2 ncells), empty if uniform
     SimDesc d;
     int geom = -1;
 };
@@ -55,9 +56,9 @@ struct mm_ctx {
     std::vector<SimHost> sims;
     std::vector<Geom> geoms;
     bool finalized = false;
-    long long total_elems = 0, spec_elems = 0, ms_elems = 0, tens_elems = 0, oct_elems = 0;
+    long long total_elems = 0, spec_elems = 0, ms_elems = 0, tens_elems = 0, oct_elems = 0, cell_elems = 0;
     void *m = nullptr, *ybuf = nullptr, *k[7] = {}, *errp = nullptr, *spec = nullptr, *Msd = nullptr,
-         *tens = nullptr, *twd = nullptr, *twf = nullptr;
+         *tens = nullptr, *twd = nullptr, *twf = nullptr, *cellp = nullptr;
     void *sc_in = nullptr, *sc_out = nullptr, *sc_h = nullptr, *heff = nullptr, *tau = nullptr;
     void** kvec_dev = nullptr;
     double* oct = nullptr;
@@ -149,10 +150,37 @@ Launch make_launch(mm_ctx* C, int sim) {
     L.smem_yzc = P.smem_yzc;
     L.tensor = C->tens;
     L.Ms = C->Msd;
+    L.cellp = C->cellp;
+    for (const SimHost& s : C->sims) L.ext = L.ext || (s.d.flags & F_EXT) != 0;
     L.tw = C->precision == MM_F32 ? C->twf : C->twd;
     L.spec = C->spec;
     L.launches = &C->launches;
     return L;
+}
+
+// Term flags and coefficients of one simulation from its parameters.
+void replan(SimHost& s) {
+    plan_coefficients(s.d, s.mat.dmi_kind == MM_DMI_INTERFACIAL);
+    bool a_any = false, d_any = false;
+    const size_t n = s.AD.size() / 2;
+    for (size_t i = 0; i < n; ++i) {
+        a_any = a_any || s.AD[i] != 0.0;
+        d_any = d_any || s.AD[n + i] != 0.0;
+    }
+    plan_extended(s.d, !s.AD.empty(), a_any, d_any);
+}
+
+bool batch_ext(const mm_ctx* C) {
+    for (const SimHost& s : C->sims)
+        if (s.d.flags & F_EXT) return true;
+    return false;
+}
+
+// Captured graphs bake in the x-inverse variant; drop them when it changes.
+void drop_graphs(mm_ctx* C) {
+    if (C->rk_exec) { cudaGraphExecDestroy(C->rk_exec); C->rk_exec = nullptr; }
+    if (C->sd_exec) { cudaGraphExecDestroy(C->sd_exec); C->sd_exec = nullptr; }
+    if (C->c4_exec) { cudaGraphExecDestroy(C->c4_exec); C->c4_exec = nullptr; }
 }
 
 int check_ready(mm_ctx* C) {
@@ -490,7 +518,7 @@ int mm_destroy(mm_ctx* C) {
     if (C->rk_exec) cudaGraphExecDestroy(C->rk_exec);
     if (C->sd_exec) cudaGraphExecDestroy(C->sd_exec);
     if (C->c4_exec) cudaGraphExecDestroy(C->c4_exec);
-    void* ptrs[] = {C->m, C->ybuf, C->errp, C->spec, C->Msd, C->tens, C->twd, C->twf, C->sc_in, C->sc_out,
+    void* ptrs[] = {C->m, C->ybuf, C->errp, C->spec, C->Msd, C->cellp, C->tens, C->twd, C->twf, C->sc_in, C->sc_out,
                     C->sc_h, C->heff, C->tau, C->kvec_dev, C->oct, C->desc_d, C->state_d, C->xi, C->y13i,
                     C->zi, C->y2i, C->flag_d, C->status_d, C->diag_d, C->sd_H, C->sd_mprev, C->sd_g,
                     C->sd_d};
@@ -531,9 +559,11 @@ int mm_add_sim(mm_ctx* C, const mm_mesh* mesh, const mm_material* mat, const dou
     d.alpha = mat->alpha; d.gamma = mat->gamma;
     d.dx = mesh->dx; d.dy = mesh->dy; d.dz = mesh->dz;
     d.flags = (mat->demag ? F_DEMAG : 0) | (mat->precession ? F_PREC : 0);
-    if (mat->dmi_kind != MM_DMI_NONE && mat->dmi_kind != MM_DMI_INTERFACIAL)
-        return fail(C, MM_EINVAL, "unsupported DMI kind");
-    plan_coefficients(d, mat->dmi_kind == MM_DMI_INTERFACIAL);
+    if (mat->dmi_kind < MM_DMI_NONE || mat->dmi_kind > MM_DMI_D2D) return fail(C, MM_EINVAL, "unsupported DMI kind");
+    d.dmi_kind = mat->dmi_kind;
+    d.cell_off = -1;
+    d.p[2] = 1.0;
+    replan(s);
     d.group_begin = d.group_end = -1;
     d.neb_index = -1;
     d.ms_off = -1;
@@ -568,8 +598,57 @@ int mm_set_field(mm_ctx* C, int sim, const double H[3]) {
         s.mat.H[i] = H[i];
         s.d.H[i] = H[i];
     }
-    plan_coefficients(s.d, s.mat.dmi_kind == MM_DMI_INTERFACIAL);
+    replan(s);
     if (C->finalized) {
+        CK(cudaMemcpyAsync(&C->desc_d[sim], &s.d, sizeof(SimDesc), cudaMemcpyHostToDevice, C->stream));
+        CK(cudaStreamSynchronize(C->stream));
+    }
+    return MM_OK;
+}
+
+int mm_set_cell_params(mm_ctx* C, int sim, const double* A_cells, const double* D_cells) {
+    if (!C) return MM_EINVAL;
+    if (sim < 0 || sim >= (int)C->sims.size()) return fail(C, MM_EINVAL, "bad sim id");
+    if (C->finalized) return fail(C, MM_EINVAL, "mm_set_cell_params after mm_precompute_demag");
+    SimHost& s = C->sims[sim];
+    const size_t n = (size_t)s.d.ncells;
+    if (!A_cells && !D_cells) {
+        s.AD.clear();
+    } else {
+        std::vector<double> ad(2 * n);
+        for (size_t i = 0; i < n; ++i) {
+            ad[i] = A_cells ? A_cells[i] : s.mat.A;
+            ad[n + i] = D_cells ? D_cells[i] : s.mat.D;
+            if (!std::isfinite(ad[i]) || !std::isfinite(ad[n + i]))
+                return fail(C, MM_EINVAL, "per-cell A and D must be finite");
+        }
+        s.AD.swap(ad);
+    }
+    replan(s);
+    return MM_OK;
+}
+
+int mm_set_spin_torque(mm_ctx* C, int sim, const double u[3], double beta, double a_J, double b_J,
+                       const double p[3]) {
+    if (!C || !u || !p) return fail(C, MM_EINVAL, "NULL argument");
+    if (sim < 0 || sim >= (int)C->sims.size()) return fail(C, MM_EINVAL, "bad sim id");
+    bool fin = std::isfinite(beta) && std::isfinite(a_J) && std::isfinite(b_J);
+    for (int i = 0; i < 3; ++i) fin = fin && std::isfinite(u[i]) && std::isfinite(p[i]);
+    if (!fin) return fail(C, MM_EINVAL, "mm_set_spin_torque: non-finite argument");
+    const double pn = std::sqrt(p[0] * p[0] + p[1] * p[1] + p[2] * p[2]);
+    if ((a_J != 0.0 || b_J != 0.0) && !(pn > 0.0)) return fail(C, MM_EINVAL, "polarisation p is zero");
+    SimHost& s = C->sims[sim];
+    const bool before = batch_ext(C);
+    for (int i = 0; i < 3; ++i) {
+        s.d.u_stt[i] = u[i];
+        s.d.p[i] = p[i];
+    }
+    s.d.beta = beta;
+    s.d.aJ = a_J;
+    s.d.bJ = b_J;
+    replan(s);
+    if (C->finalized) {
+        if (batch_ext(C) != before) drop_graphs(C);
         CK(cudaMemcpyAsync(&C->desc_d[sim], &s.d, sizeof(SimDesc), cudaMemcpyHostToDevice, C->stream));
         CK(cudaStreamSynchronize(C->stream));
     }
@@ -622,6 +701,7 @@ int mm_precompute_demag(mm_ctx* C) {
         C->total_elems += 3LL * d.ncells;
         d.tens_off = C->geoms[s.geom].tens_off;
         if (d.flags & F_MSARR) { d.ms_off = C->ms_elems; C->ms_elems += d.ncells; }
+        if (!s.AD.empty()) { d.cell_off = C->cell_elems; C->cell_elems += 2LL * d.ncells; }
         if (d.flags & F_DEMAG) {
             // 4-element (32-byte) aligned, so every Ty-wide run of Ty >= 2 values takes 16-byte copies
             d.spec_off = (C->spec_elems + 3) & ~3LL;
@@ -652,6 +732,7 @@ int mm_precompute_demag(mm_ctx* C) {
     if ((rc = dalloc(C, &C->errp, sb))) return rc;
     if ((rc = dalloc(C, &C->spec, (size_t)C->spec_elems * 2 * C->esz))) return rc;
     if ((rc = dalloc(C, &C->Msd, (size_t)C->ms_elems * C->esz))) return rc;
+    if ((rc = dalloc(C, &C->cellp, (size_t)C->cell_elems * C->esz))) return rc;
     if ((rc = dalloc(C, &C->tens, (size_t)C->tens_elems * C->esz))) return rc;
     CK(cudaMemsetAsync(C->tens, 0, (size_t)C->tens_elems * C->esz, C->stream));   // padding of blocked tensors
     if ((rc = dalloc(C, (void**)&C->oct, (size_t)C->oct_elems * 8))) return rc;
@@ -693,6 +774,19 @@ int mm_precompute_demag(mm_ctx* C) {
             CK(cudaMemcpy(C->Msd, fl.data(), fl.size() * 4, cudaMemcpyHostToDevice));
         } else {
             CK(cudaMemcpy(C->Msd, all.data(), all.size() * 8, cudaMemcpyHostToDevice));
+        }
+    }
+    // per-cell A and D
+    if (C->cell_elems) {
+        std::vector<double> all(C->cell_elems);
+        for (const SimHost& s : C->sims)
+            if (s.d.cell_off >= 0) std::copy(s.AD.begin(), s.AD.end(), all.begin() + s.d.cell_off);
+        if (f32) {
+            std::vector<float> fl(all.size());
+            to_prec(all.data(), fl.data(), all.size());
+            CK(cudaMemcpy(C->cellp, fl.data(), fl.size() * 4, cudaMemcpyHostToDevice));
+        } else {
+            CK(cudaMemcpy(C->cellp, all.data(), all.size() * 8, cudaMemcpyHostToDevice));
         }
     }
     engine_set_attributes();
@@ -969,6 +1063,10 @@ int mm_rk4(mm_ctx* C, double h, long long n_steps, int cayley) {
     if (C->neb) return fail(C, MM_EINVAL, "mm_rk4: not in a context with NEB chains");
     if (!(h > 0.0) || std::isinf(h) || n_steps < 0 || (cayley != 0 && cayley != 1))
         return fail(C, MM_EINVAL, "mm_rk4: bad arguments");
+    if (cayley)
+        for (const SimHost& s : C->sims)
+            if (s.d.eflags & (E_STT | E_SOT))
+                return fail(C, MM_EINVAL, "mm_rk4: the Cayley scheme takes f from H_eff; spin torques need cayley = 0");
     if ((rc = c4_prepare(C, h, cayley))) return rc;
     for (long long i = 0; i < n_steps; ++i) CK(cudaGraphLaunch(C->c4_exec, C->stream));
     C->launches += n_steps * C->c4_graph_kernels;

@@ -44,6 +44,8 @@ struct Launch {
     size_t smem_x = 0, smem_xi = 0, smem_y13 = 0, smem_z = 0, smem_y2 = 0, smem_yzc = 0;
     const void* tensor = nullptr;
     const void* Ms = nullptr;
+    const void* cellp = nullptr;  // per-cell A and D blocks
+    bool ext = false;             // some simulation has extended terms (F_EXT)
     const void* tw = nullptr;
     void* spec = nullptr;
     long long* launches = nullptr;

@@ -16,6 +16,7 @@ static PassParams<T> base_params(const Launch& L) {
     p.spec = reinterpret_cast<V2<T>*>(L.spec);
     p.tensor = reinterpret_cast<const T*>(L.tensor);
     p.Ms = reinterpret_cast<const T*>(L.Ms);
+    p.cellp = reinterpret_cast<const T*>(L.cellp);
     p.tw = reinterpret_cast<const V2<T>*>(L.tw);
     for (int j = 0; j < 7; ++j) p.e[j] = dp_e(j);
     return p;
@@ -113,10 +114,14 @@ static void issue_passes(const Launch& L, PassParams<T> p, const T* ys, bool inc
     }
     if (include_xinv) {
         p.items = L.x.dev;
-        if (p.mode == MODE_ENERGY || p.mode == MODE_NEB)
-            k_xinv<T, true><<<L.x.count, ntxi, L.smem_xi, s>>>(p, ys);
-        else
-            k_xinv<T, false><<<L.x.count, ntxi, L.smem_xi, s>>>(p, ys);
+        const bool en = p.mode == MODE_ENERGY || p.mode == MODE_NEB;
+        if (L.ext) {
+            if (en) k_xinv<T, true, true><<<L.x.count, ntxi, L.smem_xi, s>>>(p, ys);
+            else k_xinv<T, false, true><<<L.x.count, ntxi, L.smem_xi, s>>>(p, ys);
+        } else {
+            if (en) k_xinv<T, true, false><<<L.x.count, ntxi, L.smem_xi, s>>>(p, ys);
+            else k_xinv<T, false, false><<<L.x.count, ntxi, L.smem_xi, s>>>(p, ys);
+        }
         if (hk) hk->mark(KIND_XINV);
         ++n;
     }
@@ -227,8 +232,10 @@ static void set_attrs() {
     cudaFuncSetAttribute(k_xfwd<T, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     cudaFuncSetAttribute(k_xfwd<T, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     cudaFuncSetAttribute(k_xfwd<T, 7>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    cudaFuncSetAttribute(k_xinv<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx - 4096);
-    cudaFuncSetAttribute(k_xinv<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx - 4096);
+    cudaFuncSetAttribute(k_xinv<T, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx - 4096);
+    cudaFuncSetAttribute(k_xinv<T, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx - 4096);
+    cudaFuncSetAttribute(k_xinv<T, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx - 4096);
+    cudaFuncSetAttribute(k_xinv<T, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx - 4096);
     cudaFuncSetAttribute(k_ycol<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     cudaFuncSetAttribute(k_ycol<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     cudaFuncSetAttribute(k_ycol<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);

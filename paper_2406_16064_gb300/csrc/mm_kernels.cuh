@@ -34,7 +34,13 @@ constexpr int MM_XTHREADS_MAX = sizeof(T) == 4 ? 1024 : 512;
 #endif
 
 // F_DMI: interfacial DMI with D != 0; F_EX / F_UNI / F_CUB: A, Ku, Kc != 0.
-enum { F_DEMAG = 1, F_DMI = 2, F_PREC = 4, F_MSARR = 8, F_EX = 16, F_UNI = 32, F_CUB = 64 };
+// F_EXT: the simulation has extended terms (bulk or D_2d DMI, per-cell A / D,
+// spin torques; SimDesc::eflags), evaluated by the extended x-inverse kernel;
+// there F_DMI means DMI of the simulation's class with a non-zero constant and
+// F_EX exchange with a non-zero uniform or per-cell constant.
+enum { F_DEMAG = 1, F_DMI = 2, F_PREC = 4, F_MSARR = 8, F_EX = 16, F_UNI = 32, F_CUB = 64, F_EXT = 128 };
+// extended terms: per-cell A and D, Zhang-Li torque, Slonczewski / spin-orbit torque
+enum { E_CELL = 1, E_STT = 2, E_SOT = 4 };
 
 // Coefficients of the local fields and of the LL torque of one simulation in
 // one precision, computed once on the host (plan_coefficients).  GB300 runs
@@ -52,6 +58,17 @@ struct Coef {
     T u[3], H[3];
     T gt, agt;           // gamma/(1+alpha^2), alpha gamma/(1+alpha^2)
     T pad;
+};
+
+// Coefficients of the extended terms in one precision (plan_extended).
+template <typename T>
+struct ExtCoef {
+    T A, D;              // uniform exchange and DMI constants
+    T dinv_z;            // 1/dz (DMI along z)
+    T gu[3];             // u_c / (2 Delta_c): central-difference (u.grad)m
+    T beta, aJ, bJ;      // non-adiabaticity, Slonczewski / spin-orbit strengths (1/s)
+    T alpha, inv_q;      // alpha, 1 / (1 + alpha^2)
+    T p[3];              // unit polarisation
 };
 
 struct SimDesc {
@@ -78,11 +95,20 @@ struct SimDesc {
     double k_spring;
     Coef<double> cd;         // the coefficients in FP64 and in FP32
     Coef<float> cf;
+    int dmi_kind;            // 0 none, 1 interfacial, 2 bulk, 3 D_2d
+    int eflags;              // E_CELL | E_STT | E_SOT
+    long long cell_off;      // per-cell [A][D] block (2 ncells values), -1 if none
+    double u_stt[3], beta, aJ, bJ, p[3];
+    ExtCoef<double> xd;      // extended-term coefficients in FP64 and in FP32
+    ExtCoef<float> xf;
 };
 
 template <typename T> __host__ __device__ __forceinline__ const Coef<T>& coef(const SimDesc& d);
 template <> __host__ __device__ __forceinline__ const Coef<double>& coef<double>(const SimDesc& d) { return d.cd; }
 template <> __host__ __device__ __forceinline__ const Coef<float>& coef<float>(const SimDesc& d) { return d.cf; }
+template <typename T> __host__ __device__ __forceinline__ const ExtCoef<T>& ext_coef(const SimDesc& d);
+template <> __host__ __device__ __forceinline__ const ExtCoef<double>& ext_coef<double>(const SimDesc& d) { return d.xd; }
+template <> __host__ __device__ __forceinline__ const ExtCoef<float>& ext_coef<float>(const SimDesc& d) { return d.xf; }
 
 struct SimState {
     double t, h, t_end, rtol, max_dmdt;
@@ -551,6 +577,7 @@ struct PassParams {
     const T* __restrict__ Ms;
     const V2<T>* __restrict__ tw;
     int* errflag;           // set by checked builds on an out-of-range index
+    const T* __restrict__ cellp;   // per-cell A and D blocks (SimDesc::cell_off)
 };
 
 // Asynchronous 16-byte global -> shared copies (cp.async, L2 only): a CTA

@@ -28,10 +28,13 @@
 //            LLG equation), optional H_eff, the stage-1 max|dm/dt| and the
 //            stage-7 embedded error norm (ordered-bit max reductions, scaled
 //            and combined in FP64), or the energies (compensated per-thread
-//            sums, FP64 across threads) in energy mode.
+//            sums, FP64 across threads) in energy mode; the extended variant
+//            adds bulk / D_2d DMI, per-cell A and D and the spin torques
+//            (ext_terms.cuh).
 #pragma once
 #include <cooperative_groups.h>
 
+#include "ext_terms.cuh"
 #include "mm_kernels.cuh"
 
 namespace mm {
@@ -568,7 +571,9 @@ __device__ __forceinline__ unsigned long long block_max_u64(unsigned long long v
 
 // Shared memory: two buffers of 3*nrows padded sequences of Kx complex values.
 // ENERGY: energy accumulation (energy and NEB modes) instead of the RK reductions.
-template <typename T, bool ENERGY>
+// EXT: the extended variant, launched when some simulation of the batch has
+// F_EXT (ext_terms.cuh); its other simulations take the standard path.
+template <typename T, bool ENERGY, bool EXT>
 __global__ void __launch_bounds__(MM_XTHREADS_MAX<T>, 1) k_xinv(PassParams<T> p, const T* __restrict__ ys) {
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ unsigned long long red_u[32];
@@ -664,6 +669,9 @@ __global__ void __launch_bounds__(MM_XTHREADS_MAX<T>, 1) k_xinv(PassParams<T> p,
     const T* __restrict__ m2p = m1p + N;
     const int sz = nx * ny;
     const T* __restrict__ msp = msarr ? p.Ms + d.ms_off + (long long)row0 * nx : nullptr;
+    const bool ext = EXT && (d.flags & F_EXT) != 0;
+    const T* __restrict__ acp = (ext && (d.eflags & E_CELL)) ? p.cellp + d.cell_off + (long long)row0 * nx : nullptr;
+    const T* __restrict__ dcp = acp ? acp + N : nullptr;
     const T e7 = (T)dp_e(6);
     const bool red1 = !ENERGY && p.mode == MODE_RK && p.stage == 1;
     const bool red7 = !ENERGY && p.mode == MODE_RK && p.stage == 7;
@@ -692,7 +700,14 @@ __global__ void __launch_bounds__(MM_XTHREADS_MAX<T>, 1) k_xinv(PassParams<T> p,
                 // neighbours are loaded unconditionally (a missing one reads the cell
                 // itself) and masked afterwards, so all loads can be in flight together.
                 T ex0 = 0, ex1 = 0, ex2 = 0, dm0 = 0, dm1 = 0, dm2 = 0;
-                if (do_ex || dmi) {
+                T gv[3] = {(T)0, (T)0, (T)0};                 // (u.grad)m, extended terms
+                if (ext) {
+                    T exv[3] = {(T)0, (T)0, (T)0}, dmv[3] = {(T)0, (T)0, (T)0};
+                    ext_local<T>(d, cf, ext_coef<T>(d), m0p, m1p, m2p, msp, acp, dcp, cell, x, y, z, m0, m1, m2,
+                                 inv, exv, dmv, gv);
+                    ex0 = exv[0]; ex1 = exv[1]; ex2 = exv[2];
+                    dm0 = dmv[0]; dm1 = dmv[1]; dm2 = dmv[2];
+                } else if (do_ex || dmi) {
                     bool ok[6] = {x > 0, x < nx - 1, y > 0, y < ny - 1, z > 0, z < nz - 1};
                     const int off[6] = {-1, 1, -nx, nx, -sz, sz};
                     T j0[6], j1[6], j2[6];
@@ -756,6 +771,7 @@ __global__ void __launch_bounds__(MM_XTHREADS_MAX<T>, 1) k_xinv(PassParams<T> p,
                 const T dd0 = m1 * c2 - m2 * c1, dd1 = m2 * c0 - m0 * c2, dd2 = m0 * c1 - m1 * c0;
                 k0 = -agt * dd0; k1 = -agt * dd1; k2 = -agt * dd2;
                 if (prec) { k0 -= gt * c0; k1 -= gt * c1; k2 -= gt * c2; }
+                if (ext && (d.eflags & (E_STT | E_SOT))) ext_torque<T>(d, ext_coef<T>(d), m0, m1, m2, gv, k0, k1, k2);
             }
             const long long o = tile + cell;
             if (write_k) {

@@ -3,6 +3,7 @@
 // allocation-free entry point so both lay out a simulation the same way.
 #pragma once
 #include <algorithm>
+#include <cmath>
 #include <vector>
 
 #include "mm_kernels.cuh"
@@ -91,6 +92,43 @@ inline void plan_coefficients(SimDesc& d, bool dmi_interfacial) {
     if (d.Kc != 0.0) d.flags |= F_CUB;
     plan_fill_coef(d.cd, d);
     plan_fill_coef(d.cf, d);
+}
+
+template <typename T>
+inline void plan_fill_ext(ExtCoef<T>& c, const SimDesc& d) {
+    c.A = (T)d.A;
+    c.D = (T)d.D;
+    c.dinv_z = (T)(1.0 / d.dz);
+    c.gu[0] = (T)(d.u_stt[0] / (2.0 * d.dx));
+    c.gu[1] = (T)(d.u_stt[1] / (2.0 * d.dy));
+    c.gu[2] = (T)(d.u_stt[2] / (2.0 * d.dz));
+    c.beta = (T)d.beta;
+    c.aJ = (T)d.aJ;
+    c.bJ = (T)d.bJ;
+    c.alpha = (T)d.alpha;
+    c.inv_q = (T)(1.0 / (1.0 + d.alpha * d.alpha));
+    const double pn = std::sqrt(d.p[0] * d.p[0] + d.p[1] * d.p[1] + d.p[2] * d.p[2]);
+    for (int i = 0; i < 3; ++i) c.p[i] = pn > 0.0 ? (T)(d.p[i] / pn) : (T)0;
+}
+
+// The extended terms of d (after plan_coefficients): eflags, F_EXT and, for an
+// extended simulation, F_EX / F_DMI with the per-cell constants taken into
+// account, and both extended coefficient sets.  has_cells: per-cell A and D
+// are given; a_any / d_any: some per-cell A / D is non-zero.
+inline void plan_extended(SimDesc& d, bool has_cells, bool a_any, bool d_any) {
+    d.flags &= ~F_EXT;
+    d.eflags = 0;
+    if (has_cells) d.eflags |= E_CELL;
+    if (d.u_stt[0] != 0.0 || d.u_stt[1] != 0.0 || d.u_stt[2] != 0.0) d.eflags |= E_STT;
+    if (d.aJ != 0.0 || d.bJ != 0.0) d.eflags |= E_SOT;
+    if (d.eflags != 0 || d.dmi_kind >= 2) d.flags |= F_EXT;
+    if (d.flags & F_EXT) {
+        const bool ex = d.A != 0.0 || (has_cells && a_any);
+        const bool dmi = d.dmi_kind != 0 && (d.D != 0.0 || (has_cells && d_any));
+        d.flags = (d.flags & ~(F_EX | F_DMI)) | (ex ? F_EX : 0) | (dmi ? F_DMI : 0);
+    }
+    plan_fill_ext(d.xd, d);
+    plan_fill_ext(d.xf, d);
 }
 
 // Films with 2..kMaxClusterPlanes planes run the cluster-fused y/z pass, which

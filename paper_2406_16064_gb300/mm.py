@@ -69,6 +69,8 @@ SIGNATURES = {
                               C.POINTER(C.c_int)]),
     "mm_minimize_info": (C.c_int, [_P, C.c_int, C.POINTER(C.c_longlong), _D, _D, C.POINTER(C.c_int)]),
     "mm_rk4": (C.c_int, [_P, C.c_double, C.c_longlong, C.c_int]),
+    "mm_set_cell_params": (C.c_int, [_P, C.c_int, _D, _D]),
+    "mm_set_spin_torque": (C.c_int, [_P, C.c_int, _D, C.c_double, C.c_double, C.c_double, _D]),
     "mm_profile_attempts": (C.c_int, [_P, C.c_int, _D, C.POINTER(C.c_longlong)]),
     "mm_debug_bounded_wait": (C.c_int, [_P, C.c_longlong]),
     "mm_kernel_launches": (C.c_longlong, [_P]),
@@ -154,7 +156,27 @@ class Context:
         sid = C.c_int()
         self._check(self.L.mm_add_sim(self.h, C.byref(m), C.byref(t), _dptr(ms), C.byref(sid)))
         self.sims.append((mesh.nx * mesh.ny * mesh.nz))
+        Ac, Dc = getattr(mat, "A_cells", None), getattr(mat, "D_cells", None)
+        if Ac is not None or Dc is not None:
+            self.set_cell_params(sid.value, Ac, Dc)
+        u = tuple(getattr(mat, "u_stt", (0.0, 0.0, 0.0)))
+        if any(v != 0.0 for v in u) or getattr(mat, "aJ", 0.0) != 0.0 or getattr(mat, "bJ", 0.0) != 0.0:
+            self.set_spin_torque(sid.value, u, mat.beta, mat.aJ, mat.bJ, mat.p)
         return sid.value
+
+    def set_cell_params(self, sim, A_cells=None, D_cells=None):
+        """Per-cell exchange / DMI constants (arrays of nz*ny*nx values, None = uniform)."""
+        a = None if A_cells is None else np.ascontiguousarray(A_cells, dtype=np.float64).ravel()
+        d = None if D_cells is None else np.ascontiguousarray(D_cells, dtype=np.float64).ravel()
+        n = self.sims[sim]
+        assert (a is None or a.size == n) and (d is None or d.size == n)
+        self._check(self.L.mm_set_cell_params(self.h, sim, _dptr(a), _dptr(d)))
+
+    def set_spin_torque(self, sim, u=(0.0, 0.0, 0.0), beta=0.0, aJ=0.0, bJ=0.0, p=(0.0, 0.0, 1.0)):
+        """Zhang-Li (u in m/s, beta) and Slonczewski / spin-orbit (a_J, b_J in 1/s, p) torques."""
+        uu = np.ascontiguousarray(u, dtype=np.float64)
+        pp = np.ascontiguousarray(p, dtype=np.float64)
+        self._check(self.L.mm_set_spin_torque(self.h, sim, _dptr(uu), float(beta), float(aJ), float(bJ), _dptr(pp)))
 
     def precompute(self):
         self._check(self.L.mm_precompute_demag(self.h))

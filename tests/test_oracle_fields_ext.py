@@ -107,7 +107,7 @@ def test_extended_fields_are_energy_gradients(kind, cells, masked):
     mesh = synth.Mesh(6, 5, 3, 2e-9, 2.5e-9, 1.5e-9)
     rng = np.random.default_rng(11)
     A_cells = rng.uniform(0.5e-11, 2e-11, mesh.shape) if cells else None
-    D_cells = rng.uniform(-4e-3, 4e-3, mesh.shape) if cells else None
+    D_cells = rng.uniform(1e-3, 4e-3, mesh.shape) if cells else None
     if cells:
         A_cells[1, 2, 2] = 0.0                          # a cell decoupled from its neighbours
     mat = synth.Material(Ms=8e5, A=1.3e-11, D=3e-3, dmi=kind, demag=0, A_cells=A_cells, D_cells=D_cells)

@@ -69,3 +69,19 @@ def test_static_rhs_rejects_meshes_beyond_the_scratch():
     rc = L.mm_rhs_eval_static(ctypes.byref(cm), ctypes.byref(cmat), mm.MM_F64, p, p, None, None)
     assert rc == mm.MM_EINVAL
     assert b"32 MiB" in L.mm_last_error(None)
+
+
+@pytest.mark.parametrize("kind", [2, 3])
+def test_static_rhs_rejects_other_dmi_classes(kind):
+    """Bulk and D_2d DMI run in the context path only; the static entry refuses them
+    before touching the GPU."""
+    torch = pytest.importorskip("torch")
+    from paper_2406_16064_gb300 import mm
+    mesh = synth.Mesh(8, 8, 1, 2e-9, 2e-9, 2e-9)
+    cm, cmat = _structs(mm, mesh, synth.Material(Ms=8e5, A=1e-11, D=3e-3, dmi=kind))
+    L = mm.lib()
+    buf = torch.zeros(16, dtype=torch.float64, device="cuda")
+    p = ctypes.c_void_p(buf.data_ptr())
+    rc = L.mm_rhs_eval_static(ctypes.byref(cm), ctypes.byref(cmat), mm.MM_F64, p, p, None, None)
+    assert rc == mm.MM_EINVAL
+    assert b"DMI" in L.mm_last_error(None)
