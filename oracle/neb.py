@@ -23,10 +23,14 @@ the published geodesic NEB (Bessarab, Uzdin & Jonsson, CPC 196, 335
     adaptive RK45 of oracle.integrate (a single h, the error is the max
     over all images).
 
-Parity: partially pinned.  tests/test_oracle_neb.py checks a single-cell
-uniaxial chain (in a field along the axis) against the Stoner-Wohlfarth
-energy at equally spaced angles, fixed ends and |m| = 1; beyond that the
-chain dynamics are "parity unpinned" and are compared GPU-vs-oracle only.
+Parity: pinned by tests/test_oracle_neb.py -- a single-cell uniaxial chain
+(in a field along the axis) against the Stoner-Wohlfarth energy at equally
+spaced angles, fixed ends and |m| = 1; a chain of two uncoupled particles
+(a multi-cell image whose path turns one cell, then the other) against the
+closed-form energy of every image at equal geodesic spacing, the path
+length 2 pi and the intermediate minimum (this fails with the tangent
+normalised per cell or a wrong spring sign); the geodesic distance against
+theta sqrt(N) for N cells turned by theta.
 """
 from __future__ import annotations
 
