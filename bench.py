@@ -143,7 +143,7 @@ def kernel_bytes(w, e):
     return out
 
 
-def step_bytes_survey(w, e):
+def step_bytes_whole(w, e):
     """The whole-step algorithmic figure: 22.5 e + T bytes per cell-update (T = tensor bytes / cell)."""
     tot = 0.0
     for s in w.sims:
@@ -453,7 +453,7 @@ def run_gpu(args, rank, world, dist):
     bytes_per_launch = kb[dom] / launches_dom
     achieved = bytes_per_launch / (avg_launch_ms / 1e3) / 1e9
     step_ms = ms_max / args.steps
-    step_bytes = step_bytes_survey(w, e)
+    step_bytes = step_bytes_whole(w, e)
     # end to end through the C ABI with host buffers: H2D of m, one attempt, D2H of m
     ke = max(3, min(50, args.steps // 20))
     mhost = ctx.get_m(-1)
