@@ -100,7 +100,9 @@ const char *mm_last_error(const mm_ctx *ctx);
 /* Add a simulation (mesh + material + optional per-cell Ms, host double
  * array of nx*ny*nz values, NULL for uniform Ms = mat->Ms; Ms = 0 marks
  * cells outside the shape, Listing 1).  Must precede mm_precompute_demag.
- * Limits: each padded FFT length (next power of two >= 2n-1) <= 8192. */
+ * Limits: each padded FFT length (next power of two >= 2n-1) <= 8192 in an
+ * FP32 context, <= 4096 in an FP64 context (one row or column tile in shared
+ * memory); MM_EINVAL otherwise. */
 int mm_add_sim(mm_ctx *ctx, const mm_mesh *mesh, const mm_material *mat,
                const double *Ms_cells, int *sim_id);
 

@@ -547,9 +547,10 @@ int mm_add_sim(mm_ctx* C, const mm_mesh* mesh, const mm_material* mat, const dou
     memset(&d, 0, sizeof(d));
     d.nx = mesh->nx; d.ny = mesh->ny; d.nz = mesh->nz;
     d.ncells = (int)ncells;
-    const int lim_yz = C->precision == MM_F32 ? 8192 : 4096;
-    if (plan_pad_len(d.nx, true) > 8192 || plan_pad_len(d.ny, false) > lim_yz || plan_pad_len(d.nz, false) > lim_yz)
-        return fail(C, MM_EINVAL, "padded FFT length too large (max 8192 along x, %d along y/z)", lim_yz);
+    // one x row (two padded buffers of three components) and one column tile must fit a CTA's shared memory
+    const int lim = C->precision == MM_F32 ? 8192 : 4096;
+    if (plan_pad_len(d.nx, true) > lim || plan_pad_len(d.ny, false) > lim || plan_pad_len(d.nz, false) > lim)
+        return fail(C, MM_EINVAL, "padded FFT length too large (max %d along each axis in this precision)", lim);
     plan_geometry(d, C->precision == MM_F32);
     double un = std::sqrt(mat->u[0] * mat->u[0] + mat->u[1] * mat->u[1] + mat->u[2] * mat->u[2]);
     if (mat->Ku != 0.0 && !(un > 0)) return fail(C, MM_EINVAL, "anisotropy axis is zero");
