@@ -41,7 +41,9 @@ energy gap) and tests/test_oracle_fields_ext.py (bulk and D_2d helix closed
 forms, the continuum DMI fields of the paper on a smooth texture, energy
 gradients with every DMI class and cell-based A / D, the Gilbert-form torques
 solved per cell, spin-orbit macrospin closed forms, uniform translation at
-beta = alpha).
+beta = alpha, and the head-to-head wall of Sec. "Domain-wall motion under
+currents" under the paper's time-dependent current, whose centre and tilt
+follow the closed form).
 """
 from __future__ import annotations
 

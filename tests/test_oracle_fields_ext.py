@@ -269,3 +269,45 @@ def test_zhang_li_uniform_translation_and_gradient():
     Mx = synth.Material(Ms=8e5, demag=0, u_stt=(50.0, 0.0, 0.0))
     Gx = F.u_grad_m(thin, Mx, mt, F.ms_array(thin, Mx))
     np.testing.assert_allclose(Gx[:, 0, 1, 0], 50.0 * (mt[:, 0, 1, 1] - mt[:, 0, 1, 0]) / 2e-9, rtol=1e-14)
+
+
+@pytest.mark.parametrize("beta", [0.0, 0.3])
+def test_head_to_head_wall_under_time_dependent_current(beta):
+    """Sec. "Domain-wall motion under currents": a 1D head-to-head wall (uniaxial K along
+    the wire, no demag) driven by u(t) = u0 exp(-b t) cos(w t) with b = 5e8 1/s, w = 2e9 1/s,
+    Permalloy constants, alpha = 0.1.  For dm/dt = -gamma m x H + alpha m x dm/dt
+    - (u.grad)m + beta m x (u.grad)m the rigid wall moves with dz/dt = (1 + alpha beta) u /
+    (1 + alpha^2) and tilts with dphi/dt = (beta - alpha) u / ((1 + alpha^2) Delta),
+    Delta = sqrt(A/K) (the paper prints both with u of the opposite sign; magnitudes and
+    their ratio agree)."""
+    from dataclasses import replace
+    nx, dx = 200, 1e-9
+    mesh = synth.Mesh(nx, 1, 1, dx, dx, dx)
+    A, K, al = 1.3e-11, 1e5, 0.1
+    Dw = math.sqrt(A / K)
+    mat = synth.Material(Ms=8e5, A=A, Ku=K, u=(1, 0, 0), alpha=al, beta=beta, demag=0)
+    u0, b, w = 100.0, 5e8, 2e9
+    u = lambda t: u0 * math.exp(-b * t) * math.cos(w * t)
+    Iu = lambda t: u0 * (math.exp(-b * t) * (w * math.sin(w * t) - b * math.cos(w * t)) + b) / (b * b + w * w)
+    x = (np.arange(nx) + 0.5) * dx
+    th = 2 * np.arctan(np.exp((x - 60e-9) / Dw))            # +x on the left, -x on the right
+    m = np.stack([np.cos(th), np.sin(th) * np.cos(0.4), np.sin(th) * np.sin(0.4)]).reshape(3, 1, 1, nx)
+    Ms = F.ms_array(mesh, mat)
+    f = lambda t, y: F.rhs(mesh, replace(mat, u_stt=(u(t), 0.0, 0.0)), y, Ms)[0]
+    centre = lambda m: nx * dx - ((1 - m[0].ravel()) / 2).sum() * dx
+    tilt = lambda m: math.atan2(m[2].sum(), m[1].sum())
+    z0, p0 = centre(m), tilt(m)
+    h, n = 8e-14, 5000
+    t = 0.0
+    dz, dp, ez, ep = [], [], [], []
+    for i in range(n):                                    # classical RK4 with u at the stage times
+        k1 = f(t, m); k2 = f(t + h / 2, m + h / 2 * k1); k3 = f(t + h / 2, m + h / 2 * k2); k4 = f(t + h, m + h * k3)
+        m = m + h / 6 * (k1 + 2 * k2 + 2 * k3 + k4)
+        m = m / np.sqrt((m ** 2).sum(0))[None]
+        t += h
+        if (i + 1) % 250 == 0:
+            dz.append(centre(m) - z0); ez.append((1 + al * beta) / (1 + al * al) * Iu(t))
+            dp.append(tilt(m) - p0); ep.append((beta - al) / ((1 + al * al) * Dw) * Iu(t))
+    dz, ez, dp, ep = map(np.array, (dz, ez, dp, ep))
+    assert np.abs(dz - ez).max() < 0.01 * np.abs(ez).max()
+    assert np.abs(dp - ep).max() < 0.02 * np.abs(ep).max()
