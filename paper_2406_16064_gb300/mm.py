@@ -160,8 +160,9 @@ class Context:
         if Ac is not None or Dc is not None:
             self.set_cell_params(sid.value, Ac, Dc)
         u = tuple(getattr(mat, "u_stt", (0.0, 0.0, 0.0)))
-        if any(v != 0.0 for v in u) or getattr(mat, "aJ", 0.0) != 0.0 or getattr(mat, "bJ", 0.0) != 0.0:
-            self.set_spin_torque(sid.value, u, mat.beta, mat.aJ, mat.bJ, mat.p)
+        aJ, bJ = getattr(mat, "aJ", 0.0), getattr(mat, "bJ", 0.0)
+        if any(v != 0.0 for v in u) or aJ != 0.0 or bJ != 0.0:
+            self.set_spin_torque(sid.value, u, getattr(mat, "beta", 0.0), aJ, bJ, getattr(mat, "p", (0.0, 0.0, 1.0)))
         return sid.value
 
     def set_cell_params(self, sim, A_cells=None, D_cells=None):
