@@ -185,6 +185,28 @@ int mm_relax(mm_ctx *ctx, double rtol, double t_end, double max_dmdt, long long 
 int mm_get_status(mm_ctx *ctx, int sim_id, mm_status *out);
 int mm_reset_time(mm_ctx *ctx);
 
+/* Integrator state of one simulation, for checkpoint and resume.  Together
+ * with its magnetisation (mm_get_m / mm_set_m; a host round trip is exact in
+ * both precisions) it is everything the next RK45 attempt reads: there is no
+ * first-same-as-last stage carried between attempts, and the reduction
+ * fields an attempt accumulates start from zero.  Restoring both into the
+ * same context, or into one built with the same simulations and precision,
+ * continues the integration exactly as the uninterrupted run would.
+ * mm_set_checkpoint returns MM_EINVAL for rtol <= 0, a negative or
+ * non-finite h or t, or a status outside {0, 1, 2} and the error codes. */
+typedef struct {
+    double t;             /* simulated time, s */
+    double h;             /* next step size, s (0: chosen at the next attempt) */
+    double t_end;         /* stop time, s (0: none) */
+    double rtol;          /* step-controller tolerance */
+    double max_dmdt;      /* relax threshold, rad/s (0: none) */
+    long long n_accepted, n_rejected;
+    int status;           /* as in mm_status */
+    int pad;
+} mm_checkpoint;
+int mm_get_checkpoint(mm_ctx *ctx, int sim_id, mm_checkpoint *out);
+int mm_set_checkpoint(mm_ctx *ctx, int sim_id, const mm_checkpoint *in);
+
 /* Energies of one simulation at its current m, J:
  * E[0..6] = exchange, dmi, uniaxial, cubic, zeeman, demag, total. */
 int mm_energy(mm_ctx *ctx, int sim_id, double E[7]);

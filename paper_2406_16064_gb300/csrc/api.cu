@@ -1102,6 +1102,39 @@ int mm_get_status(mm_ctx* C, int sim, mm_status* out) {
     return MM_OK;
 }
 
+int mm_get_checkpoint(mm_ctx* C, int sim, mm_checkpoint* out) {
+    int rc = check_ready(C);
+    if (rc) return rc;
+    if (!out || sim < 0 || sim >= (int)C->sims.size()) return fail(C, MM_EINVAL, "bad arguments");
+    SimState s;
+    CK(cudaMemcpyAsync(&s, C->state_d + sim, sizeof(s), cudaMemcpyDeviceToHost, C->stream));
+    CK(cudaStreamSynchronize(C->stream));
+    out->t = s.t; out->h = s.h; out->t_end = s.t_end; out->rtol = s.rtol; out->max_dmdt = s.max_dmdt;
+    out->n_accepted = s.n_acc; out->n_rejected = s.n_rej;
+    out->status = s.status; out->pad = 0;
+    return MM_OK;
+}
+
+int mm_set_checkpoint(mm_ctx* C, int sim, const mm_checkpoint* in) {
+    int rc = check_ready(C);
+    if (rc) return rc;
+    if (!in || sim < 0 || sim >= (int)C->sims.size()) return fail(C, MM_EINVAL, "bad arguments");
+    const bool st_ok = in->status == 0 || in->status == 1 || in->status == 2 || in->status == MM_ENAN ||
+                       in->status == MM_ESTEP;
+    if (!(in->rtol > 0.0) || !(in->h >= 0.0) || std::isinf(in->h) || !std::isfinite(in->t) ||
+        !(in->t_end >= 0.0) || std::isinf(in->t_end) || !(in->max_dmdt >= 0.0) || in->n_accepted < 0 ||
+        in->n_rejected < 0 || !st_ok)
+        return fail(C, MM_EINVAL, "mm_set_checkpoint: invalid checkpoint");
+    SimState s;
+    memset(&s, 0, sizeof(s));   // reductions start from zero, as after the controller of an attempt
+    s.t = in->t; s.h = in->h; s.t_end = in->t_end; s.rtol = in->rtol; s.max_dmdt = in->max_dmdt;
+    s.n_acc = in->n_accepted; s.n_rej = in->n_rejected;
+    s.status = in->status;
+    CK(cudaMemcpyAsync(C->state_d + sim, &s, sizeof(s), cudaMemcpyHostToDevice, C->stream));
+    CK(cudaStreamSynchronize(C->stream));
+    return MM_OK;
+}
+
 int mm_energy(mm_ctx* C, int sim, double E[7]) {
     int rc = check_ready(C);
     if (rc) return rc;

@@ -33,6 +33,12 @@ class mm_material(C.Structure):
                 ("alpha", C.c_double), ("gamma", C.c_double), ("precession", C.c_int), ("demag", C.c_int)]
 
 
+class mm_checkpoint(C.Structure):
+    _fields_ = [("t", C.c_double), ("h", C.c_double), ("t_end", C.c_double), ("rtol", C.c_double),
+                ("max_dmdt", C.c_double), ("n_accepted", C.c_longlong), ("n_rejected", C.c_longlong),
+                ("status", C.c_int), ("pad", C.c_int)]
+
+
 class mm_status(C.Structure):
     _fields_ = [("t", C.c_double), ("h", C.c_double), ("err", C.c_double), ("max_dmdt", C.c_double),
                 ("n_accepted", C.c_longlong), ("n_rejected", C.c_longlong), ("status", C.c_int),
@@ -70,6 +76,8 @@ SIGNATURES = {
     "mm_minimize_info": (C.c_int, [_P, C.c_int, C.POINTER(C.c_longlong), _D, _D, C.POINTER(C.c_int)]),
     "mm_rk4": (C.c_int, [_P, C.c_double, C.c_longlong, C.c_int]),
     "mm_set_cell_params": (C.c_int, [_P, C.c_int, _D, _D]),
+    "mm_get_checkpoint": (C.c_int, [_P, C.c_int, C.POINTER(mm_checkpoint)]),
+    "mm_set_checkpoint": (C.c_int, [_P, C.c_int, C.POINTER(mm_checkpoint)]),
     "mm_set_spin_torque": (C.c_int, [_P, C.c_int, _D, C.c_double, C.c_double, C.c_double, _D]),
     "mm_profile_attempts": (C.c_int, [_P, C.c_int, _D, C.POINTER(C.c_longlong)]),
     "mm_debug_bounded_wait": (C.c_int, [_P, C.c_longlong]),
@@ -252,6 +260,17 @@ class Context:
         s = mm_status()
         self._check(self.L.mm_get_status(self.h, sim, C.byref(s)))
         return {k: getattr(s, k) for k, _ in mm_status._fields_ if k != "pad"}
+
+    def checkpoint(self, sim):
+        """Integrator state of one simulation (t, h, t_end, rtol, max_dmdt, counters, status)."""
+        c = mm_checkpoint()
+        self._check(self.L.mm_get_checkpoint(self.h, sim, C.byref(c)))
+        return {k: getattr(c, k) for k, _ in mm_checkpoint._fields_ if k != "pad"}
+
+    def restore(self, sim, ckpt):
+        """Set the integrator state of one simulation from checkpoint()'s dict."""
+        c = mm_checkpoint(**{k: ckpt[k] for k, _ in mm_checkpoint._fields_ if k != "pad"})
+        self._check(self.L.mm_set_checkpoint(self.h, sim, C.byref(c)))
 
     def energy(self, sim):
         E = np.zeros(7)
