@@ -194,3 +194,40 @@ def test_rk4_cayley_with_bulk_dmi_and_refusal_with_torques():
     with pytest.raises(mm.MMError):
         ctx.rk4(2e-14, 1, True)
     ctx.rk4(2e-14, 1, False)                       # the projected scheme takes them
+
+
+def test_wall_under_time_dependent_current_on_gpu():
+    """The paper's head-to-head wall under u(t) = u0 exp(-b t) cos(w t) (Sec. "Domain-wall
+    motion under currents"), FP64 on the GPU: fixed RK4 steps with projection, u set at
+    each step's midpoint; centre and tilt follow dz/dt = (1 + alpha beta) u / (1 + alpha^2)
+    and dphi/dt = (beta - alpha) u / ((1 + alpha^2) Delta) as in the oracle's test."""
+    import math
+    nx, dx = 200, 1e-9
+    mesh = synth.Mesh(nx, 1, 1, dx, dx, dx)
+    A, K, al, beta = 1.3e-11, 1e5, 0.1, 0.3
+    Dw = math.sqrt(A / K)
+    mat = synth.Material(Ms=8e5, A=A, Ku=K, u=(1, 0, 0), alpha=al, beta=beta, demag=0)
+    u0, b, w = 100.0, 5e8, 2e9
+    u = lambda t: u0 * math.exp(-b * t) * math.cos(w * t)
+    Iu = lambda t: u0 * (math.exp(-b * t) * (w * math.sin(w * t) - b * math.cos(w * t)) + b) / (b * b + w * w)
+    x = (np.arange(nx) + 0.5) * dx
+    th = 2 * np.arctan(np.exp((x - 60e-9) / Dw))
+    m0 = np.stack([np.cos(th), np.sin(th) * np.cos(0.4), np.sin(th) * np.sin(0.4)]).reshape(3, 1, 1, nx)
+    ctx = make_ctx("f64", [synth.Sim(mesh, mat, m0)])
+    ctx.set_m(m0.ravel())
+    centre = lambda m: nx * dx - ((1 - m[0].ravel()) / 2).sum() * dx
+    tilt = lambda m: math.atan2(m[2].sum(), m[1].sum())
+    z0, p0 = centre(m0), tilt(m0)
+    h, n = 8e-14, 5000
+    dz, dp, ez, ep = [], [], [], []
+    for i in range(n):
+        ctx.set_spin_torque(0, (u((i + 0.5) * h), 0.0, 0.0), beta, 0.0, 0.0, (0.0, 0.0, 1.0))
+        ctx.rk4(h, 1, False)
+        if (i + 1) % 250 == 0:
+            m = ctx.get_m(0).reshape(3, 1, 1, nx)
+            t = (i + 1) * h
+            dz.append(centre(m) - z0); ez.append((1 + al * beta) / (1 + al * al) * Iu(t))
+            dp.append(tilt(m) - p0); ep.append((beta - al) / ((1 + al * al) * Dw) * Iu(t))
+    dz, ez, dp, ep = map(np.array, (dz, ez, dp, ep))
+    assert np.abs(dz - ez).max() < 0.01 * np.abs(ez).max()
+    assert np.abs(dp - ep).max() < 0.02 * np.abs(ep).max()
