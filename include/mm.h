@@ -53,7 +53,8 @@ enum {
     MM_ENAN = -4,       /* non-finite error norm in a step */
     MM_ESTEP = -5,      /* step size underflow */
     MM_ETIMEOUT = -6,   /* a bounded device wait ran out */
-    MM_EBOUNDS = -7     /* a checked kernel saw an out-of-range index */
+    MM_EBOUNDS = -7     /* a work item or block offset of the plan would leave its buffer
+                           (checked on the host before the first launch) */
 };
 
 enum { MM_F64 = 0, MM_F32 = 1 };          /* context precision */

@@ -207,6 +207,8 @@ int validate_items(mm_ctx* C) {
             if ((d.NBx << d.lTy) < d.Kx || d.Ty != (1 << d.lTy)) return fail(C, MM_EBOUNDS, "kx blocks");
         }
         if (d.ms_off >= 0 && d.ms_off + d.ncells > C->ms_elems) return fail(C, MM_EBOUNDS, "Ms array");
+        if ((d.eflags & E_CELL) && (d.cell_off < 0 || d.cell_off + 2LL * d.ncells > C->cell_elems))
+            return fail(C, MM_EBOUNDS, "per-cell A and D block");
     }
     for (const WorkItem& w : P.x) {
         const SimDesc& d = C->sims[w.sim].d;

@@ -29,10 +29,6 @@
 template <typename T>
 constexpr int MM_XTHREADS_MAX = sizeof(T) == 4 ? 1024 : 512;
 
-#ifndef MM_CHECKED
-#define MM_CHECKED 0
-#endif
-
 // F_DMI: interfacial DMI with D != 0; F_EX / F_UNI / F_CUB: A, Ku, Kc != 0.
 // F_EXT: the simulation has extended terms (bulk or D_2d DMI, per-cell A / D,
 // spin torques; SimDesc::eflags), evaluated by the extended x-inverse kernel;
@@ -576,7 +572,6 @@ struct PassParams {
     const T* __restrict__ tensor;
     const T* __restrict__ Ms;
     const V2<T>* __restrict__ tw;
-    int* errflag;           // set by checked builds on an out-of-range index
     const T* __restrict__ cellp;   // per-cell A and D blocks (SimDesc::cell_off)
 };
 
