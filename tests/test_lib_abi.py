@@ -56,3 +56,5 @@ def test_struct_layouts_match_the_header(libpath):
     # Ms A D (24) + int+pad (8) + Ku u[3] Kc (40) + H[3] (24) + alpha gamma (16) + 2 ints (8)
     assert ctypes.sizeof(mm.mm_material) == 120
     assert ctypes.sizeof(mm.mm_status) == 4 * 8 + 2 * 8 + 2 * 4
+    # t h t_end rtol max_dmdt (40) + two counters (16) + status, pad (8)
+    assert ctypes.sizeof(mm.mm_checkpoint) == 5 * 8 + 2 * 8 + 2 * 4
