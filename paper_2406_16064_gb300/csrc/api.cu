@@ -22,6 +22,12 @@
 
 using namespace mm;
 
+// the Python binding and other callers lay these out from the header by hand
+static_assert(sizeof(mm_mesh) == 40, "mm_mesh layout");
+static_assert(sizeof(mm_material) == 120, "mm_material layout");
+static_assert(sizeof(mm_status) == 56, "mm_status layout");
+static_assert(sizeof(mm_checkpoint) == 64, "mm_checkpoint layout");
+
 namespace {
 
 constexpr double kPi = 3.14159265358979323846;
