@@ -23,6 +23,9 @@ and with steepest descent and reports both wall times.
 projection; `--driver cayley-error` runs the paper's macrospin comparison of the
 two schemes (error against the closed form at 1 ns over a range of h).
 
+`--ext` adds per-cell exchange and DMI constants and a Zhang-Li drift to the
+workload, so the extended x-inverse variant runs (workload name `*_ext`).
+
 `--workload sweep` times the N x N x 1 family of the paper's throughput
 comparison (demag + exchange + Zeeman, N = 128 ... 4096, FP32) and reports each
 N as RHS cell-updates/s and as Heun-equivalent cells/s (RHS rate / 2).
@@ -62,6 +65,11 @@ def peaks():
 
 
 # ------------------------------------------------------------------ workloads
+def workload_for(args, world=1):
+    w = workload(args.workload, world)
+    return synth.with_extended_terms(w) if getattr(args, "ext", False) else w
+
+
 def workload(name, world=1):
     if name == "film":
         return synth.skyrmion_film(precision="f32")
@@ -139,6 +147,8 @@ def kernel_bytes(w, e):
                 elif Py > 1:
                     out["y_fused"] += 2 * spec_rows + tens
             out["x_inverse_epilogue"] += (spec_rows if demag else 0) + 6 * e * n + (3 * e * n if st == 7 else 0)
+            if getattr(s.mat, "A_cells", None) is not None or getattr(s.mat, "D_cells", None) is not None:
+                out["x_inverse_epilogue"] += 2 * e * n          # per-cell A and D
         out["project"] += 6 * e * n
     return out
 
@@ -289,7 +299,7 @@ def run_reference(args, rank, world):
     take about REFERENCE_BUDGET_S seconds."""
     from oracle import demag as D
     from oracle import fields as F
-    w = workload(args.workload)
+    w = workload_for(args)
     line = {"impl": "reference", "metric": METRIC, "unit": UNIT, "n_gpus": world, "higher_is_better": True,
             "data": "synthetic", "dtype": "f64",
             "config": {"workload": w.name, "cells": cells(w), "path": "FP64 numpy oracle, host cores"}}
@@ -401,7 +411,7 @@ def run_gpu(args, rank, world, dist):
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
     stream = torch.cuda.Stream()
-    w = workload(args.workload, world)
+    w = workload_for(args, world)
     sharded = world > 1 and len(w.sims) > 1 and not w.neb
     if sharded:
         # independent simulations: each rank owns a cost-balanced share of the global batch
@@ -687,6 +697,8 @@ def main():
                     help="rk45 (default), sd (steepest-descent steps), relax-compare, rk4-cayley, "
                          "rk4-proj or cayley-error")
     ap.add_argument("--max-dmdt", type=float, default=1e7, help="relax-compare threshold, rad/s")
+    ap.add_argument("--ext", action="store_true",
+                    help="add per-cell A and D and a Zhang-Li drift to the workload (extended epilogue)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -343,3 +343,16 @@ def uneven_batch(seed: int = 5, count: int = 64, precision: str = "f32",
 
 def with_precision(w: Workload, precision: str) -> Workload:
     return replace(w, precision=precision)
+
+
+def with_extended_terms(w: Workload, seed: int = 7) -> Workload:
+    """The workload with per-cell exchange and DMI constants (uniform within +-10 % of
+    the material's) and a Zhang-Li drift u = (50, 0, 0) m/s, beta = 0.1: inputs that
+    run the extended epilogue on the same meshes and states."""
+    sims = []
+    for i, s in enumerate(w.sims):
+        r = uniform(seed + i, 2 * s.mesh.ncells).reshape((2,) + s.mesh.shape)
+        mat = replace(s.mat, A_cells=s.mat.A * (0.9 + 0.2 * r[0]), D_cells=s.mat.D * (0.9 + 0.2 * r[1]),
+                      u_stt=(50.0, 0.0, 0.0), beta=0.1)
+        sims.append(replace(s, mat=mat))
+    return replace(w, name=w.name + "_ext", sims=sims)

@@ -28,3 +28,20 @@ def test_reference_block_is_a_power_of_two_crop_of_the_workload():
     assert np.array_equal(b.m0, s.m0[:, :, :16, :16]) and b.mat is s.mat
     tiny = bench.reference_block(s, 1e-6)
     assert (tiny.mesh.nx, tiny.mesh.ny) == (8, 8)
+
+
+def test_extended_workload_switch():
+    """--ext: per-cell A and D within 10 % of the material's and a Zhang-Li drift on the
+    same meshes and states; the x inverse reads 2 more values a cell per stage; the
+    reference arm runs the oracle on it."""
+    args = argparse.Namespace(workload="film_relax_32", steps=2, warmup=3, ext=True)
+    w0 = bench.workload("film_relax_32")
+    w = bench.workload_for(args)
+    assert w.name == w0.name + "_ext"
+    s, s0 = w.sims[0], w0.sims[0]
+    assert np.array_equal(s.m0, s0.m0) and s.mesh == s0.mesh and s0.mat.A_cells is None
+    assert np.all(np.abs(s.mat.A_cells / s0.mat.A - 1) <= 0.1) and s.mat.u_stt == (50.0, 0.0, 0.0)
+    kb, kb0 = bench.kernel_bytes(w, 8), bench.kernel_bytes(w0, 8)
+    assert kb["x_inverse_epilogue"] - kb0["x_inverse_epilogue"] == 7 * 2 * 8 * s.mesh.ncells
+    line = bench.run_reference(args, 0, 1)
+    assert line["config"]["workload"].endswith("_ext") and line["value"] > 0
