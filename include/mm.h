@@ -5,16 +5,23 @@
  *   the Landau-Lifshitz-Gilbert right-hand side on a regular cell mesh,
  *   dm/dt = -g~ m x H - alpha g~ m x (m x H), g~ = gamma/(1+alpha^2)
  *   (Sec. "LLG equation", LL form), with the effective field (Eq. 1) the sum of
- *     exchange             Sec. "Exchange energy", Eq. 5 (6-neighbour stencil)
- *     interfacial DMI      Sec. "Dzyaloshinskii-Moriya Energy", Eq. 14
+ *     exchange             Sec. "Exchange energy", Eq. 5 (6-neighbour stencil;
+ *                          uniform A or cell-based A with harmonic-mean pairs)
+ *     DMI                  Sec. "Dzyaloshinskii-Moriya Energy", Eq. 14 and its
+ *                          unified form: interfacial, bulk or D_2d vectors,
+ *                          uniform or cell-based D
  *     uniaxial / cubic     Sec. "Anisotropy"
  *     Zeeman               Sec. "Zeeman energy"
  *     demagnetising field  Sec. "Magnetostatic energy", Eqs. 6-8: the discrete
  *                          convolution with the Newell tensor, evaluated by
  *                          zero-padded FFTs;
- *   integrated with adaptive Dormand-Prince RK45 and projection onto |m| = 1
- *   after every accepted step (Sec. "LLG equation"), and the nudged elastic
- *   band of Sec. "Miscellaneous".
+ *   plus, optionally, the spin-transfer and spin-orbit torques of Sec. "Spin
+ *   transfer torques" in the right-hand side; integrated with adaptive
+ *   Dormand-Prince RK45 and projection onto |m| = 1 after every accepted step
+ *   (Sec. "LLG equation") or fixed-step RK4 with projection or on the Cayley
+ *   variable (Sec. "Cayley transform"), minimised by steepest descent (Sec.
+ *   "Steepest descent energy minimization"), and the nudged elastic band of
+ *   Sec. "Miscellaneous".
  *
  * Conventions
  *   Units are SI: lengths m, fields A/m, Ms A/m, A J/m, D J/m^2, K J/m^3,
