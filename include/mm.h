@@ -163,10 +163,11 @@ int mm_newell_tensor(mm_ctx *ctx, int sim_id, double *out_host);
 int mm_set_m(mm_ctx *ctx, int sim_id, const void *m, int where);
 int mm_get_m(mm_ctx *ctx, int sim_id, void *m, int where);
 
-/* One right-hand-side evaluation (Eqs. 1-14 + LL form) of caller-owned
- * device buffers: m_dev in, dmdt_dev out, heff_dev (nullable) out, all in
- * the context precision, [3][N] per simulation (sim_id = -1: whole batch
- * layout).  Asynchronous on the context stream. */
+/* One right-hand-side evaluation (Eqs. 1-14 + LL form, with the spin torques
+ * when set) of caller-owned device buffers: m_dev in, dmdt_dev out, heff_dev
+ * (nullable) out, all in the context precision, [3][N] per simulation
+ * (sim_id = -1: whole batch layout).  H_eff holds the field terms only (the
+ * spin torques are not fields).  Asynchronous on the context stream. */
 int mm_rhs_eval(mm_ctx *ctx, int sim_id, const void *m_dev, void *dmdt_dev, void *heff_dev);
 
 /* The same evaluation with host double buffers (copies inside the call). */
