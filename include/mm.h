@@ -283,7 +283,10 @@ int mm_rk4(mm_ctx *ctx, double h, long long n_steps, int cayley);
 int mm_profile_attempts(mm_ctx *ctx, int reps, double *ms, long long *counts);
 
 /* Debugging aid: bounded-wait check.  Runs a kernel that waits on a device
- * flag nobody sets, for at most `spins` polls, and returns MM_ETIMEOUT. */
+ * flag nobody sets, for at most `spins` polls, and returns MM_ETIMEOUT.
+ * `spins` must lie in [0, MM_MAX_WAIT_SPINS] (2^22 polls, about a second of
+ * polling at most); other values return MM_EINVAL before anything runs. */
+#define MM_MAX_WAIT_SPINS (1LL << 22)
 int mm_debug_bounded_wait(mm_ctx *ctx, long long spins);
 
 /* Number of kernels this context launched (graph launches count their
@@ -306,8 +309,10 @@ long long mm_kernel_launches(const mm_ctx *ctx);
  * that every GPU loading libmm holds until the process exits.  A mesh whose
  * padded FFT grid, Newell octant, tensor and spectrum do not fit returns
  * MM_EINVAL with a message (mm_last_error(NULL)); for example 256x256x1 fits,
- * 512x512x1 does not.  The first call on a device looks the array's device
- * address up (cudaGetSymbolAddress): make it before any stream capture.  All
+ * 512x512x1 does not.  The first call in each CUDA context (with the
+ * runtime's primary contexts: the first call on each device) looks the
+ * array's device address up (cudaGetSymbolAddress) and remembers it under the
+ * context's unique id: make that first call before any stream capture.  All
  * calls share the array and it keeps the last call's contents, so calls that
  * overlap on the GPU race: serialise them.  The call synchronises the stream
  * once (after the tensor), then returns with the evaluation queued. */

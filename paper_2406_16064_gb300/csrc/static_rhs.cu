@@ -11,12 +11,17 @@
 // lives in one file-scope __device__ array of MM_STATIC_SCRATCH_BYTES.  Every
 // GPU that loads libmm holds that array until the process exits.
 //
-// The first call on a device looks up the array's device address with
+// The first call in each CUDA context (one per device for callers of the
+// runtime's primary contexts) looks up the array's device address with
 // cudaGetSymbolAddress (host code cannot use the symbol itself: in host code it
-// names a host-side shadow, not device memory); make that first call before any
-// stream capture.  All calls share the array and it keeps the last call's
-// contents, so calls that overlap on the GPU (different streams, or host
-// threads) race: serialise them.
+// names a host-side shadow, not device memory) and remembers it under that
+// context's unique id, so a call made in another context -- a context the
+// host application created and made current, or the new primary context
+// after cudaDeviceReset -- looks the address up again instead of reusing one
+// that belongs to a context that no longer applies.  Make that first call in a
+// context before any stream capture.  All calls share the array and it keeps
+// the last call's contents, so calls that overlap on the GPU (different
+// streams, or host threads) race: serialise them.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -31,7 +36,7 @@
 using namespace mm;
 
 #define MM_STATIC_SCRATCH_BYTES (32u << 20)   // 32 MiB
-#define MM_STATIC_MAX_DEVICES 64
+#define MM_STATIC_MAX_CONTEXTS 64              // remembered (context id, address) pairs
 
 static __device__ __align__(256) unsigned char g_static_scratch[MM_STATIC_SCRATCH_BYTES];
 
@@ -40,7 +45,67 @@ void mm_internal_set_error(const char* msg);   // api.cu
 namespace {
 
 std::mutex g_lock;
-void* g_base[MM_STATIC_MAX_DEVICES] = {};
+
+// The array's device address per CUDA context, keyed by the context's unique id
+// (cuCtxGetId: never reused within a process, unlike the context handle).
+struct CtxAddr {
+    unsigned long long id;
+    void* base;
+};
+CtxAddr g_addr[MM_STATIC_MAX_CONTEXTS];
+int g_naddr = 0;
+
+// Driver entry points for the current context's id, fetched through the runtime
+// (libmm does not link the driver library).  Signatures of cuCtxGetCurrent and
+// cuCtxGetId; CUresult 0 is success.
+typedef int (*CtxGetCurrentFn)(void** ctx);
+typedef int (*CtxGetIdFn)(void* ctx, unsigned long long* id);
+
+bool current_context_id(unsigned long long* id) {
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {
+        looked_up = true;
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = (CtxGetCurrentFn)f;
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = (CtxGetIdFn)f;
+        cudaGetLastError();
+    }
+    void* ctx = nullptr;
+    if (!get_current || !get_id || get_current(&ctx) != 0 || !ctx) return false;
+    return get_id(ctx, id) == 0;
+}
+
+// Device address of g_static_scratch in the current context (cudaGetSymbolAddress,
+// remembered per context id); nullptr on failure.  Call with g_lock held.
+void* scratch_base() {
+    unsigned long long id = 0;
+    const bool have_id = current_context_id(&id);
+    if (have_id)
+        for (int i = 0; i < g_naddr; ++i)
+            if (g_addr[i].id == id) return g_addr[i].base;
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (have_id) {
+        // a full table forgets its oldest entry; a forgotten context just looks up again
+        if (g_naddr == MM_STATIC_MAX_CONTEXTS) {
+            std::memmove(g_addr, g_addr + 1, (MM_STATIC_MAX_CONTEXTS - 1) * sizeof(CtxAddr));
+            --g_naddr;
+        }
+        g_addr[g_naddr++] = {id, p};
+    }
+    return p;
+}
 
 int err(int code, const char* msg) {
     mm_internal_set_error(msg);
@@ -74,16 +139,13 @@ extern "C" int mm_rhs_eval_static(const mm_mesh* mesh, const mm_material* mat, i
     const size_t e = f32 ? 4 : 8;
 
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MM_STATIC_MAX_DEVICES)
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
         return err(MM_ECUDA, "mm_rhs_eval_static: no current CUDA device");
-    std::lock_guard<std::mutex> guard(g_lock);
-    if (!g_base[dev]) {
-        void* p = nullptr;
-        const cudaError_t rc = cudaGetSymbolAddress(&p, g_static_scratch);
-        if (rc != cudaSuccess || !p) return err(MM_ECUDA, "mm_rhs_eval_static: cudaGetSymbolAddress failed");
-        g_base[dev] = p;
     }
-    unsigned char* base = (unsigned char*)g_base[dev];
+    std::lock_guard<std::mutex> guard(g_lock);
+    unsigned char* base = (unsigned char*)scratch_base();
+    if (!base) return err(MM_ECUDA, "mm_rhs_eval_static: cudaGetSymbolAddress failed");
 
     // descriptor of the single simulation (same layout rules as a context: plan.h)
     SimDesc d;
@@ -93,8 +155,11 @@ extern "C" int mm_rhs_eval_static(const mm_mesh* mesh, const mm_material* mat, i
     if (n > (1LL << 26)) return err(MM_EINVAL, "mm_rhs_eval_static: mesh too large for the static scratch");
     d.ncells = (int)n;
     const int lim = f32 ? 8192 : 4096;
-    if (plan_pad_len(d.nx, true) > 8192 || plan_pad_len(d.ny, false) > lim || plan_pad_len(d.nz, false) > lim)
-        return err(MM_EINVAL, "mm_rhs_eval_static: padded FFT too long");
+    if (plan_pad_len(d.nx, true) > lim || plan_pad_len(d.ny, false) > lim || plan_pad_len(d.nz, false) > lim)
+        return err(MM_EINVAL, f32 ? "mm_rhs_eval_static: padded FFT length too large (max 8192 along each axis in "
+                                    "this precision)"
+                                  : "mm_rhs_eval_static: padded FFT length too large (max 4096 along each axis in "
+                                    "this precision)");
     plan_geometry(d, f32);
     const double un = sqrt(mat->u[0] * mat->u[0] + mat->u[1] * mat->u[1] + mat->u[2] * mat->u[2]);
     if (mat->Ku != 0.0 && !(un > 0)) return err(MM_EINVAL, "mm_rhs_eval_static: anisotropy axis is zero");
