@@ -1261,6 +1261,8 @@ int mm_profile_attempts(mm_ctx* C, int reps, double* ms, long long* counts) {
 }
 
 int mm_debug_bounded_wait(mm_ctx* C, long long spins) {
+    if (spins < 0 || spins > MM_MAX_WAIT_SPINS)
+        return fail(C, MM_EINVAL, "mm_debug_bounded_wait: spins must be in [0, %lld]", (long long)MM_MAX_WAIT_SPINS);
     int rc = check_ready(C);
     if (rc) return rc;
     CK(cudaMemsetAsync(C->flag_d, 0, 16, C->stream));

@@ -58,3 +58,13 @@ def test_struct_layouts_match_the_header(libpath):
     assert ctypes.sizeof(mm.mm_status) == 4 * 8 + 2 * 8 + 2 * 4
     # t h t_end rtol max_dmdt (40) + two counters (16) + status, pad (8)
     assert ctypes.sizeof(mm.mm_checkpoint) == 5 * 8 + 2 * 8 + 2 * 4
+
+
+def test_bounded_wait_rejects_spins_beyond_the_limit(libpath):
+    """The range check runs before anything else, so it needs neither a context nor a GPU."""
+    import ctypes
+    from paper_2406_16064_gb300 import mm
+    L = mm.lib()
+    for spins in (-1, (1 << 22) + 1, 1 << 62):
+        assert L.mm_debug_bounded_wait(None, ctypes.c_longlong(spins)) == mm.MM_EINVAL
+        assert b"spins must be in [0, 4194304]" in L.mm_last_error(None)
