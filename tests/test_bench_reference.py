@@ -16,6 +16,9 @@ def test_reference_arm_runs_exactly_the_requested_steps():
     assert line["value"] > 0 and line["cpu_baseline"]["kind"] == "oracle"
     assert line["cpu_baseline"]["value"] == line["value"] == line["e2e"]["value"]
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
+    # one oracle process per host core (fewer only when memory is short)
+    assert 1 <= line["cpu_baseline"]["cores"] <= bench.host_cores()
+    assert line["cpu_baseline"]["cores"] == bench.oracle_workers(bench.workload("film_relax_32").sims[0])
     assert bench.run_reference(args, 1, 2) is None          # other ranks do no work
 
 

@@ -49,3 +49,7 @@ def test_algorithmic_bytes_of_the_film_by_hand():
     assert kb["x_forward"] == sum(3 * e * n * s + (3 * e * n if s > 1 else 0) + (3 * e * n if s == 7 else 0)
                                   for s in range(1, 8)) + 7 * rows
     assert kb["project"] == 6 * e * n and not kb["z_fused"] and not kb["y_fused"]
+    alg = bench.kernel_bytes(w, e, spectrum=False)
+    assert alg["yz_cluster"] / 7 == tens
+    assert alg["x_inverse_epilogue"] == 7 * 6 * e * n + 3 * e * n
+    assert kb["x_forward"] - alg["x_forward"] == 7 * rows
