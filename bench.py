@@ -26,6 +26,11 @@ two schemes (error against the closed form at 1 ns over a range of h).
 `--ext` adds per-cell exchange and DMI constants and a Zhang-Li drift to the
 workload, so the extended x-inverse variant runs (workload name `*_ext`).
 
+`--driver cufft-compare` times the zero-padded demag convolution done with cuFFT
+(torch.fft, three R2C + product + three C2R on the padded grid) against this
+library's whole right-hand side on the workload's first simulation (a timed
+comparison only; cuFFT is never on the product path).
+
 `--workload sweep` times the N x N x 1 family of the paper's throughput
 comparison (demag + exchange + Zeeman, N = 128 ... 4096, FP32) and reports each
 N as RHS cell-updates/s and as Heun-equivalent cells/s (RHS rate / 2).
@@ -410,10 +415,21 @@ def timed_attempts(ctx, torch, stream, k):
     return start.elapsed_time(end)
 
 
-def setup_ctx(mm, w, precision, stream, rtol):
+def setup_ctx(mm, w, precision, stream, rtol, tune=False, info=None):
+    """A context with the workload's simulations, state and RK45 settings.  tune: give
+    every mesh its autotuned tiles (cached per GPU, build, precision and mesh), recording
+    the choices in `info`."""
     ctx = mm.Context(precision, stream=stream.cuda_stream)
     for s in w.sims:
         ctx.add_sim(s.mesh, s.mat, s.Ms_cells)
+    if tune:
+        import torch
+        from paper_2406_16064_gb300 import tuning
+        t0 = time.perf_counter()
+        got = tuning.tune_context(ctx, [s.mesh for s in w.sims], torch.cuda.get_device_name(), reps=8)
+        if info is not None:
+            info["tuning"] = {k.split("|", 2)[2]: v for k, v in got.items()}
+            info["tuning_seconds"] = time.perf_counter() - t0
     ctx.precompute()
     ctx.set_m(np.concatenate([s.m0.ravel() for s in w.sims]))
     if w.neb:
@@ -486,7 +502,8 @@ def run_gpu(args, rank, world, dist):
     w.precision = prec
     e = 8 if prec == "f64" else 4
     ncell = cells(w)
-    ctx = setup_ctx(mm, w, prec, stream, w.rtol)
+    tinfo = {}
+    ctx = setup_ctx(mm, w, prec, stream, w.rtol, tune=not args.no_autotune, info=tinfo)
     ctx.rk45_attempts(args.warmup)
     torch.cuda.synchronize()
     n0 = ctx.launches()
@@ -527,10 +544,11 @@ def run_gpu(args, rank, world, dist):
     dom = max((k for k in rows if kb.get(k)), key=lambda k: rows[k]["ms_per_attempt"])
     launches_dom = prof[dom][1] / reps
     avg_launch_ms = prof[dom][0] / prof[dom][1]
-    bytes_per_launch = kb_alg[dom] / launches_dom
+    alg_per_launch = kb_alg[dom] / launches_dom
     spectrum_per_launch = (kb[dom] - kb_alg[dom]) / launches_dom
+    bytes_per_launch = alg_per_launch + spectrum_per_launch
     achieved = bytes_per_launch / (avg_launch_ms / 1e3) / 1e9
-    achieved_sp = (bytes_per_launch + spectrum_per_launch) / (avg_launch_ms / 1e3) / 1e9
+    achieved_alg = alg_per_launch / (avg_launch_ms / 1e3) / 1e9
     step_ms = ms_max / args.steps
     step_bytes = step_bytes_whole(w, e)
     # end to end through the C ABI with host buffers: H2D of m, one attempt, D2H of m
@@ -556,15 +574,17 @@ def run_gpu(args, rank, world, dist):
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm if achieved else None, "peak_kind": f"of {peak_kind}",
                      "bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_launch_ms,
-                     "bytes_meaning": "algorithmic: state, stage vectors and tensor of the launch; the demag "
-                                      "spectrum written and read between passes is implementation traffic, "
-                                      "reported separately",
+                     "bytes_meaning": "compulsory bytes of the launch: state, stage vectors and tensor (the "
+                                      "algorithmic bytes) plus the demag spectrum it reads and writes between "
+                                      "passes (implementation traffic), each given below",
+                     "algorithmic_bytes_per_launch": alg_per_launch,
                      "spectrum_bytes_per_launch": spectrum_per_launch,
-                     "achieved_with_spectrum": achieved_sp, "frac_with_spectrum": achieved_sp / hbm,
+                     "achieved_algorithmic": achieved_alg, "frac_algorithmic": achieved_alg / hbm,
                      "traffic": recorded_traffic(dom, w.name), "source_fingerprint": source_fingerprint(),
                      "step_algorithmic_gbs": step_bytes / (step_ms / 1e3) / 1e9,
                      "step_frac": step_bytes / (step_ms / 1e3) / 1e9 / hbm},
         "kernels": rows,
+        "autotune": tinfo or None,
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 3 * ncell * e,
                 "d2h_bytes_per_step": 3 * ncell * e, "steps": ke},
@@ -576,11 +596,16 @@ def run_gpu(args, rank, world, dist):
         w64 = workload(args.workload, world)
         w64.sims = w.sims
         w64.precision = "f64"
-        ctx64 = setup_ctx(mm, w64, "f64", stream, 1e-6)
+        t64 = {}
+        ctx64 = setup_ctx(mm, w64, "f64", stream, 1e-6, tune=not args.no_autotune, info=t64)
         ctx64.rk45_attempts(max(1, args.warmup // 4))
         k64 = max(3, min(args.steps, 100))
         ms64 = timed_attempts(ctx64, torch, stream, k64)
-        line["f64"] = {"value": (ncell_job / ncell) * ncell * 7 * k64 / (ms64 / 1e3), "ms_per_step": ms64 / k64, "steps": k64}
+        v64 = (ncell_job / ncell) * ncell * 7 * k64 / (ms64 / 1e3)
+        line["f64"] = {"value": v64, "ms_per_step": ms64 / k64, "steps": k64,
+                       "step_algorithmic_gbs": step_bytes_whole(w, 8) / (ms64 / k64 / 1e3) / 1e9,
+                       "step_frac": step_bytes_whole(w, 8) / (ms64 / k64 / 1e3) / 1e9 / hbm,
+                       "autotune": t64 or None}
         ctx64.close()
     if rank == 0 and not args.no_cpu:
         v, P, n, dt, mesh = oracle_rate(w, 12.0)
@@ -716,6 +741,74 @@ def run_cayley_error(args, rank, world, dist):
             "value": rows[2]["cayley"], "rows": rows, "order_coarsest": order}
 
 
+def run_cufft_compare(args, rank, world, dist):
+    """Timed comparison with cuFFT (through torch.fft), never on the product path: the
+    zero-padded demag convolution of the workload's first simulation done the library
+    way -- three 3-D R2C transforms of M on the padded grid, the symmetric tensor product
+    per bin, three C2R transforms, crop -- against this library's whole right-hand side
+    (mm_rhs_eval: its transforms skip the zero padding, the product is fused into the
+    innermost transform, and the exchange / DMI / anisotropy / Zeeman / torque epilogue
+    is included).  The cuFFT tensor spectrum is random (timing only)."""
+    import torch
+    from paper_2406_16064_gb300 import mm
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    w = workload(args.workload, world)
+    prec = args.precision or "f32"
+    s = w.sims[0]
+    nx, ny, nz = s.mesh.nx, s.mesh.ny, s.mesh.nz
+    P = (pad(nz), pad(ny), pad(nx, True))
+    rdt = torch.float32 if prec == "f32" else torch.float64
+    cdt = torch.complex64 if prec == "f32" else torch.complex128
+    dev = "cuda"
+    M = torch.tensor(s.m0 * s.mat.Ms, dtype=rdt, device=dev)
+    g = torch.Generator(device=dev).manual_seed(0)
+    Nk = torch.randn((6, P[0], P[1], P[2] // 2 + 1), dtype=cdt, device=dev, generator=g)
+
+    def cufft_conv(fft_only=False):
+        Mk = torch.fft.rfftn(M, s=P, dim=(1, 2, 3))
+        if fft_only:
+            Hk = Mk
+        else:
+            xx, yy, zz, xy, xz, yz = Nk
+            Hk = torch.stack([xx * Mk[0] + xy * Mk[1] + xz * Mk[2],
+                              xy * Mk[0] + yy * Mk[1] + yz * Mk[2],
+                              xz * Mk[0] + yz * Mk[1] + zz * Mk[2]])
+        return torch.fft.irfftn(Hk, s=P, dim=(1, 2, 3))[:, :nz, :ny, :nx].contiguous()
+
+    def timed(fn, reps):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        st, en = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        st.record()
+        for _ in range(reps):
+            fn()
+        en.record()
+        en.synchronize()
+        return st.elapsed_time(en) / reps
+
+    reps = max(10, args.steps)
+    t_conv = timed(cufft_conv, reps)
+    t_fft = timed(lambda: cufft_conv(True), reps)
+    del Nk
+    torch.cuda.empty_cache()
+    stream = torch.cuda.current_stream()
+    ctx = mm.Context(prec, stream=stream.cuda_stream)
+    ctx.add_sim(s.mesh, s.mat, s.Ms_cells)
+    ctx.precompute()
+    mt = torch.tensor(s.m0.ravel(), dtype=rdt, device=dev)
+    kt, ht = torch.empty_like(mt), torch.empty_like(mt)
+    n0 = ctx.launches()
+    t_ours = timed(lambda: ctx.rhs_device(mt, kt, ht), reps)
+    launches = ctx.launches() - n0
+    ctx.close()
+    return {"metric": "demag convolution time per evaluation: cuFFT (torch.fft) vs this library's whole RHS",
+            "unit": "ms", "higher_is_better": False, "n_gpus": 1, "dtype": prec, "data": "synthetic",
+            "config": {"workload": w.name, "mesh": [nx, ny, nz], "padded_grid_zyx": list(P)},
+            "value": t_ours, "ours_rhs_ms": t_ours, "cufft_conv_ms": t_conv, "cufft_fft_only_ms": t_fft,
+            "ours_vs_cufft_conv": t_conv / t_ours, "gpu_launches": launches}
+
+
 def run_relax_compare(args, rank, world, dist):
     """Wall time to relax the workload from its start below --max-dmdt (rad/s): RK45
     (mm_relax, the workload's rtol) against steepest descent (mm_minimize)."""
@@ -770,8 +863,10 @@ def main():
     ap.add_argument("--sweep-n", default=None, help="comma-separated N for --workload sweep")
     ap.add_argument("--driver", default="rk45",
                     help="rk45 (default), sd (steepest-descent steps), relax-compare, rk4-cayley, "
-                         "rk4-proj or cayley-error")
+                         "rk4-proj, cayley-error or cufft-compare")
     ap.add_argument("--max-dmdt", type=float, default=1e7, help="relax-compare threshold, rad/s")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the fixed tile rules instead of the autotuned (cached) tiles")
     ap.add_argument("--ext", action="store_true",
                     help="add per-cell A and D and a Zhang-Li drift to the workload (extended epilogue)")
     args = ap.parse_args()
@@ -795,6 +890,8 @@ def main():
             line = run_cayley_error(args, rank, world, dist) if rank == 0 else None
         elif args.driver == "relax-compare":
             line = run_relax_compare(args, rank, world, dist) if rank == 0 else None
+        elif args.driver == "cufft-compare":
+            line = run_cufft_compare(args, rank, world, dist) if rank == 0 else None
         else:
             line = (run_sweep if args.workload == "sweep" else run_gpu)(args, rank, world, dist)
         if dist:

@@ -119,6 +119,41 @@ int mm_add_sim(mm_ctx *ctx, const mm_mesh *mesh, const mm_material *mat,
 int mm_batch_layout(const mm_ctx *ctx, long long *offsets, long long *total);
 int mm_num_sims(const mm_ctx *ctx);
 
+/* Tile shapes and schedules of one simulation's passes (an implementation
+ * choice: the paper's kernels use library FFTs and have no counterpart).
+ * 0 in a field keeps the library's fixed rule.
+ *   Ty          kx columns per spectrum block and column tile (power of two, 1..32)
+ *   Rx          rows per x-pass CTA (1..ny)
+ *   x_threads   threads per x-pass CTA (multiple of 32, <= 1024 FP32 / 512 FP64)
+ *   col_threads threads per column-pass CTA of meshes with one plane or more
+ *               than 8 planes (same limits)
+ *   col_group   cluster pass (2..8 planes): column FFT stages per register
+ *               group, 1 = 16-point groups, 2 = 32-point groups
+ * The two CTA widths act per launch, which covers the whole batch: they apply
+ * when every simulation of the context has the same value (else the rule). */
+typedef struct { int Ty, Rx, x_threads, col_threads, col_group; } mm_tuning;
+
+/* Set the tuning of one simulation (sim_id = -1: every simulation); must
+ * precede mm_precompute_demag.  MM_EINVAL if the tiles do not fit the kernels
+ * (shared memory, limits above). */
+int mm_set_tuning(mm_ctx *ctx, int sim_id, const mm_tuning *t);
+
+/* The tuning in use by one simulation, every field resolved (rule values
+ * filled in; col_group 0 for a simulation without the cluster pass). */
+int mm_get_tuning(const mm_ctx *ctx, int sim_id, mm_tuning *out);
+
+/* Autotune the geometry of simulation sim_id (before mm_precompute_demag):
+ * time candidate tunings -- kx block width and column register groups, then
+ * rows per x tile and x-pass CTA width, then column-pass CTA width, each
+ * phase starting from the best of the last, the fixed rule first -- as `reps`
+ * RK45 attempts each (CUDA events, after two untimed ones) in a scratch
+ * context of one simulation with the same mesh, material and per-cell
+ * constants on the same device, and set the fastest on every simulation of
+ * this context with the same mesh.  best (nullable) receives it resolved,
+ * best_ms / rule_ms (nullable) the milliseconds per attempt of the best and of
+ * the rule.  The scratch context allocates and frees device memory. */
+int mm_autotune(mm_ctx *ctx, int sim_id, int reps, mm_tuning *best, double *best_ms, double *rule_ms);
+
 /* Applied field of one simulation (field sweeps, Listing 2), A/m. */
 int mm_set_field(mm_ctx *ctx, int sim_id, const double H[3]);
 

@@ -40,6 +40,7 @@ struct SimHost {
     std::vector<double> AD;     // per-cell A then D (2 ncells), empty if uniform
     SimDesc d;
     int geom = -1;
+    Tuning tune;                // autotuned / caller-set tiles (0 = rule)
 };
 
 struct Geom {
@@ -154,6 +155,13 @@ Launch make_launch(mm_ctx* C, int sim) {
     L.smem_z = P.smem_z;
     L.smem_y2 = P.smem_y2;
     L.smem_yzc = P.smem_yzc;
+    // launch-wide CTA widths: the tuned value when every simulation has the same one
+    L.x_threads = C->sims.empty() ? 0 : C->sims[0].tune.x_threads;
+    L.col_threads = C->sims.empty() ? 0 : C->sims[0].tune.col_threads;
+    for (const SimHost& s : C->sims) {
+        if (s.tune.x_threads != L.x_threads) L.x_threads = 0;
+        if (s.tune.col_threads != L.col_threads) L.col_threads = 0;
+    }
     L.tensor = C->tens;
     L.Ms = C->Msd;
     L.cellp = C->cellp;
@@ -587,6 +595,152 @@ int mm_add_sim(mm_ctx* C, const mm_mesh* mesh, const mm_material* mat, const dou
 }
 
 int mm_num_sims(const mm_ctx* C) { return C ? (int)C->sims.size() : MM_EINVAL; }
+
+namespace {
+
+Tuning from_abi(const mm_tuning& t) {
+    Tuning u;
+    u.Ty = t.Ty; u.Rx = t.Rx; u.x_threads = t.x_threads; u.col_threads = t.col_threads; u.col_group = t.col_group;
+    return u;
+}
+
+// Plan sim s with tuning t (before finalisation); MM_EINVAL if its tiles do not fit.
+int apply_tuning(mm_ctx* C, SimHost& s, const Tuning& t) {
+    const bool f32 = C->precision == MM_F32;
+    if (t.Ty < 0 || t.Rx < 0 || t.x_threads < 0 || t.col_threads < 0 || t.col_group < 0 || t.col_group > 2)
+        return fail(C, MM_EINVAL, "mm_set_tuning: negative or unknown value");
+    if (t.Ty > 32 || (t.Ty & (t.Ty - 1))) return fail(C, MM_EINVAL, "mm_set_tuning: Ty must be a power of two <= 32");
+    SimDesc d = s.d;
+    plan_geometry(d, f32, t);
+    if (!plan_tuning_valid(d, 2 * C->esz, t, f32 ? 1024 : 512))
+        return fail(C, MM_EINVAL, "mm_set_tuning: tiles exceed the kernels' limits (Ty %d, Rx %d, threads %d / %d)",
+                    d.Ty, d.Rx, t.x_threads, t.col_threads);
+    s.d = d;
+    s.tune = t;
+    return MM_OK;
+}
+
+// The tuning of s with every rule value filled in.
+mm_tuning resolved_tuning(const mm_ctx* C, const SimHost& s) {
+    const bool f32 = C->precision == MM_F32;
+    const int maxth = f32 ? 1024 : 512;
+    PlanItems P;
+    SimDesc e = s.d;
+    e.flags |= F_DEMAG;
+    plan_items(e, 0, 2 * C->esz, P);
+    mm_tuning r;
+    r.Ty = s.d.Ty;
+    r.Rx = s.d.Rx;
+    r.x_threads = s.tune.x_threads ? s.tune.x_threads : plan_wide_threads(P.smem_x, maxth);
+    const size_t sc = std::max(P.smem_y13, std::max(P.smem_z, P.smem_y2));
+    r.col_threads = s.tune.col_threads ? s.tune.col_threads : (sc ? plan_wide_threads(sc, maxth) : 0);
+    r.col_group = plan_uses_yzc(s.d) ? (plan_yzc_list(s.d, f32) >= kYzcLists ? 2 : 1) : 0;
+    return r;
+}
+
+// Milliseconds per RK45 attempt of one simulation like s under tuning t, in a
+// scratch context on C's device (two untimed attempts, then `reps` timed).
+int time_tuning(mm_ctx* C, const SimHost& s, const Tuning& t, int reps, double* ms) {
+    mm_ctx* T = nullptr;
+    int rc = mm_create(&T, C->device, C->precision, nullptr);
+    if (rc) return fail(C, rc, "mm_autotune: scratch context: %s", g_last_error);
+    SimHost h = s;
+    h.d.group_begin = h.d.group_end = -1;
+    h.d.neb_index = -1;
+    T->sims.push_back(h);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    auto done = [&](int code) -> int {
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        if (code && code != MM_OK) { std::string m = T->err; mm_destroy(T); return fail(C, code, "mm_autotune: %s", m.c_str()); }
+        mm_destroy(T);
+        return MM_OK;
+    };
+    if ((rc = apply_tuning(T, T->sims[0], t))) return done(rc);
+    if ((rc = mm_precompute_demag(T))) return done(rc);
+    const long long n = 3LL * h.d.ncells, N = h.d.ncells;
+    std::vector<double> m(n);
+    for (long long i = 0; i < N; ++i) {          // a smooth unit-vector texture
+        const double a = 0.37 * (double)(i % 97), b = 0.11 * (double)(i % 89);
+        m[i] = std::cos(a) * std::sin(b + 0.3);
+        m[N + i] = std::sin(a) * std::sin(b + 0.3);
+        m[2 * N + i] = std::cos(b + 0.3);
+    }
+    if ((rc = mm_set_m(T, 0, m.data(), MM_HOST))) return done(rc);
+    if ((rc = mm_rk45_setup(T, 1e-5, 0.0, 0.0))) return done(rc);
+    if ((rc = launch_attempts(T, 2))) return done(rc);
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return done(MM_ECUDA);
+    cudaEventRecord(e0, T->stream);
+    if ((rc = launch_attempts(T, reps))) return done(rc);
+    cudaEventRecord(e1, T->stream);
+    if (cudaEventSynchronize(e1) != cudaSuccess) return done(MM_ECUDA);
+    float t_ms = 0.f;
+    cudaEventElapsedTime(&t_ms, e0, e1);
+    *ms = (double)t_ms / reps;
+    return done(MM_OK);
+}
+
+bool same_mesh(const mm_mesh& a, const mm_mesh& b) {
+    return a.nx == b.nx && a.ny == b.ny && a.nz == b.nz && a.dx == b.dx && a.dy == b.dy && a.dz == b.dz;
+}
+
+}  // namespace
+
+int mm_set_tuning(mm_ctx* C, int sim, const mm_tuning* t) {
+    if (!C || !t) return fail(C, MM_EINVAL, "NULL argument");
+    if (C->finalized) return fail(C, MM_EINVAL, "mm_set_tuning after mm_precompute_demag");
+    if (sim < -1 || sim >= (int)C->sims.size()) return fail(C, MM_EINVAL, "bad sim id");
+    for (int i = (sim < 0 ? 0 : sim); i < (sim < 0 ? (int)C->sims.size() : sim + 1); ++i) {
+        const int rc = apply_tuning(C, C->sims[i], from_abi(*t));
+        if (rc) return rc;
+    }
+    return MM_OK;
+}
+
+int mm_get_tuning(const mm_ctx* C, int sim, mm_tuning* out) {
+    if (!C || !out || sim < 0 || sim >= (int)C->sims.size()) return MM_EINVAL;
+    *out = resolved_tuning(C, C->sims[sim]);
+    return MM_OK;
+}
+
+int mm_autotune(mm_ctx* C, int sim, int reps, mm_tuning* best_out, double* best_ms, double* rule_ms) {
+    if (!C) return MM_EINVAL;
+    if (C->finalized) return fail(C, MM_EINVAL, "mm_autotune after mm_precompute_demag");
+    if (sim < 0 || sim >= (int)C->sims.size() || reps < 1) return fail(C, MM_EINVAL, "bad arguments");
+    const bool f32 = C->precision == MM_F32;
+    const SimHost& s = C->sims[sim];
+    SimDesc r = s.d;
+    plan_geometry(r, f32);                       // the rule
+    Tuning best;
+    best.Ty = r.Ty;
+    best.Rx = r.Rx;
+    best.col_group = (f32 && plan_uses_yzc(r)) ? (plan_yzc_list(r, f32) >= kYzcLists ? 2 : 1) : 0;
+    double tbest = 0.0, trule = 0.0;
+    bool first = true;
+    for (int phase = 0; phase < 3; ++phase) {
+        const std::vector<Tuning> cand = plan_tuning_candidates(r, f32, phase, best);
+        const Tuning fixed = best;
+        for (size_t i = 0; i < cand.size(); ++i) {
+            if (i == 0 && !first) continue;      // the phase's starting point was timed already
+            double ms = 0.0;
+            const int rc = time_tuning(C, s, cand[i], reps, &ms);
+            if (rc) return rc;
+            if (first) { trule = ms; tbest = ms; best = cand[i]; first = false; continue; }
+            if (ms < tbest) { tbest = ms; best = cand[i]; }
+        }
+        (void)fixed;
+    }
+    const mm_mesh mesh = s.mesh;
+    for (SimHost& o : C->sims)
+        if (same_mesh(o.mesh, mesh)) {
+            const int rc = apply_tuning(C, o, best);
+            if (rc) return rc;
+        }
+    if (best_out) *best_out = resolved_tuning(C, C->sims[sim]);
+    if (best_ms) *best_ms = tbest;
+    if (rule_ms) *rule_ms = trule;
+    return MM_OK;
+}
 
 int mm_batch_layout(const mm_ctx* C, long long* offsets, long long* total) {
     if (!C) return MM_EINVAL;

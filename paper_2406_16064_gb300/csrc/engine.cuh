@@ -42,6 +42,7 @@ struct Launch {
     ItemSet x, y13, z, y2;        // x rows, y fwd/inv (nz > 8), z fused, y fused (films)
     ItemSet yzc[18];              // cluster-fused y/z: list nz + 9 wide (plan_yzc_list)
     size_t smem_x = 0, smem_xi = 0, smem_y13 = 0, smem_z = 0, smem_y2 = 0, smem_yzc = 0;
+    int x_threads = 0, col_threads = 0;   // tuned CTA widths of the x and column passes (0: rule)
     const void* tensor = nullptr;
     const void* Ms = nullptr;
     const void* cellp = nullptr;  // per-cell A and D blocks

@@ -22,16 +22,13 @@ static PassParams<T> base_params(const Launch& L) {
     return p;
 }
 
-// Threads of an x- or column-pass CTA.  Long rows and columns need large
-// shared-memory tiles, which cap the CTAs resident on an SM (228 KB each); the
-// CTA then widens so the SM still holds about MM_XTHREADS_MAX<T> threads (32
-// warps FP32, 16 FP64, the register budget of those kernels' launch bounds).
+// Threads of an x- or column-pass CTA: the tuned width when the batch has one
+// (Launch::x_threads / col_threads), else the fixed rule (plan_wide_threads: 32
+// warps FP32, 16 FP64 per SM, the register budget of those kernels' launch bounds).
 template <typename T>
-static int wide_threads(size_t smem) {
-    int b = (int)(233472 / (smem + 1024));
-    if (b < 1) b = 1;
-    const int nt = 32 * ((MM_XTHREADS_MAX<T> / b) / 32);
-    return nt < MM_THREADS ? MM_THREADS : nt;
+static int wide_threads(size_t smem, int tuned = 0) {
+    if (tuned >= 32 && tuned <= MM_XTHREADS_MAX<T> && tuned % 32 == 0) return tuned;
+    return plan_wide_threads(smem, MM_XTHREADS_MAX<T>);
 }
 
 // The cluster kernel for nz planes (2..8) and the column group width.
@@ -54,7 +51,7 @@ static void issue_passes(const Launch& L, PassParams<T> p, const T* ys, bool inc
     cudaStream_t s = L.stream;
     ProfileHook* hk = L.hook;
     p.items = L.x.dev;
-    const int ntx = wide_threads<T>(L.smem_x), ntxi = wide_threads<T>(L.smem_xi + 2048);
+    const int ntx = wide_threads<T>(L.smem_x, L.x_threads), ntxi = wide_threads<T>(L.smem_xi + 2048, L.x_threads);
     switch ((p.mode == MODE_RK || p.mode == MODE_NEB) ? p.stage : 0) {
         case 2: k_xfwd<T, 2><<<L.x.count, ntx, L.smem_x, s>>>(p); break;
         case 3: k_xfwd<T, 3><<<L.x.count, ntx, L.smem_x, s>>>(p); break;
@@ -68,19 +65,19 @@ static void issue_passes(const Launch& L, PassParams<T> p, const T* ys, bool inc
     long long n = 1;
     if (L.y13.count) {
         p.items = L.y13.dev;
-        k_ycol<T, 0><<<L.y13.count, wide_threads<T>(L.smem_y13), L.smem_y13, s>>>(p);
+        k_ycol<T, 0><<<L.y13.count, wide_threads<T>(L.smem_y13, L.col_threads), L.smem_y13, s>>>(p);
         if (hk) hk->mark(KIND_YFWD);
         ++n;
     }
     if (L.z.count) {
         p.items = L.z.dev;
-        k_zcol<T><<<L.z.count, wide_threads<T>(L.smem_z), L.smem_z, s>>>(p);
+        k_zcol<T><<<L.z.count, wide_threads<T>(L.smem_z, L.col_threads), L.smem_z, s>>>(p);
         if (hk) hk->mark(KIND_ZCOL);
         ++n;
     }
     if (L.y13.count) {
         p.items = L.y13.dev;
-        k_ycol<T, 1><<<L.y13.count, wide_threads<T>(L.smem_y13), L.smem_y13, s>>>(p);
+        k_ycol<T, 1><<<L.y13.count, wide_threads<T>(L.smem_y13, L.col_threads), L.smem_y13, s>>>(p);
         if (hk) hk->mark(KIND_YINV);
         ++n;
     }
@@ -108,7 +105,7 @@ static void issue_passes(const Launch& L, PassParams<T> p, const T* ys, bool inc
     }
     if (L.y2.count) {
         p.items = L.y2.dev;
-        k_ycol<T, 2><<<L.y2.count, wide_threads<T>(L.smem_y2), L.smem_y2, s>>>(p);
+        k_ycol<T, 2><<<L.y2.count, wide_threads<T>(L.smem_y2, L.col_threads), L.smem_y2, s>>>(p);
         if (hk) hk->mark(KIND_YFUSED);
         ++n;
     }

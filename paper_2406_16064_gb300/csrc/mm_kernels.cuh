@@ -29,6 +29,17 @@
 template <typename T>
 constexpr int MM_XTHREADS_MAX = sizeof(T) == 4 ? 1024 : 512;
 
+// Threads of an x- or column-pass CTA by the fixed rule.  Long rows and columns
+// need large shared-memory tiles, which cap the CTAs resident on an SM (228 KB
+// each); the CTA then widens so the SM still holds about `maxthreads` threads
+// (the launch bound of those kernels).
+inline int plan_wide_threads(size_t smem, int maxthreads) {
+    int b = (int)(233472 / (smem + 1024));
+    if (b < 1) b = 1;
+    const int nt = 32 * ((maxthreads / b) / 32);
+    return nt < MM_THREADS ? MM_THREADS : nt;
+}
+
 // F_DMI: interfacial DMI with D != 0; F_EX / F_UNI / F_CUB: A, Ku, Kc != 0.
 // F_EXT: the simulation has extended terms (bulk or D_2d DMI, per-cell A / D,
 // spin torques; SimDesc::eflags), evaluated by the extended x-inverse kernel;
@@ -81,7 +92,7 @@ struct SimDesc {
     int NBx;                 // number of kx blocks, ceil(Kx / Ty)
     int group_begin, group_end;   // NEB chain members [begin, end), -1 if none
     int neb_index;                // image index in its chain
-    int pad0;
+    int colgroup;                 // cluster-pass column register groups: 0 rule, 1 16-point, 2 32-point
     long long off;           // element offset of the [3][N] state block
     long long spec_off;      // complex offset of the spectrum block
     long long ms_off;        // offset into the per-cell Ms array, -1 if uniform

@@ -33,11 +33,23 @@ inline int plan_pad_len(int n, bool min2) {
 // Largest plane count handled by the cluster-fused y/z pass (portable cluster size).
 constexpr int kMaxClusterPlanes = 8;
 
-// Fill the padded sizes, tensor bins and tile shapes of d from d.nx, d.ny, d.nz.
+// Tile shapes and schedules an autotuner may set per simulation; 0 keeps the
+// fixed rule of plan_geometry / plan_yzc_list / plan_wide_threads.
+//   Ty          kx block width (power of two, 1..32)
+//   Rx          rows per x-pass CTA (1..ny)
+//   x_threads   threads of an x-pass CTA (multiple of 32; launch-wide)
+//   col_threads threads of a column-pass CTA outside the cluster pass (launch-wide)
+//   col_group   cluster-pass column register groups: 1 16-point, 2 32-point
+struct Tuning {
+    int Ty = 0, Rx = 0, x_threads = 0, col_threads = 0, col_group = 0;
+};
+
+// Fill the padded sizes, tensor bins and tile shapes of d from d.nx, d.ny, d.nz
+// (the rule, unless the tuning t sets a value).
 //   Rx : rows per x-pass CTA, 3 * Rx * padded_len(Kx) <= 4096 complex values per
 //        buffer (two buffers), Rx <= ny; tiles never cross a plane
 //   Ty : kx block width (power of two, <= 32): Py * Ty <= 4096 (FP32) / 2048 (FP64)
-inline void plan_geometry(SimDesc& d, bool f32) {
+inline void plan_geometry(SimDesc& d, bool f32, const Tuning& t = Tuning()) {
     d.Px = plan_pad_len(d.nx, true);
     d.Py = plan_pad_len(d.ny, false);
     d.Pz = plan_pad_len(d.nz, false);
@@ -56,8 +68,11 @@ inline void plan_geometry(SimDesc& d, bool f32) {
     const int EB = f32 ? 4096 : 2048;
     const int kcap = std::min(32, std::max(1, plan_pow2floor(std::max(1, d.Kx / 8))));
     d.Ty = std::min(kcap, plan_pow2floor(std::max(1, EB / d.Py)));
+    if (t.Rx > 0) d.Rx = std::min(t.Rx, d.ny);
+    if (t.Ty > 0) d.Ty = plan_pow2floor(std::min(t.Ty, 32));
     d.lTy = plan_ilog2(d.Ty);
     d.NBx = (d.Kx + d.Ty - 1) >> d.lTy;
+    d.colgroup = (t.col_group == 1 || t.col_group == 2) ? t.col_group : 0;
 }
 
 template <typename T>
@@ -144,7 +159,7 @@ inline bool plan_uses_yzc(const SimDesc& d) { return d.Pz > 1 && d.Py > 1 && d.n
 // measured faster as (4,3,3) than as (5,5)).
 constexpr int kYzcLists = kMaxClusterPlanes + 1;
 inline int plan_yzc_list(const SimDesc& d, bool f32) {
-    const bool wide = f32 && (d.lPy == 5 || d.lPy == 9 || d.lPy == 13);
+    const bool wide = d.colgroup ? d.colgroup == 2 : f32 && (d.lPy == 5 || d.lPy == 9 || d.lPy == 13);
     return d.nz + kYzcLists * (wide ? 1 : 0);
 }
 
@@ -196,6 +211,95 @@ inline void plan_items(const SimDesc& d, int sid, size_t vsz, PlanItems& P) {
         for (int b = 0; b < d.NBx; ++b) P.y2.push_back({sid, 0, b, -1});
         P.smem_y2 = std::max(P.smem_y2, 3 * (size_t)d.Py * d.Ty * vsz);
     }
+}
+
+}  // namespace mm
+
+namespace mm {
+
+// A planned simulation's tiles fit the kernels: Ty a power of two up to 32, at
+// least one row per x tile, every pass's shared memory within one CTA's, and
+// tuned CTA widths multiples of 32 up to maxthreads (the x and column kernels'
+// launch bound).  vsz = bytes of one complex value.
+inline bool plan_tuning_valid(const SimDesc& d, size_t vsz, const Tuning& t, int maxthreads) {
+    if (d.Ty < 1 || d.Ty > 32 || (d.Ty & (d.Ty - 1)) || d.Rx < 1 || d.Rx > d.ny) return false;
+    for (int th : {t.x_threads, t.col_threads})
+        if (th != 0 && (th < 32 || th > maxthreads || th % 32)) return false;
+    PlanItems P;
+    SimDesc e = d;
+    e.flags |= F_DEMAG;
+    plan_items(e, 0, vsz, P);
+    const size_t cap = 227 * 1024;
+    return P.smem_x <= cap - 4096 && P.smem_xi <= cap - 4096 && P.smem_y13 <= cap && P.smem_y2 <= cap &&
+           P.smem_z <= cap && P.smem_yzc <= cap;
+}
+
+// Candidates of one autotuning phase for the geometry of d0 (planned by the rule):
+//   phase 0  kx block width Ty in {rule/2, rule, 2 rule} (at most the next power of
+//            two above Kx) x, for FP32 cluster-pass films, both column group widths;
+//   phase 1  with `fixed`'s Ty and groups: rows per x tile in {rule/2, rule, 2 rule}
+//            x x-pass CTA width in {rule, 2 rule};
+//   phase 2  with `fixed`'s other values: column-pass CTA width in {rule, 2 rule}
+//            (meshes with column passes outside the cluster pass only).
+// Every candidate passes plan_tuning_valid; the first is `fixed` itself.
+inline std::vector<Tuning> plan_tuning_candidates(const SimDesc& d0, bool f32, int phase, const Tuning& fixed) {
+    const size_t vsz = f32 ? 8 : 16;
+    const int maxthreads = f32 ? 1024 : 512;
+    std::vector<Tuning> out;
+    auto add = [&](Tuning t) {
+        SimDesc d = d0;
+        plan_geometry(d, f32, t);
+        if (!plan_tuning_valid(d, vsz, t, maxthreads)) return;
+        for (const Tuning& u : out)
+            if (u.Ty == t.Ty && u.Rx == t.Rx && u.x_threads == t.x_threads && u.col_threads == t.col_threads &&
+                u.col_group == t.col_group)
+                return;
+        out.push_back(t);
+    };
+    add(fixed);
+    SimDesc r = d0;
+    plan_geometry(r, f32, fixed);
+    if (phase == 0) {
+        const int tymax = std::min(32, 1 << plan_ilog2(std::max(1, r.Kx)));
+        const bool groups = f32 && plan_uses_yzc(r);
+        const int g0 = plan_yzc_list(r, f32) >= kYzcLists ? 2 : 1;
+        for (int ty : {r.Ty / 2, r.Ty, 2 * r.Ty}) {
+            if (ty < 1 || ty > tymax) continue;
+            for (int g : {g0, 3 - g0}) {
+                if (!groups && g != g0) continue;
+                Tuning t = fixed;
+                t.Ty = ty;
+                t.col_group = groups ? g : 0;
+                add(t);
+            }
+        }
+    } else if (phase == 1) {
+        PlanItems P;
+        SimDesc e = r;
+        e.flags |= F_DEMAG;
+        plan_items(e, 0, vsz, P);
+        const int nt0 = plan_wide_threads(P.smem_x, maxthreads);
+        for (int rx : {r.Rx / 2, r.Rx, 2 * r.Rx})
+            for (int nt : {0, 2 * nt0}) {
+                if (rx < 1) continue;
+                Tuning t = fixed;
+                t.Rx = rx;
+                t.x_threads = nt;
+                add(t);
+            }
+    } else if (phase == 2) {
+        PlanItems P;
+        SimDesc e = r;
+        e.flags |= F_DEMAG;
+        plan_items(e, 0, vsz, P);
+        const size_t sc = std::max(P.smem_y13, std::max(P.smem_z, P.smem_y2));
+        if (sc > 0) {
+            Tuning t = fixed;
+            t.col_threads = 2 * plan_wide_threads(sc, maxthreads);
+            add(t);
+        }
+    }
+    return out;
 }
 
 }  // namespace mm

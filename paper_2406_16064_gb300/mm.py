@@ -45,6 +45,13 @@ class mm_status(C.Structure):
                 ("pad", C.c_int)]
 
 
+class mm_tuning(C.Structure):
+    _fields_ = [("Ty", C.c_int), ("Rx", C.c_int), ("x_threads", C.c_int), ("col_threads", C.c_int),
+                ("col_group", C.c_int)]
+
+
+TUNING_FIELDS = ("Ty", "Rx", "x_threads", "col_threads", "col_group")
+
 _P = C.c_void_p
 _D = C.POINTER(C.c_double)
 SIGNATURES = {
@@ -83,6 +90,9 @@ SIGNATURES = {
     "mm_debug_bounded_wait": (C.c_int, [_P, C.c_longlong]),
     "mm_kernel_launches": (C.c_longlong, [_P]),
     "mm_rhs_eval_static": (C.c_int, [C.POINTER(mm_mesh), C.POINTER(mm_material), C.c_int, _P, _P, _P, _P]),
+    "mm_set_tuning": (C.c_int, [_P, C.c_int, C.POINTER(mm_tuning)]),
+    "mm_get_tuning": (C.c_int, [_P, C.c_int, C.POINTER(mm_tuning)]),
+    "mm_autotune": (C.c_int, [_P, C.c_int, C.c_int, C.POINTER(mm_tuning), _D, _D]),
 }
 
 _lib = None
@@ -189,6 +199,24 @@ class Context:
 
     def precompute(self):
         self._check(self.L.mm_precompute_demag(self.h))
+
+    # ---- tile shapes and schedules (mm_tuning; 0 = the library's rule)
+    def set_tuning(self, sim, tuning):
+        t = mm_tuning(*(int(tuning.get(k, 0)) for k in TUNING_FIELDS))
+        self._check(self.L.mm_set_tuning(self.h, sim, C.byref(t)))
+
+    def get_tuning(self, sim):
+        t = mm_tuning()
+        self._check(self.L.mm_get_tuning(self.h, sim, C.byref(t)))
+        return {k: getattr(t, k) for k in TUNING_FIELDS}
+
+    def autotune(self, sim, reps=8):
+        """Time candidate tunings of sim's mesh (mm_autotune) and set the fastest on every
+        simulation with that mesh; returns (tuning, ms per attempt, rule ms per attempt)."""
+        t = mm_tuning()
+        best, rule = C.c_double(), C.c_double()
+        self._check(self.L.mm_autotune(self.h, sim, reps, C.byref(t), C.byref(best), C.byref(rule)))
+        return {k: getattr(t, k) for k in TUNING_FIELDS}, best.value, rule.value
 
     def layout(self):
         n = len(self.sims)

@@ -41,7 +41,29 @@ int main() {
         std::vector<WorkItem> all;
         for (int li = 0; li < 2 * kYzcLists; ++li) all.insert(all.end(), P.yzc[li].begin(), P.yzc[li].end());
         print_items("yzc_items", all);
-        printf("}\n");
+        // autotuner candidates of each phase, starting from the rule
+        Tuning fixed;
+        fixed.Ty = d.Ty;
+        fixed.Rx = d.Rx;
+        fixed.col_group = (f32 && plan_uses_yzc(d)) ? (plan_yzc_list(d, true) >= kYzcLists ? 2 : 1) : 0;
+        printf(", \"cands\": [");
+        for (int ph = 0; ph < 3; ++ph) {
+            const std::vector<Tuning> c = plan_tuning_candidates(d, f32 != 0, ph, fixed);
+            printf("%s[", ph ? "," : "");
+            for (size_t i = 0; i < c.size(); ++i) {
+                SimDesc e = d;
+                plan_geometry(e, f32 != 0, c[i]);
+                PlanItems Q;
+                plan_items(e, 0, vsz, Q);
+                printf("%s{\"Ty\": %d, \"Rx\": %d, \"xt\": %d, \"ct\": %d, \"g\": %d, \"pTy\": %d, \"pRx\": %d, "
+                       "\"smem\": [%zu,%zu,%zu,%zu,%zu,%zu], \"list\": %d}",
+                       i ? "," : "", c[i].Ty, c[i].Rx, c[i].x_threads, c[i].col_threads, c[i].col_group, e.Ty, e.Rx,
+                       Q.smem_x, Q.smem_xi, Q.smem_y13, Q.smem_z, Q.smem_y2, Q.smem_yzc,
+                       plan_uses_yzc(e) ? plan_yzc_list(e, f32 != 0) : -1);
+            }
+            printf("]");
+        }
+        printf("]}\n");
     }
     // term flags: (dmi kind, D, A, cells, A cells any, D cells any, u_x, aJ)
     const double cases[][8] = {

@@ -124,3 +124,39 @@ def test_term_flags(probe):
         assert r["flags"] == want, r
         want_e = (E_CELL if cells else 0) | (E_STT if ux != 0 else 0) | (E_SOT if aJ != 0 else 0)
         assert r["eflags"] == want_e, r
+
+
+def test_autotuner_candidates(probe):
+    """Every candidate of every phase fits the kernels (power-of-two Ty <= 32 and at most
+    the next power of two above Kx, 1 <= Rx <= ny, shared memory within a CTA's, CTA
+    widths multiples of 32 up to the launch bound); the first candidate of each phase is
+    its starting point (the rule in phase 0); the column group width only varies for FP32
+    cluster-pass films, and selects the 32-point list when it is 2."""
+    meshes, _ = probe
+    cap = 227 * 1024
+    for r in meshes:
+        ph0, ph1, ph2 = r["cands"]
+        if max(r["smem"][:2]) > cap - 4096:          # the mesh itself is refused (mm_add_sim)
+            assert not ph0
+            continue
+        assert ph0 and ph1 and ph2
+        assert (ph0[0]["pTy"], ph0[0]["pRx"]) == (r["Ty"], r["Rx"])
+        maxth = 1024 if r["f32"] else 512
+        kx2 = 1
+        while kx2 < r["Kx"]:
+            kx2 *= 2
+        for c in ph0 + ph1 + ph2:
+            Ty, Rx = c["pTy"], c["pRx"]
+            assert Ty & (Ty - 1) == 0 and 1 <= Ty <= min(32, max(kx2, r["Ty"]))
+            assert 1 <= Rx <= r["mesh"][1]
+            sx, sxi, sy13, sz, sy2, syzc = c["smem"]
+            assert max(sx, sxi) <= cap - 4096 and max(sy13, sz, sy2, syzc) <= cap
+            for th in (c["xt"], c["ct"]):
+                assert th == 0 or (th % 32 == 0 and 32 <= th <= maxth)
+            if c["g"]:
+                assert r["f32"] and r["yzc"] and c["list"] == r["mesh"][2] + 9 * (c["g"] - 1)
+        if not (r["f32"] and r["yzc"]):
+            assert all(c["g"] == 0 for c in ph0)
+        # phase 1 starts from phase 0's start, phase 2 from phase 1's
+        assert (ph1[0]["Ty"], ph1[0]["g"]) == (ph0[0]["Ty"], ph0[0]["g"])
+        assert (ph2[0]["Rx"], ph2[0]["xt"]) == (ph1[0]["Rx"], ph1[0]["xt"])
