@@ -792,7 +792,8 @@ def run_cufft_compare(args, rank, world, dist):
     t_fft = timed(lambda: cufft_conv(True), reps)
     del Nk
     torch.cuda.empty_cache()
-    stream = torch.cuda.current_stream()
+    stream = torch.cuda.Stream()                 # a real stream: the context launches on it
+    torch.cuda.set_stream(stream)
     ctx = mm.Context(prec, stream=stream.cuda_stream)
     ctx.add_sim(s.mesh, s.mat, s.Ms_cells)
     ctx.precompute()

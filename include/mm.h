@@ -129,9 +129,12 @@ int mm_num_sims(const mm_ctx *ctx);
  *               than 8 planes (same limits)
  *   col_group   cluster pass (2..8 planes): column FFT stages per register
  *               group, 1 = 16-point groups, 2 = 32-point groups
+ *   col_occ     cluster pass: CTAs per SM its kernel is built for, 3 (FP32 up
+ *               to 4 planes, column tiles small enough for three CTAs' shared
+ *               memory; fewer registers a thread) or 0 / 2 (the rule)
  * The two CTA widths act per launch, which covers the whole batch: they apply
  * when every simulation of the context has the same value (else the rule). */
-typedef struct { int Ty, Rx, x_threads, col_threads, col_group; } mm_tuning;
+typedef struct { int Ty, Rx, x_threads, col_threads, col_group, col_occ; } mm_tuning;
 
 /* Set the tuning of one simulation (sim_id = -1: every simulation); must
  * precede mm_precompute_demag.  MM_EINVAL if the tiles do not fit the kernels
@@ -142,16 +145,18 @@ int mm_set_tuning(mm_ctx *ctx, int sim_id, const mm_tuning *t);
  * filled in; col_group 0 for a simulation without the cluster pass). */
 int mm_get_tuning(const mm_ctx *ctx, int sim_id, mm_tuning *out);
 
-/* Autotune the geometry of simulation sim_id (before mm_precompute_demag):
- * time candidate tunings -- kx block width and column register groups, then
- * rows per x tile and x-pass CTA width, then column-pass CTA width, each
- * phase starting from the best of the last, the fixed rule first -- as `reps`
- * RK45 attempts each (CUDA events, after two untimed ones) in a scratch
- * context of one simulation with the same mesh, material and per-cell
- * constants on the same device, and set the fastest on every simulation of
- * this context with the same mesh.  best (nullable) receives it resolved,
- * best_ms / rule_ms (nullable) the milliseconds per attempt of the best and of
- * the rule.  The scratch context allocates and frees device memory. */
+/* Autotune the mesh of simulation sim_id (before mm_precompute_demag): time
+ * candidate tunings -- kx block width and column register groups, then rows
+ * per x tile and x-pass CTA width, then column-pass CTA width, each phase
+ * starting from the best of the last, the fixed rule first -- as `reps` RK45
+ * attempts each (CUDA events, after two untimed ones) of a scratch copy of the
+ * whole batch (every simulation with its material, per-cell constants and
+ * current tuning) on the same device, the candidate on the simulations of that
+ * mesh, and set the fastest on them; its CTA widths, which act on the whole
+ * batch, go to every simulation.  best (nullable) receives the chosen values
+ * (0 where the rule was kept), best_ms / rule_ms (nullable) the milliseconds
+ * per attempt of the batch with the best and with the starting tuning.  The
+ * scratch context allocates and frees device memory. */
 int mm_autotune(mm_ctx *ctx, int sim_id, int reps, mm_tuning *best, double *best_ms, double *rule_ms);
 
 /* Applied field of one simulation (field sweeps, Listing 2), A/m. */

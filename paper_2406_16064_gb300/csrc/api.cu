@@ -72,7 +72,7 @@ struct mm_ctx {
     SimDesc* desc_d = nullptr;
     SimState* state_d = nullptr;
     WorkItem *xi = nullptr, *y13i = nullptr, *zi = nullptr, *y2i = nullptr;
-    WorkItem* yzci[2 * kYzcLists] = {};
+    WorkItem* yzci[kYzcListCount] = {};
     PlanItems plan;
     // per simulation: first item and item count in each list (the yzc list is the
     // one of its plane count and group width, yzcl)
@@ -145,7 +145,7 @@ Launch make_launch(mm_ctx* C, int sim) {
     set(L.y13, C->y13i, C->y13b, C->y13c, P.y13);
     set(L.z, C->zi, C->zb, C->zc, P.z);
     set(L.y2, C->y2i, C->y2b, C->y2c, P.y2);
-    for (int li = 0; li < 2 * kYzcLists; ++li) {
+    for (int li = 0; li < kYzcListCount; ++li) {
         if (sim < 0) L.yzc[li] = {C->yzci[li], (int)P.yzc[li].size()};
         else if (C->yzcl[sim] == li) L.yzc[li] = {C->yzci[li] + C->yzcb[sim], C->yzcc[sim]};
     }
@@ -248,8 +248,8 @@ int validate_items(mm_ctx* C) {
         if (w.a < 0 || w.a >= d.Py || w.b < 0 || w.b >= d.NBx) return fail(C, MM_EBOUNDS, "z item range");
         if (3ULL * d.Pz * d.Ty * vsz > P.smem_z) return fail(C, MM_EBOUNDS, "z item smem");
     }
-    for (int li = 0; li < 2 * kYzcLists; ++li) {
-        const int nz = li % kYzcLists;
+    for (int li = 0; li < kYzcListCount; ++li) {
+        const int nz = plan_yzc_nz(li);
         for (const WorkItem& w : P.yzc[li]) {
             const SimDesc& d = C->sims[w.sim].d;
             if (d.nz != nz || d.Py < 2 || w.b < 0 || w.b >= d.NBx || d.Pz != plan_pad_len(nz, false) ||
@@ -541,7 +541,7 @@ int mm_destroy(mm_ctx* C) {
     for (void* p : ptrs) if (p) cudaFree(p);
     if (C->host_stage) cudaFreeHost(C->host_stage);
     for (int j = 0; j < 7; ++j) if (C->k[j]) cudaFree(C->k[j]);
-    for (int li = 0; li < 2 * kYzcLists; ++li) if (C->yzci[li]) cudaFree(C->yzci[li]);
+    for (int li = 0; li < kYzcListCount; ++li) if (C->yzci[li]) cudaFree(C->yzci[li]);
     if (C->own_stream) cudaStreamDestroy(C->stream);
     delete C;
     return MM_OK;
@@ -601,13 +601,15 @@ namespace {
 Tuning from_abi(const mm_tuning& t) {
     Tuning u;
     u.Ty = t.Ty; u.Rx = t.Rx; u.x_threads = t.x_threads; u.col_threads = t.col_threads; u.col_group = t.col_group;
+    u.col_occ = t.col_occ;
     return u;
 }
 
 // Plan sim s with tuning t (before finalisation); MM_EINVAL if its tiles do not fit.
 int apply_tuning(mm_ctx* C, SimHost& s, const Tuning& t) {
     const bool f32 = C->precision == MM_F32;
-    if (t.Ty < 0 || t.Rx < 0 || t.x_threads < 0 || t.col_threads < 0 || t.col_group < 0 || t.col_group > 2)
+    if (t.Ty < 0 || t.Rx < 0 || t.x_threads < 0 || t.col_threads < 0 || t.col_group < 0 || t.col_group > 2 ||
+        (t.col_occ != 0 && t.col_occ != 2 && t.col_occ != 3))
         return fail(C, MM_EINVAL, "mm_set_tuning: negative or unknown value");
     if (t.Ty > 32 || (t.Ty & (t.Ty - 1))) return fail(C, MM_EINVAL, "mm_set_tuning: Ty must be a power of two <= 32");
     SimDesc d = s.d;
@@ -634,20 +636,39 @@ mm_tuning resolved_tuning(const mm_ctx* C, const SimHost& s) {
     r.x_threads = s.tune.x_threads ? s.tune.x_threads : plan_wide_threads(P.smem_x, maxth);
     const size_t sc = std::max(P.smem_y13, std::max(P.smem_z, P.smem_y2));
     r.col_threads = s.tune.col_threads ? s.tune.col_threads : (sc ? plan_wide_threads(sc, maxth) : 0);
-    r.col_group = plan_uses_yzc(s.d) ? (plan_yzc_list(s.d, f32) >= kYzcLists ? 2 : 1) : 0;
+    r.col_group = plan_uses_yzc(s.d) ? (plan_yzc_wide(plan_yzc_list(s.d, f32)) ? 2 : 1) : 0;
+    r.col_occ = (plan_uses_yzc(s.d) && s.d.yzcocc == 3) ? 3 : 0;
     return r;
 }
 
-// Milliseconds per RK45 attempt of one simulation like s under tuning t, in a
-// scratch context on C's device (two untimed attempts, then `reps` timed).
-int time_tuning(mm_ctx* C, const SimHost& s, const Tuning& t, int reps, double* ms) {
+bool same_mesh(const mm_mesh& a, const mm_mesh& b) {
+    return a.nx == b.nx && a.ny == b.ny && a.nz == b.nz && a.dx == b.dx && a.dy == b.dy && a.dz == b.dz;
+}
+
+// Tuning t for the simulations of the tuned mesh, and t's launch-wide CTA widths
+// (which act on the whole batch) with its own tiles for any other simulation.
+Tuning tuning_for(const SimHost& o, const mm_mesh& tuned, const Tuning& t) {
+    if (same_mesh(o.mesh, tuned)) return t;
+    Tuning u = o.tune;
+    u.x_threads = t.x_threads;
+    u.col_threads = t.col_threads;
+    return u;
+}
+
+// Milliseconds per RK45 attempt of a copy of C's whole batch with tuning t on the
+// simulations of `tuned`'s mesh, in a scratch context on C's device (two untimed
+// attempts, then `reps` timed): the batch as it will run, so a mesh is tuned for
+// the launches it shares with the other meshes.
+int time_tuning(mm_ctx* C, const mm_mesh& tuned, const Tuning& t, int reps, double* ms) {
     mm_ctx* T = nullptr;
     int rc = mm_create(&T, C->device, C->precision, nullptr);
     if (rc) return fail(C, rc, "mm_autotune: scratch context: %s", g_last_error);
-    SimHost h = s;
-    h.d.group_begin = h.d.group_end = -1;
-    h.d.neb_index = -1;
-    T->sims.push_back(h);
+    for (const SimHost& o : C->sims) {
+        SimHost h = o;
+        h.d.group_begin = h.d.group_end = -1;
+        h.d.neb_index = -1;
+        T->sims.push_back(h);
+    }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     auto done = [&](int code) -> int {
         if (e0) cudaEventDestroy(e0);
@@ -656,17 +677,20 @@ int time_tuning(mm_ctx* C, const SimHost& s, const Tuning& t, int reps, double* 
         mm_destroy(T);
         return MM_OK;
     };
-    if ((rc = apply_tuning(T, T->sims[0], t))) return done(rc);
+    for (SimHost& h : T->sims)
+        if ((rc = apply_tuning(T, h, tuning_for(h, tuned, t)))) return done(rc);
     if ((rc = mm_precompute_demag(T))) return done(rc);
-    const long long n = 3LL * h.d.ncells, N = h.d.ncells;
-    std::vector<double> m(n);
-    for (long long i = 0; i < N; ++i) {          // a smooth unit-vector texture
-        const double a = 0.37 * (double)(i % 97), b = 0.11 * (double)(i % 89);
-        m[i] = std::cos(a) * std::sin(b + 0.3);
-        m[N + i] = std::sin(a) * std::sin(b + 0.3);
-        m[2 * N + i] = std::cos(b + 0.3);
+    for (size_t j = 0; j < T->sims.size(); ++j) {
+        const long long N = T->sims[j].d.ncells;
+        std::vector<double> m(3 * N);
+        for (long long i = 0; i < N; ++i) {      // a smooth unit-vector texture
+            const double a = 0.37 * (double)(i % 97), b = 0.11 * (double)(i % 89);
+            m[i] = std::cos(a) * std::sin(b + 0.3);
+            m[N + i] = std::sin(a) * std::sin(b + 0.3);
+            m[2 * N + i] = std::cos(b + 0.3);
+        }
+        if ((rc = mm_set_m(T, (int)j, m.data(), MM_HOST))) return done(rc);
     }
-    if ((rc = mm_set_m(T, 0, m.data(), MM_HOST))) return done(rc);
     if ((rc = mm_rk45_setup(T, 1e-5, 0.0, 0.0))) return done(rc);
     if ((rc = launch_attempts(T, 2))) return done(rc);
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return done(MM_ECUDA);
@@ -678,10 +702,6 @@ int time_tuning(mm_ctx* C, const SimHost& s, const Tuning& t, int reps, double* 
     cudaEventElapsedTime(&t_ms, e0, e1);
     *ms = (double)t_ms / reps;
     return done(MM_OK);
-}
-
-bool same_mesh(const mm_mesh& a, const mm_mesh& b) {
-    return a.nx == b.nx && a.ny == b.ny && a.nz == b.nz && a.dx == b.dx && a.dy == b.dy && a.dz == b.dz;
 }
 
 }  // namespace
@@ -709,12 +729,15 @@ int mm_autotune(mm_ctx* C, int sim, int reps, mm_tuning* best_out, double* best_
     if (sim < 0 || sim >= (int)C->sims.size() || reps < 1) return fail(C, MM_EINVAL, "bad arguments");
     const bool f32 = C->precision == MM_F32;
     const SimHost& s = C->sims[sim];
+    const mm_mesh mesh = s.mesh;
     SimDesc r = s.d;
     plan_geometry(r, f32);                       // the rule
     Tuning best;
     best.Ty = r.Ty;
     best.Rx = r.Rx;
-    best.col_group = (f32 && plan_uses_yzc(r)) ? (plan_yzc_list(r, f32) >= kYzcLists ? 2 : 1) : 0;
+    best.x_threads = s.tune.x_threads;           // launch-wide: as the batch has them
+    best.col_threads = s.tune.col_threads;
+    best.col_group = (f32 && plan_uses_yzc(r)) ? (plan_yzc_wide(plan_yzc_list(r, f32)) ? 2 : 1) : 0;
     double tbest = 0.0, trule = 0.0;
     bool first = true;
     for (int phase = 0; phase < 3; ++phase) {
@@ -723,20 +746,22 @@ int mm_autotune(mm_ctx* C, int sim, int reps, mm_tuning* best_out, double* best_
         for (size_t i = 0; i < cand.size(); ++i) {
             if (i == 0 && !first) continue;      // the phase's starting point was timed already
             double ms = 0.0;
-            const int rc = time_tuning(C, s, cand[i], reps, &ms);
+            const int rc = time_tuning(C, mesh, cand[i], reps, &ms);
             if (rc) return rc;
             if (first) { trule = ms; tbest = ms; best = cand[i]; first = false; continue; }
             if (ms < tbest) { tbest = ms; best = cand[i]; }
         }
         (void)fixed;
     }
-    const mm_mesh mesh = s.mesh;
-    for (SimHost& o : C->sims)
-        if (same_mesh(o.mesh, mesh)) {
-            const int rc = apply_tuning(C, o, best);
-            if (rc) return rc;
-        }
-    if (best_out) *best_out = resolved_tuning(C, C->sims[sim]);
+    for (SimHost& o : C->sims) {
+        const int rc = apply_tuning(C, o, tuning_for(o, mesh, best));
+        if (rc) return rc;
+    }
+    if (best_out) {
+        best_out->Ty = best.Ty; best_out->Rx = best.Rx; best_out->x_threads = best.x_threads;
+        best_out->col_threads = best.col_threads; best_out->col_group = best.col_group;
+        best_out->col_occ = best.col_occ;
+    }
     if (best_ms) *best_ms = tbest;
     if (rule_ms) *rule_ms = trule;
     return MM_OK;
@@ -918,7 +943,7 @@ int mm_precompute_demag(mm_ctx* C) {
     if ((rc = up_items(&C->y13i, P.y13))) return rc;
     if ((rc = up_items(&C->zi, P.z))) return rc;
     if ((rc = up_items(&C->y2i, P.y2))) return rc;
-    for (int li = 0; li < 2 * kYzcLists; ++li)
+    for (int li = 0; li < kYzcListCount; ++li)
         if ((rc = up_items(&C->yzci[li], P.yzc[li]))) return rc;
     CK(cudaMemcpyAsync(C->kvec_dev, C->k, 7 * sizeof(void*), cudaMemcpyHostToDevice, C->stream));
     CK(cudaMemsetAsync(C->spec, 0, (size_t)C->spec_elems * 2 * C->esz, C->stream));

@@ -31,9 +31,17 @@ static int wide_threads(size_t smem, int tuned = 0) {
     return plan_wide_threads(smem, MM_XTHREADS_MAX<T>);
 }
 
-// The cluster kernel for nz planes (2..8) and the column group width.
+// The cluster kernel for nz planes (2..8), the column group width and the CTAs
+// per SM it is built for (3: FP32 up to kYzcOcc3MaxPlanes planes).
 template <typename T>
-static void (*yzc_kernel(int nz, bool wide))(PassParams<T>) {
+static void (*yzc_kernel(int nz, bool wide, bool occ3 = false))(PassParams<T>) {
+    if (occ3 && sizeof(T) == 4 && nz <= kYzcOcc3MaxPlanes) {
+        switch (nz) {
+            case 2: return wide ? k_yzc<T, 2, true, 3> : k_yzc<T, 2, false, 3>;
+            case 3: return wide ? k_yzc<T, 3, true, 3> : k_yzc<T, 3, false, 3>;
+            default: return wide ? k_yzc<T, 4, true, 3> : k_yzc<T, 4, false, 3>;
+        }
+    }
     switch (nz) {
         case 2: return wide ? k_yzc<T, 2, true> : k_yzc<T, 2, false>;
         case 3: return wide ? k_yzc<T, 3, true> : k_yzc<T, 3, false>;
@@ -81,10 +89,10 @@ static void issue_passes(const Launch& L, PassParams<T> p, const T* ys, bool inc
         if (hk) hk->mark(KIND_YINV);
         ++n;
     }
-    for (int li = 0; li < 18; ++li) {
+    for (int li = 0; li < kYzcListCount; ++li) {
         if (!L.yzc[li].count) continue;
-        const int nz = li % 9;
-        const bool wide = li >= 9;
+        const int nz = li % kYzcLists;
+        const bool wide = ((li / kYzcLists) & 1) != 0, occ3 = li >= 2 * kYzcLists;
         p.items = L.yzc[li].dev;
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)(L.yzc[li].count * nz), 1, 1);
@@ -99,7 +107,7 @@ static void issue_passes(const Launch& L, PassParams<T> p, const T* ys, bool inc
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         // one instantiation per plane count; wide: 32-point column groups
-        cudaLaunchKernelEx(&cfg, yzc_kernel<T>(nz, wide), p);
+        cudaLaunchKernelEx(&cfg, yzc_kernel<T>(nz, wide, occ3), p);
         if (hk) hk->mark(KIND_YZC);
         ++n;
     }
@@ -237,10 +245,10 @@ static void set_attrs() {
     cudaFuncSetAttribute(k_ycol<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     cudaFuncSetAttribute(k_ycol<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     cudaFuncSetAttribute(k_zcol<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    for (int nz = 2; nz <= 8; ++nz) {
-        cudaFuncSetAttribute(yzc_kernel<T>(nz, false), cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-        cudaFuncSetAttribute(yzc_kernel<T>(nz, true), cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    }
+    for (int nz = 2; nz <= 8; ++nz)
+        for (int v = 0; v < 4; ++v)
+            cudaFuncSetAttribute(yzc_kernel<T>(nz, (v & 1) != 0, v >= 2), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 mx);
 }
 
 }  // namespace mm

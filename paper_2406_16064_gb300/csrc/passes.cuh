@@ -491,9 +491,12 @@ __device__ void yzc_zstep(const PassParams<T>& p, const SimDesc& d, V2<T>* const
 // small spill there costs less than the halved occupancy, measured on the
 // 512x512x4 film); FP64 with more planes keeps the registers it needs.
 // NZ: planes (= cluster size); WIDE: 32-point register groups for the y columns
-// (FP32; see plan_yzc_list).
-template <typename T, int NZ, bool WIDE>
-__global__ void __launch_bounds__(MM_THREADS, (sizeof(T) == 4 || NZ <= 4) ? 2 : 1) k_yzc(PassParams<T> p) {
+// (FP32; see plan_yzc_list); MINB: CTAs per SM the build is bounded for (0: the
+// rule above; 3: 85 registers a thread, for narrow column tiles whose shared
+// memory lets three CTAs share an SM).
+template <typename T, int NZ, bool WIDE, int MINB = 0>
+__global__ void __launch_bounds__(MM_THREADS, MINB ? MINB : ((sizeof(T) == 4 || NZ <= 4) ? 2 : 1))
+    k_yzc(PassParams<T> p) {
     namespace cg = cooperative_groups;
     extern __shared__ __align__(16) unsigned char smraw[];
     V2<T>* sm = reinterpret_cast<V2<T>*>(smraw);

@@ -30,8 +30,6 @@ inline int plan_pad_len(int n, bool min2) {
     return p;
 }
 
-// Largest plane count handled by the cluster-fused y/z pass (portable cluster size).
-constexpr int kMaxClusterPlanes = 8;
 
 // Tile shapes and schedules an autotuner may set per simulation; 0 keeps the
 // fixed rule of plan_geometry / plan_yzc_list / plan_wide_threads.
@@ -40,8 +38,10 @@ constexpr int kMaxClusterPlanes = 8;
 //   x_threads   threads of an x-pass CTA (multiple of 32; launch-wide)
 //   col_threads threads of a column-pass CTA outside the cluster pass (launch-wide)
 //   col_group   cluster-pass column register groups: 1 16-point, 2 32-point
+//   col_occ     cluster-pass CTAs per SM its kernel is built for: 3 (FP32, up to
+//               kYzcOcc3MaxPlanes planes; fewer registers a thread), else the rule (2)
 struct Tuning {
-    int Ty = 0, Rx = 0, x_threads = 0, col_threads = 0, col_group = 0;
+    int Ty = 0, Rx = 0, x_threads = 0, col_threads = 0, col_group = 0, col_occ = 0;
 };
 
 // Fill the padded sizes, tensor bins and tile shapes of d from d.nx, d.ny, d.nz
@@ -73,6 +73,7 @@ inline void plan_geometry(SimDesc& d, bool f32, const Tuning& t = Tuning()) {
     d.lTy = plan_ilog2(d.Ty);
     d.NBx = (d.Kx + d.Ty - 1) >> d.lTy;
     d.colgroup = (t.col_group == 1 || t.col_group == 2) ? t.col_group : 0;
+    d.yzcocc = t.col_occ == 3 ? 3 : 0;
 }
 
 template <typename T>
@@ -150,18 +151,21 @@ inline void plan_extended(SimDesc& d, bool has_cells, bool a_any, bool d_any) {
 // reads its tensor in a blocked layout (plan_tens_elems).
 inline bool plan_uses_yzc(const SimDesc& d) { return d.Pz > 1 && d.Py > 1 && d.nz <= kMaxClusterPlanes; }
 
-// Cluster-pass work lists, one per (plane count nz, register-group width):
-// list nz + kYzcLists * wide.  FP32 columns of 2^5, 2^9 or 2^13 points run
+// Cluster-pass work lists, one per (plane count nz, register-group width, CTAs
+// per SM): list nz + kYzcLists * wide + 2 kYzcLists * occ3.  FP32 columns of
+// 2^5, 2^9 or 2^13 points run
 // with 32-point register groups (their schedule then holds exactly one
 // 32-point group: (5), (5,4), (5,4,4)); every other length with 16-point
 // groups, whose schedule is the same or better (two unrolled 32-point groups
 // per direction no longer fit the instruction cache: 1024-point columns
 // measured faster as (4,3,3) than as (5,5)).
-constexpr int kYzcLists = kMaxClusterPlanes + 1;
 inline int plan_yzc_list(const SimDesc& d, bool f32) {
     const bool wide = d.colgroup ? d.colgroup == 2 : f32 && (d.lPy == 5 || d.lPy == 9 || d.lPy == 13);
-    return d.nz + kYzcLists * (wide ? 1 : 0);
+    return d.nz + kYzcLists * (wide ? 1 : 0) + 2 * kYzcLists * (d.yzcocc == 3 ? 1 : 0);
 }
+inline int plan_yzc_nz(int li) { return li % kYzcLists; }
+inline bool plan_yzc_wide(int li) { return ((li / kYzcLists) & 1) != 0; }
+inline bool plan_yzc_occ3(int li) { return li >= 2 * kYzcLists; }
 
 // Elements of a geometry's stored tensor:
 //   standard [ncomp][Pz/2+1][Py/2+1][Kx];
@@ -181,7 +185,7 @@ inline size_t plan_xinv_smem(const SimDesc& d, size_t vsz) {
 }
 
 struct PlanItems {
-    std::vector<WorkItem> x, y13, z, y2, yzc[2 * kYzcLists];
+    std::vector<WorkItem> x, y13, z, y2, yzc[kYzcListCount];
     size_t smem_x = 0, smem_xi = 0, smem_y13 = 0, smem_z = 0, smem_y2 = 0, smem_yzc = 0;
 };
 
@@ -223,6 +227,9 @@ namespace mm {
 // launch bound).  vsz = bytes of one complex value.
 inline bool plan_tuning_valid(const SimDesc& d, size_t vsz, const Tuning& t, int maxthreads) {
     if (d.Ty < 1 || d.Ty > 32 || (d.Ty & (d.Ty - 1)) || d.Rx < 1 || d.Rx > d.ny) return false;
+    if (d.yzcocc == 3 && !(vsz == 8 && plan_uses_yzc(d) && d.nz <= kYzcOcc3MaxPlanes &&
+                           3 * ((size_t)3 * d.Py * d.Ty * vsz + 1024) <= 233472))
+        return false;
     for (int th : {t.x_threads, t.col_threads})
         if (th != 0 && (th < 32 || th > maxthreads || th % 32)) return false;
     PlanItems P;
@@ -252,7 +259,7 @@ inline std::vector<Tuning> plan_tuning_candidates(const SimDesc& d0, bool f32, i
         if (!plan_tuning_valid(d, vsz, t, maxthreads)) return;
         for (const Tuning& u : out)
             if (u.Ty == t.Ty && u.Rx == t.Rx && u.x_threads == t.x_threads && u.col_threads == t.col_threads &&
-                u.col_group == t.col_group)
+                u.col_group == t.col_group && u.col_occ == t.col_occ)
                 return;
         out.push_back(t);
     };
@@ -262,17 +269,19 @@ inline std::vector<Tuning> plan_tuning_candidates(const SimDesc& d0, bool f32, i
     if (phase == 0) {
         const int tymax = std::min(32, 1 << plan_ilog2(std::max(1, r.Kx)));
         const bool groups = f32 && plan_uses_yzc(r);
-        const int g0 = plan_yzc_list(r, f32) >= kYzcLists ? 2 : 1;
-        for (int ty : {r.Ty / 2, r.Ty, 2 * r.Ty}) {
-            if (ty < 1 || ty > tymax) continue;
-            for (int g : {g0, 3 - g0}) {
-                if (!groups && g != g0) continue;
-                Tuning t = fixed;
-                t.Ty = ty;
-                t.col_group = groups ? g : 0;
-                add(t);
+        const int g0 = plan_yzc_wide(plan_yzc_list(r, f32)) ? 2 : 1;
+        for (int ty : {r.Ty / 2, r.Ty, 2 * r.Ty, r.Ty / 4})
+            for (int occ : {0, 3}) {
+                if (ty < 1 || ty > tymax || (occ && !groups)) continue;
+                for (int g : {g0, 3 - g0}) {
+                    if (!groups && g != g0) continue;
+                    Tuning t = fixed;
+                    t.Ty = ty;
+                    t.col_group = groups ? g : 0;
+                    t.col_occ = occ;
+                    add(t);
+                }
             }
-        }
     } else if (phase == 1) {
         PlanItems P;
         SimDesc e = r;

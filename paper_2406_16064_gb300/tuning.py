@@ -34,8 +34,21 @@ def cache_path():
         os.path.expanduser("~"), ".cache", "paper_2406_16064_gb300", "tuning.json")
 
 
-def key(gpu, precision, mesh):
-    return f"{gpu}|{build_id()}|{precision}|{mesh.nx}x{mesh.ny}x{mesh.nz}"
+def _dims(m):
+    return (m.nx, m.ny, m.nz)
+
+
+def batch_signature(meshes):
+    """The batch's meshes and their counts: a mesh is tuned for the launches it shares."""
+    count = {}
+    for m in meshes:
+        count[_dims(m)] = count.get(_dims(m), 0) + 1
+    return ",".join(f"{a}x{b}x{c}*{n}" for (a, b, c), n in sorted(count.items()))
+
+
+def key(gpu, precision, mesh, meshes=None):
+    sig = batch_signature(meshes if meshes is not None else [mesh])
+    return f"{gpu}|{build_id()}|{precision}|{mesh.nx}x{mesh.ny}x{mesh.nz}|{sig}"
 
 
 def load(path=None):
@@ -58,30 +71,29 @@ def save(entries, path=None):
 
 def tune_context(ctx, meshes, gpu, reps=8, path=None, retune=False):
     """Give every simulation of ctx (not yet precomputed; meshes[i] is simulation i's
-    mesh) the autotuned tiles of its mesh: from the cache when it has them, else by
-    mm_autotune (which sets them on every simulation with that mesh), then cached.
-    Returns {mesh key: entry} with the tuning, its ms per attempt and the rule's."""
+    mesh) the autotuned tiles of its mesh: from the cache when it has every mesh of
+    this batch, else by mm_autotune, one mesh after the other (each timed inside a
+    copy of the whole batch), then cached.  The CTA widths act on whole launches, so
+    every mesh's entry carries the widths the last tuning chose.  Returns {mesh key:
+    entry} with the tuning, its ms per attempt and the starting tuning's."""
     cache = load(path)
-    out, seen = {}, set()
-    changed = False
+    firsts = {}
     for i, m in enumerate(meshes):
-        k = key(gpu, ctx.precision, m)
-        if k in seen:
-            continue
-        seen.add(k)
-        if k in cache and not retune:
-            for j, mj in enumerate(meshes):
-                if (mj.nx, mj.ny, mj.nz) == (m.nx, m.ny, m.nz):
-                    ctx.set_tuning(j, cache[k]["tuning"])
-            out[k] = dict(cache[k], cached=True)
-            continue
+        firsts.setdefault(_dims(m), i)
+    keys = {d: key(gpu, ctx.precision, meshes[i], meshes) for d, i in firsts.items()}
+    if not retune and all(k in cache for k in keys.values()):
+        for j, m in enumerate(meshes):
+            ctx.set_tuning(j, cache[keys[_dims(m)]]["tuning"])
+        return {k: dict(cache[k], cached=True) for k in keys.values()}
+    out = {}
+    for d, i in firsts.items():
         t, best, rule = ctx.autotune(i, reps)
-        for j, mj in enumerate(meshes):   # same cells, other cell sizes: same tiles
-            if (mj.nx, mj.ny, mj.nz) == (m.nx, m.ny, m.nz):
-                ctx.set_tuning(j, t)
-        cache[k] = {"tuning": t, "ms_per_attempt": best, "rule_ms_per_attempt": rule}
-        out[k] = dict(cache[k], cached=False)
-        changed = True
-    if changed:
-        save(cache, path)
-    return out
+        out[keys[d]] = {"tuning": t, "ms_per_attempt": best, "rule_ms_per_attempt": rule}
+    widths = {k: t[k] for k in ("x_threads", "col_threads")}
+    for k in out:
+        out[k]["tuning"].update(widths)
+        cache[k] = dict(out[k])
+    save(cache, path)
+    for j, m in enumerate(meshes):             # the same values as the tuning left them
+        ctx.set_tuning(j, out[keys[_dims(m)]]["tuning"])
+    return {k: dict(v, cached=False) for k, v in out.items()}

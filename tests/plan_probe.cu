@@ -39,13 +39,13 @@ int main() {
         print_items("z", P.z); printf(", ");
         print_items("y2", P.y2); printf(", ");
         std::vector<WorkItem> all;
-        for (int li = 0; li < 2 * kYzcLists; ++li) all.insert(all.end(), P.yzc[li].begin(), P.yzc[li].end());
+        for (int li = 0; li < kYzcListCount; ++li) all.insert(all.end(), P.yzc[li].begin(), P.yzc[li].end());
         print_items("yzc_items", all);
         // autotuner candidates of each phase, starting from the rule
         Tuning fixed;
         fixed.Ty = d.Ty;
         fixed.Rx = d.Rx;
-        fixed.col_group = (f32 && plan_uses_yzc(d)) ? (plan_yzc_list(d, true) >= kYzcLists ? 2 : 1) : 0;
+        fixed.col_group = (f32 && plan_uses_yzc(d)) ? (plan_yzc_wide(plan_yzc_list(d, true)) ? 2 : 1) : 0;
         printf(", \"cands\": [");
         for (int ph = 0; ph < 3; ++ph) {
             const std::vector<Tuning> c = plan_tuning_candidates(d, f32 != 0, ph, fixed);
@@ -55,9 +55,9 @@ int main() {
                 plan_geometry(e, f32 != 0, c[i]);
                 PlanItems Q;
                 plan_items(e, 0, vsz, Q);
-                printf("%s{\"Ty\": %d, \"Rx\": %d, \"xt\": %d, \"ct\": %d, \"g\": %d, \"pTy\": %d, \"pRx\": %d, "
+                printf("%s{\"Ty\": %d, \"Rx\": %d, \"xt\": %d, \"ct\": %d, \"g\": %d, \"occ\": %d, \"pTy\": %d, \"pRx\": %d, "
                        "\"smem\": [%zu,%zu,%zu,%zu,%zu,%zu], \"list\": %d}",
-                       i ? "," : "", c[i].Ty, c[i].Rx, c[i].x_threads, c[i].col_threads, c[i].col_group, e.Ty, e.Rx,
+                       i ? "," : "", c[i].Ty, c[i].Rx, c[i].x_threads, c[i].col_threads, c[i].col_group, c[i].col_occ, e.Ty, e.Rx,
                        Q.smem_x, Q.smem_xi, Q.smem_y13, Q.smem_z, Q.smem_y2, Q.smem_yzc,
                        plan_uses_yzc(e) ? plan_yzc_list(e, f32 != 0) : -1);
             }

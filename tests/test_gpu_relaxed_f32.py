@@ -22,7 +22,10 @@ pytestmark = pytest.mark.gpu
 def test_field_sweep_uneven_batch_f32_matches_f64_oracle():
     """Listing-2 style sweep on an uneven FP32 batch (films of 1 and 2 planes, DMI and
     anisotropy drawn per simulation): at each field every simulation relaxes below
-    1e-2 rad/ns, and the end state of the sweep is within 1e-3 of the FP64 oracle's."""
+    1e-2 rad/ns, and the end state of the sweep is within 1e-3 of the FP64 oracle's.
+    The FP32 run uses rtol = 1e-6: near equilibrium the controller holds the error of
+    the stiff exchange modes at about rtol, which leaves |dm/dt| near rtol times their
+    frequency (~2e12 /s with 2 nm cells), above the 1e7 rad/s threshold at 1e-5."""
     w = synth.uneven_batch(seed=7, count=3, precision="f32", choices=[(8, 8, 1), (6, 4, 2), (12, 6, 1)])
     ctx = make_ctx("f32", w.sims)
     ctx.set_m(np.concatenate([s.m0.ravel() for s in w.sims]))
@@ -33,7 +36,7 @@ def test_field_sweep_uneven_batch_f32_matches_f64_oracle():
     for H in sweep:
         for i in range(len(w.sims)):
             ctx.set_field(i, (0.0, 0.0, H * synth.MT))
-        ctx.relax(1e-5, max_dmdt=w.max_dmdt, max_steps=50000, sync_every=32)
+        ctx.relax(1e-6, max_dmdt=w.max_dmdt, max_steps=50000, sync_every=32)
         for i in range(len(w.sims)):
             assert ctx.status(i)["status"] == 2
         ends.append(ctx.get_m(-1))

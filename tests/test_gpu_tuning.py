@@ -25,11 +25,12 @@ MESHES = [(40, 24, 3), (48, 40, 1), (20, 12, 10)]
 
 
 def _tunings(nz):
-    """Every kx block width, one or two row tiles, three CTA widths, both column groups."""
+    """Every kx block width, one or two row tiles, three CTA widths, both column groups and
+    both cluster-kernel builds (2 or 3 CTAs per SM)."""
     for ty, rx, xt in itertools.product((1, 2, 4, 8, 16, 32), (1, 3), (0, 128, 512)):
-        for g in ((1, 2) if 1 < nz <= 8 else (0,)):
+        for g, occ in (itertools.product((1, 2), (0, 3)) if 1 < nz <= 8 else ((0, 0),)):
             yield {"Ty": ty, "Rx": rx, "x_threads": xt, "col_threads": xt if nz == 1 or nz > 8 else 0,
-                   "col_group": g}
+                   "col_group": g, "col_occ": occ}
 
 
 @pytest.mark.parametrize("precision", ["f32", "f64"])
@@ -52,7 +53,7 @@ def test_every_selectable_tuning_gives_the_oracle_field(precision, dims):
             continue
         ctx.precompute()
         got = ctx.get_tuning(0)
-        assert got["Ty"] == t["Ty"] and got["Rx"] == min(t["Rx"], mesh.ny)
+        assert got["Ty"] == t["Ty"] and got["Rx"] == min(t["Rx"], mesh.ny) and got["col_occ"] == t["col_occ"]
         dmdt, heff = ctx.rhs_host(sim.m0.ravel())
         ctx.close()
         if precision == "f64":
@@ -71,7 +72,10 @@ def test_autotune_picks_no_slower_than_the_rule_and_keeps_parity():
     ctx.add_sim(mesh, sim.mat)                   # a second simulation of the same mesh
     t, best, rule = ctx.autotune(0, reps=4)
     assert best <= rule and best > 0
-    assert ctx.get_tuning(0) == t == ctx.get_tuning(1)
+    got = ctx.get_tuning(0)
+    assert got == ctx.get_tuning(1)
+    assert (got["Ty"], got["Rx"], got["col_group"]) == (t["Ty"], t["Rx"], t["col_group"])
+    assert t["x_threads"] in (0, got["x_threads"])
     ctx.precompute()
     dmdt, heff = ctx.rhs_host(np.concatenate([sim.m0.ravel()] * 2))
     ref_k, ref_H = oracle_rhs(sim, method="fft")
@@ -90,6 +94,7 @@ def test_tuning_cache_round_trip(tmp_path):
     ctx.add_sim(mesh, _mat())
     first = tuning.tune_context(ctx, [mesh], "gpu", reps=3, path=path)
     (k, e), = first.items()
+    assert k.endswith("|64x64x1|64x64x1*1")
     assert e["cached"] is False and e["ms_per_attempt"] <= e["rule_ms_per_attempt"]
     t0 = ctx.get_tuning(0)
     ctx.close()

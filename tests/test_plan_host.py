@@ -154,7 +154,11 @@ def test_autotuner_candidates(probe):
             for th in (c["xt"], c["ct"]):
                 assert th == 0 or (th % 32 == 0 and 32 <= th <= maxth)
             if c["g"]:
-                assert r["f32"] and r["yzc"] and c["list"] == r["mesh"][2] + 9 * (c["g"] - 1)
+                assert r["f32"] and r["yzc"]
+                assert c["list"] == r["mesh"][2] + 9 * (c["g"] - 1) + 18 * (c["occ"] == 3)
+            if c["occ"]:
+                # three CTAs per SM: FP32, at most 4 planes, three column tiles in 228 KB
+                assert r["f32"] and r["yzc"] and r["mesh"][2] <= 4 and 3 * (syzc + 1024) <= 233472
         if not (r["f32"] and r["yzc"]):
             assert all(c["g"] == 0 for c in ph0)
         # phase 1 starts from phase 0's start, phase 2 from phase 1's
