@@ -103,14 +103,18 @@ def done_time(st):
     return st.t_end > 0.0 and st.t_end - st.t <= 1e-12 * st.t_end
 
 
-def step(f, m, st: Stepper, max_dmdt=0.0):
+def step(f, m, st: Stepper, max_dmdt=0.0, reduce=None):
     """Attempt one step.
 
     Returns (m, status): status 1 accepted (m projected), 0 rejected,
     2 converged (max|dm/dt| at m below max_dmdt; nothing stepped).
+    reduce (optional) turns a maximum over the local state into the maximum over
+    a state split across processes (the max|dm/dt| and the error norm); the
+    default is the local maximum itself.
     """
+    red = reduce if reduce is not None else (lambda x: x)
     k1 = f(m)
-    st.last_maxdmdt = max_norm(k1)
+    st.last_maxdmdt = red(max_norm(k1))
     if max_dmdt > 0.0 and st.last_maxdmdt < max_dmdt:
         return m, 2
     if st.h <= 0.0:
@@ -119,7 +123,7 @@ def step(f, m, st: Stepper, max_dmdt=0.0):
             st.h = min(st.h, st.t_end - st.t)
     h = st.h
     y5, errvec, _ = attempt(f, m, h, k1)
-    err = float(np.abs(errvec).max()) / st.rtol if errvec.size else 0.0
+    err = red(float(np.abs(errvec).max()) if errvec.size else 0.0) / st.rtol
     st.last_err = err
     if not np.isfinite(err):
         raise FloatingPointError("non-finite error norm")

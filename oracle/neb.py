@@ -75,11 +75,16 @@ def tangents(chain, energies):
     return tau
 
 
-def chain_rhs(mesh, mat, Ms, chain, k_spring, Ntab=None, method="auto"):
-    """d(chain)/dt and the image energies for a chain of shape (n, 3, nz, ny, nx)."""
+def image_field_energy(mesh, mat, Ms, m, Ntab=None, method="auto"):
+    """Effective field and total energy of one image."""
+    return F.h_eff(mesh, mat, m, Ms, Ntab, method), F.energies(mesh, mat, m, Ms, Ntab, method)["total"]
+
+
+def chain_forces(mat, Ms, chain, H, E, k_spring):
+    """d(chain)/dt of the images 1..n-2 of `chain` (shape (n, 3, nz, ny, nx)) from their
+    fields H[i] and the energies E of all n images; images 0 and n-1 get zeros (the
+    chain's fixed ends, or neighbours owned by another process)."""
     n = chain.shape[0]
-    H = np.stack([F.h_eff(mesh, mat, chain[i], Ms, Ntab, method) for i in range(n)])
-    E = np.array([F.energies(mesh, mat, chain[i], Ms, Ntab, method)["total"] for i in range(n)])
     tau = tangents(chain, E)
     L = [geodesic_distance(chain[i], chain[i + 1]) for i in range(n - 1)]
     gt = mat.gamma / (1.0 + mat.alpha ** 2)
@@ -89,7 +94,16 @@ def chain_rhs(mesh, mat, Ms, chain, k_spring, Ntab=None, method="auto"):
         Fi = H[i] - Ht * tau[i] + k_spring * (L[i] - L[i - 1]) * tau[i]
         m = chain[i]
         out[i] = -mat.alpha * gt * _cross(m, _cross(m, Fi)) * (Ms > 0)[None]
-    return out, E
+    return out
+
+
+def chain_rhs(mesh, mat, Ms, chain, k_spring, Ntab=None, method="auto"):
+    """d(chain)/dt and the image energies for a chain of shape (n, 3, nz, ny, nx)."""
+    n = chain.shape[0]
+    HE = [image_field_energy(mesh, mat, Ms, chain[i], Ntab, method) for i in range(n)]
+    H = np.stack([h for h, _ in HE])
+    E = np.array([e for _, e in HE])
+    return chain_forces(mat, Ms, chain, H, E, k_spring), E
 
 
 def relax(mesh, mat, Ms, chain, k_spring, rtol, steps, Ntab=None, method="auto"):
