@@ -605,8 +605,17 @@ def run_gpu(args, rank, world, dist):
         line["f64"] = {"value": v64, "ms_per_step": ms64 / k64, "steps": k64,
                        "step_algorithmic_gbs": step_bytes_whole(w, 8) / (ms64 / k64 / 1e3) / 1e9,
                        "step_frac": step_bytes_whole(w, 8) / (ms64 / k64 / 1e3) / 1e9 / hbm,
-                       "autotune": t64 or None}
+                       "autotune": t64 or None,
+                       "transforms": "double-float (FP32 pairs); FP64 state, prologue, epilogue and reductions"}
         ctx64.close()
+        # the same FP64 workload with native FP64 arithmetic in every kernel, for comparison
+        ctxn = setup_ctx(mm, w64, "f64_native", stream, 1e-6)
+        ctxn.rk45_attempts(1)
+        kn = 3
+        msn = timed_attempts(ctxn, torch, stream, kn)
+        line["f64"]["native_fp64"] = {"value": (ncell_job / ncell) * ncell * 7 * kn / (msn / 1e3),
+                                      "ms_per_step": msn / kn, "steps": kn}
+        ctxn.close()
     if rank == 0 and not args.no_cpu:
         v, P, n, dt, mesh = oracle_rate(w, 12.0)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": P, "kind": "oracle",

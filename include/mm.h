@@ -64,7 +64,14 @@ enum {
                            (checked on the host before the first launch) */
 };
 
-enum { MM_F64 = 0, MM_F32 = 1 };          /* context precision */
+/* Context precision.  MM_F64: FP64 state, stage vectors, fields and
+ * reductions; the FFT transforms, the tensor product and the z convolution
+ * compute in double-float arithmetic (an FP32 pair hi + lo, about 48
+ * significant bits) on the FP32 pipe, since GB300's FP64 rate is a small
+ * fraction of its FP32 rate; fields agree with native FP64 to ~1e-14.
+ * MM_F32: FP32 state and arithmetic with FP64-accurate norms, error norm and
+ * energies.  MM_F64_NATIVE: FP64 arithmetic in every kernel. */
+enum { MM_F64 = 0, MM_F32 = 1, MM_F64_NATIVE = 2 };
 enum { MM_HOST = 0, MM_DEVICE = 1 };      /* where a buffer lives */
 /* DMI symmetry class (Sec. "Dzyaloshinskii-Moriya Energy"): DMI vectors e_ij
  * for the neighbours (-x, +x, -y, +y, -z, +z): interfacial (C_nv)

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmm.so")
-SOURCES = ["api.cu", "engine_f32.cu", "engine_f64.cu", "newell.cu", "static_rhs.cu", "minimize.cu",
+SOURCES = ["api.cu", "engine_f32.cu", "engine_f64.cu", "engine_dd.cu", "newell.cu", "static_rhs.cu", "minimize.cu",
            "cayley.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

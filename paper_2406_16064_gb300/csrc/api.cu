@@ -65,7 +65,8 @@ struct mm_ctx {
     bool finalized = false;
     long long total_elems = 0, spec_elems = 0, ms_elems = 0, tens_elems = 0, oct_elems = 0, cell_elems = 0;
     void *m = nullptr, *ybuf = nullptr, *k[7] = {}, *errp = nullptr, *spec = nullptr, *Msd = nullptr,
-         *tens = nullptr, *twd = nullptr, *twf = nullptr, *cellp = nullptr;
+         *tens = nullptr, *twd = nullptr, *twf = nullptr, *twdd = nullptr, *cellp = nullptr;
+    bool dd = false;            // FP64 storage with double-float transforms (MM_F64)
     void *sc_in = nullptr, *sc_out = nullptr, *sc_h = nullptr, *heff = nullptr, *tau = nullptr;
     void** kvec_dev = nullptr;
     double* oct = nullptr;
@@ -166,7 +167,8 @@ Launch make_launch(mm_ctx* C, int sim) {
     L.Ms = C->Msd;
     L.cellp = C->cellp;
     for (const SimHost& s : C->sims) L.ext = L.ext || (s.d.flags & F_EXT) != 0;
-    L.tw = C->precision == MM_F32 ? C->twf : C->twd;
+    L.tw = C->precision == MM_F32 ? C->twf : (C->dd ? C->twdd : C->twd);
+    L.dd = C->dd;
     L.spec = C->spec;
     L.launches = &C->launches;
     return L;
@@ -309,7 +311,8 @@ int precompute_geometry(mm_ctx* C, Geom& g, const SimDesc& d) {
             launch_fft_axis_f64(C->stream, buf, d.Px, d.Py, d.Pz, ax, C->twd);
         char* out = (char*)C->tens + (size_t)g.tens_off * C->esz;
         launch_newell_extract(C->stream, buf, c, d.Px, d.Py, d.Kx, d.Pyh, blocked ? d.nz : d.Pzh, scale, out,
-                              C->precision == MM_F32, blocked ? d.Ty : 0, yzc_qp(d.nz), blocked ? 1 : 0,
+                              C->precision == MM_F32 ? 1 : (C->dd ? 2 : 0), blocked ? d.Ty : 0, yzc_qp(d.nz),
+                              blocked ? 1 : 0,
                               C->diag_d, C->diag_d + 1);
         C->launches += blocked ? 4 : 5;
         CK(cudaGetLastError());
@@ -503,7 +506,8 @@ const char* mm_last_error(const mm_ctx* C) { return C ? C->err.c_str() : g_last_
 int mm_create(mm_ctx** out, int device, int precision, void* cuda_stream) {
     if (!out) return fail(nullptr, MM_EINVAL, "out is NULL");
     *out = nullptr;
-    if (precision != MM_F64 && precision != MM_F32) return fail(nullptr, MM_EINVAL, "precision must be MM_F64 or MM_F32");
+    if (precision != MM_F64 && precision != MM_F32 && precision != MM_F64_NATIVE)
+        return fail(nullptr, MM_EINVAL, "precision must be MM_F64, MM_F32 or MM_F64_NATIVE");
     int n = 0;
     cudaError_t e = cudaGetDeviceCount(&n);
     if (e != cudaSuccess || n == 0) {
@@ -513,7 +517,8 @@ int mm_create(mm_ctx** out, int device, int precision, void* cuda_stream) {
     if (device < 0 || device >= n) return fail(nullptr, MM_EINVAL, "device %d out of range", device);
     mm_ctx* C = new mm_ctx;
     C->device = device;
-    C->precision = precision;
+    C->precision = precision == MM_F32 ? MM_F32 : MM_F64;
+    C->dd = precision == MM_F64;
     C->esz = precision == MM_F32 ? 4 : 8;
     e = cudaSetDevice(device);
     if (e != cudaSuccess) { delete C; return fail(nullptr, MM_ECUDA, "cudaSetDevice: %s", cudaGetErrorString(e)); }
@@ -534,7 +539,8 @@ int mm_destroy(mm_ctx* C) {
     if (C->rk_exec) cudaGraphExecDestroy(C->rk_exec);
     if (C->sd_exec) cudaGraphExecDestroy(C->sd_exec);
     if (C->c4_exec) cudaGraphExecDestroy(C->c4_exec);
-    void* ptrs[] = {C->m, C->ybuf, C->errp, C->spec, C->Msd, C->cellp, C->tens, C->twd, C->twf, C->sc_in, C->sc_out,
+    void* ptrs[] = {C->m, C->ybuf, C->errp, C->spec, C->Msd, C->cellp, C->tens, C->twd, C->twf, C->twdd, C->sc_in,
+                    C->sc_out,
                     C->sc_h, C->heff, C->tau, C->kvec_dev, C->oct, C->desc_d, C->state_d, C->xi, C->y13i,
                     C->zi, C->y2i, C->flag_d, C->status_d, C->diag_d, C->sd_H, C->sd_mprev, C->sd_g,
                     C->sd_d};
@@ -661,7 +667,7 @@ Tuning tuning_for(const SimHost& o, const mm_mesh& tuned, const Tuning& t) {
 // the launches it shares with the other meshes.
 int time_tuning(mm_ctx* C, const mm_mesh& tuned, const Tuning& t, int reps, double* ms) {
     mm_ctx* T = nullptr;
-    int rc = mm_create(&T, C->device, C->precision, nullptr);
+    int rc = mm_create(&T, C->device, C->precision == MM_F32 ? MM_F32 : (C->dd ? MM_F64 : MM_F64_NATIVE), nullptr);
     if (rc) return fail(C, rc, "mm_autotune: scratch context: %s", g_last_error);
     for (const SimHost& o : C->sims) {
         SimHost h = o;
@@ -926,6 +932,7 @@ int mm_precompute_demag(mm_ctx* C) {
     if ((rc = dalloc(C, (void**)&C->oct, (size_t)C->oct_elems * 8))) return rc;
     if ((rc = dalloc(C, &C->twd, (size_t)MM_TW_ENTRIES * 16))) return rc;
     if ((rc = dalloc(C, &C->twf, (size_t)MM_TW_ENTRIES * 8))) return rc;
+    if ((rc = dalloc(C, &C->twdd, (size_t)MM_TW_ENTRIES * 16))) return rc;
     if ((rc = dalloc(C, (void**)&C->kvec_dev, 7 * sizeof(void*)))) return rc;
     if ((rc = dalloc(C, (void**)&C->desc_d, C->sims.size() * sizeof(SimDesc)))) return rc;
     if ((rc = dalloc(C, (void**)&C->state_d, C->sims.size() * sizeof(SimState)))) return rc;
@@ -978,7 +985,7 @@ int mm_precompute_demag(mm_ctx* C) {
         }
     }
     engine_set_attributes();
-    launch_twiddles(C->stream, C->twd, C->twf);
+    launch_twiddles(C->stream, C->twd, C->twf, C->twdd);
     upload_gauss_legendre();
     C->launches += 1;
     CK(cudaGetLastError());

@@ -43,6 +43,7 @@ struct Launch {
     ItemSet yzc[kYzcListCount];   // cluster-fused y/z, one list per plane count, groups, CTAs per SM
     size_t smem_x = 0, smem_xi = 0, smem_y13 = 0, smem_z = 0, smem_y2 = 0, smem_yzc = 0;
     int x_threads = 0, col_threads = 0;   // tuned CTA widths of the x and column passes (0: rule)
+    bool dd = false;              // FP64 storage with double-float transforms (tensor, spectrum, tw in dd)
     const void* tensor = nullptr;
     const void* Ms = nullptr;
     const void* cellp = nullptr;  // per-cell A and D blocks
@@ -65,6 +66,10 @@ struct RkBuffers {
 
 template <typename T>
 void engine_rhs(const Launch& L, int mode, const T* m, T* dmdt, T* heff, long long off_adjust);
+// FP64 storage, double-float transforms (engine_dd.cu)
+void engine_rhs_dd(const Launch& L, int mode, const double* m, double* dmdt, double* heff, long long off_adjust);
+void engine_attempt_dd(const Launch& L, const RkBuffers& B);
+void engine_neb_attempt_dd(const Launch& L, const RkBuffers& B);
 template <typename T>
 void engine_attempt(const Launch& L, const RkBuffers& B);
 template <typename T>
@@ -75,7 +80,8 @@ void engine_after_stage1(const Launch& L);
 
 // newell.cu
 void upload_gauss_legendre();
-void launch_twiddles(cudaStream_t s, void* twd, void* twf);
+// FP64, FP32 and double-float (hi, lo pairs of the FP64 values) twiddle tables
+void launch_twiddles(cudaStream_t s, void* twd, void* twf, void* twdd);
 void launch_newell_octant(cudaStream_t s, int nx, int ny, int nz, double dx, double dy, double dz, double* oct);
 void launch_newell_place(cudaStream_t s, const double* oct, int c, int nx, int ny, int nz, int Px, int Py, int Pz,
                          void* buf);
@@ -83,8 +89,9 @@ void launch_fft_axis_f64(cudaStream_t s, void* buf, int Px, int Py, int Pz, int 
 // Ty > 0: the blocked layout of the cluster-fused y/z pass with qp values per bin;
 // nk: kz bins (Pz/2+1) or, for the cluster pass, the nz dz planes of an x-y
 // transformed buffer (imag_xz: xz and yz are imaginary there)
+// out_kind: 0 FP64, 1 FP32, 2 double-float (hi, lo FP32 pairs)
 void launch_newell_extract(cudaStream_t s, const void* buf, int c, int Px, int Py, int Kx, int Pyh, int nk,
-                           double scale, void* out, int is_f32, int Ty, int qp, int imag_xz,
+                           double scale, void* out, int out_kind, int Ty, int qp, int imag_xz,
                            unsigned long long* maxim, unsigned long long* maxre);
 
 }  // namespace mm

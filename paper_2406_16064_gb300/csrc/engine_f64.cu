@@ -8,9 +8,11 @@ template void engine_attempt<double>(const Launch&, const RkBuffers&);
 template void engine_neb_attempt<double>(const Launch&, const RkBuffers&);
 
 void engine_set_attributes_f32();
+void engine_set_attributes_dd();
 void engine_set_attributes() {
     set_attrs<double>();
     engine_set_attributes_f32();
+    engine_set_attributes_dd();
 }
 
 void engine_bounded_wait(cudaStream_t s, int* flag, long long spins, int* status) {

@@ -7,17 +7,20 @@
 
 namespace mm {
 
-template <typename T>
-static PassParams<T> base_params(const Launch& L) {
-    PassParams<T> p;
+// C: compute type of the transforms (float, double or dd); the state pointers
+// of PassParams<C> are of its storage type StoreT<C>.
+template <typename C>
+static PassParams<C> base_params(const Launch& L) {
+    using S = StoreT<C>;
+    PassParams<C> p;
     memset(&p, 0, sizeof(p));
     p.desc = L.desc;
     p.state = L.state;
-    p.spec = reinterpret_cast<V2<T>*>(L.spec);
-    p.tensor = reinterpret_cast<const T*>(L.tensor);
-    p.Ms = reinterpret_cast<const T*>(L.Ms);
-    p.cellp = reinterpret_cast<const T*>(L.cellp);
-    p.tw = reinterpret_cast<const V2<T>*>(L.tw);
+    p.spec = reinterpret_cast<V2<C>*>(L.spec);
+    p.tensor = reinterpret_cast<const C*>(L.tensor);
+    p.Ms = reinterpret_cast<const S*>(L.Ms);
+    p.cellp = reinterpret_cast<const S*>(L.cellp);
+    p.tw = reinterpret_cast<const V2<C>*>(L.tw);
     for (int j = 0; j < 7; ++j) p.e[j] = dp_e(j);
     return p;
 }
@@ -54,7 +57,7 @@ static void (*yzc_kernel(int nz, bool wide, bool occ3 = false))(PassParams<T>) {
 }
 
 template <typename T>
-static void issue_passes(const Launch& L, PassParams<T> p, const T* ys, bool include_xinv = true) {
+static void issue_passes(const Launch& L, PassParams<T> p, const StoreT<T>* ys, bool include_xinv = true) {
     if (L.x.count == 0) return;
     cudaStream_t s = L.stream;
     ProfileHook* hk = L.hook;
@@ -133,36 +136,36 @@ static void issue_passes(const Launch& L, PassParams<T> p, const T* ys, bool inc
     if (L.launches) *L.launches += n;
 }
 
-template <typename T>
-void engine_rhs(const Launch& L, int mode, const T* m, T* dmdt, T* heff, long long off_adjust) {
-    PassParams<T> p = base_params<T>(L);
+template <typename S, typename C>
+void engine_rhs_c(const Launch& L, int mode, const S* m, S* dmdt, S* heff, long long off_adjust) {
+    PassParams<C> p = base_params<C>(L);
     p.mode = mode;
     p.m = m;
     p.kout = dmdt;
     p.heff = heff;
     p.off_adjust = off_adjust;
-    issue_passes<T>(L, p, m);
+    issue_passes<C>(L, p, m);
 }
 
 static inline int blocks_for(int n) { return (n + 127) / 128; }
 
-template <typename T>
-void engine_attempt(const Launch& L, const RkBuffers& B) {
+template <typename S, typename C>
+void engine_attempt_c(const Launch& L, const RkBuffers& B) {
     cudaStream_t s = L.stream;
     for (int st = 1; st <= 7; ++st) {
-        PassParams<T> p = base_params<T>(L);
+        PassParams<C> p = base_params<C>(L);
         p.mode = MODE_RK;
         p.stage = st;
         p.nk = st - 1;
         p.write_y = st > 1;
         for (int j = 0; j < 6; ++j) p.a[j] = dp_a(st, j);
-        p.m = reinterpret_cast<const T*>(B.m);
-        p.ybuf = reinterpret_cast<T*>(B.ybuf);
-        p.kvec = reinterpret_cast<T* const*>(B.kvec_dev);
-        p.kout = reinterpret_cast<T*>(B.kvec[st - 1]);
-        p.errp = reinterpret_cast<T*>(B.errp);
-        const T* ys = st == 1 ? reinterpret_cast<const T*>(B.m) : reinterpret_cast<const T*>(B.ybuf);
-        issue_passes<T>(L, p, ys);
+        p.m = reinterpret_cast<const S*>(B.m);
+        p.ybuf = reinterpret_cast<S*>(B.ybuf);
+        p.kvec = reinterpret_cast<S* const*>(B.kvec_dev);
+        p.kout = reinterpret_cast<S*>(B.kvec[st - 1]);
+        p.errp = reinterpret_cast<S*>(B.errp);
+        const S* ys = st == 1 ? reinterpret_cast<const S*>(B.m) : reinterpret_cast<const S*>(B.ybuf);
+        issue_passes<C>(L, p, ys);
         if (st == 1) {
             k_after_stage1<<<blocks_for(L.nsims), 128, 0, s>>>(L.desc, L.state, L.nsims);
             if (L.hook) L.hook->mark(KIND_CONTROL);
@@ -171,46 +174,46 @@ void engine_attempt(const Launch& L, const RkBuffers& B) {
     }
     k_controller<<<blocks_for(L.nsims), 128, 0, s>>>(L.desc, L.state, L.nsims);
     if (L.hook) L.hook->mark(KIND_CONTROL);
-    k_project<T><<<L.x.count, MM_THREADS, 0, s>>>(L.desc, L.state, L.x.dev, reinterpret_cast<T*>(B.m),
-                                                  reinterpret_cast<const T*>(B.ybuf));
+    k_project<S><<<L.x.count, MM_THREADS, 0, s>>>(L.desc, L.state, L.x.dev, reinterpret_cast<S*>(B.m),
+                                                  reinterpret_cast<const S*>(B.ybuf));
     if (L.hook) L.hook->mark(KIND_PROJECT);
     if (L.launches) *L.launches += 2;
 }
 
-template <typename T>
-void engine_neb_attempt(const Launch& L, const RkBuffers& B) {
+template <typename S, typename C>
+void engine_neb_attempt_c(const Launch& L, const RkBuffers& B) {
     cudaStream_t s = L.stream;
     for (int st = 1; st <= 7; ++st) {
         k_neb_reset<<<blocks_for(L.nsims), 128, 0, s>>>(L.state, L.nsims);
         if (L.hook) L.hook->mark(KIND_CONTROL);
-        PassParams<T> p = base_params<T>(L);
+        PassParams<C> p = base_params<C>(L);
         p.mode = MODE_NEB;
         p.stage = st;
         p.nk = st - 1;
         p.write_y = st > 1;
         for (int j = 0; j < 6; ++j) p.a[j] = dp_a(st, j);
-        p.m = reinterpret_cast<const T*>(B.m);
-        p.ybuf = reinterpret_cast<T*>(B.ybuf);
-        p.kvec = reinterpret_cast<T* const*>(B.kvec_dev);
+        p.m = reinterpret_cast<const S*>(B.m);
+        p.ybuf = reinterpret_cast<S*>(B.ybuf);
+        p.kvec = reinterpret_cast<S* const*>(B.kvec_dev);
         p.kout = nullptr;
-        p.heff = reinterpret_cast<T*>(B.heff);
-        p.errp = reinterpret_cast<T*>(B.errp);
-        const T* ys = st == 1 ? reinterpret_cast<const T*>(B.m) : reinterpret_cast<const T*>(B.ybuf);
-        issue_passes<T>(L, p, ys);
-        NebParams<T> q;
+        p.heff = reinterpret_cast<S*>(B.heff);
+        p.errp = reinterpret_cast<S*>(B.errp);
+        const S* ys = st == 1 ? reinterpret_cast<const S*>(B.m) : reinterpret_cast<const S*>(B.ybuf);
+        issue_passes<C>(L, p, ys);
+        NebParams<S> q;
         q.desc = L.desc;
         q.state = L.state;
         q.items = L.x.dev;
         q.ys = ys;
-        q.heff = reinterpret_cast<const T*>(B.heff);
-        q.tau = reinterpret_cast<T*>(B.tau);
-        q.kout = reinterpret_cast<T*>(B.kvec[st - 1]);
-        q.errp = reinterpret_cast<const T*>(B.errp);
-        q.Ms = reinterpret_cast<const T*>(L.Ms);
+        q.heff = reinterpret_cast<const S*>(B.heff);
+        q.tau = reinterpret_cast<S*>(B.tau);
+        q.kout = reinterpret_cast<S*>(B.kvec[st - 1]);
+        q.errp = reinterpret_cast<const S*>(B.errp);
+        q.Ms = reinterpret_cast<const S*>(L.Ms);
         q.stage = st;
         q.e7 = dp_e(6);
-        k_neb_tangent<T><<<L.x.count, MM_THREADS, 0, s>>>(q);
-        k_neb_force<T><<<L.x.count, MM_THREADS, 0, s>>>(q);
+        k_neb_tangent<S><<<L.x.count, MM_THREADS, 0, s>>>(q);
+        k_neb_force<S><<<L.x.count, MM_THREADS, 0, s>>>(q);
         if (L.hook) L.hook->mark(KIND_NEB);
         if (L.launches) *L.launches += 3;
         if (st == 1) {
@@ -221,10 +224,36 @@ void engine_neb_attempt(const Launch& L, const RkBuffers& B) {
     }
     k_controller<<<blocks_for(L.nsims), 128, 0, s>>>(L.desc, L.state, L.nsims);
     if (L.hook) L.hook->mark(KIND_CONTROL);
-    k_project<T><<<L.x.count, MM_THREADS, 0, s>>>(L.desc, L.state, L.x.dev, reinterpret_cast<T*>(B.m),
-                                                  reinterpret_cast<const T*>(B.ybuf));
+    k_project<S><<<L.x.count, MM_THREADS, 0, s>>>(L.desc, L.state, L.x.dev, reinterpret_cast<S*>(B.m),
+                                                  reinterpret_cast<const S*>(B.ybuf));
     if (L.hook) L.hook->mark(KIND_PROJECT);
     if (L.launches) *L.launches += 2;
+}
+
+// The entry points, per storage type.  An FP64 launch with Launch::dd set runs its
+// transforms in double-float (engine_dd.cu); everything else in the storage type.
+template <typename S>
+void engine_rhs(const Launch& L, int mode, const S* m, S* dmdt, S* heff, long long off_adjust) {
+    if constexpr (sizeof(S) == 8) {
+        if (L.dd) { engine_rhs_dd(L, mode, m, dmdt, heff, off_adjust); return; }
+    }
+    engine_rhs_c<S, S>(L, mode, m, dmdt, heff, off_adjust);
+}
+
+template <typename S>
+void engine_attempt(const Launch& L, const RkBuffers& B) {
+    if constexpr (sizeof(S) == 8) {
+        if (L.dd) { engine_attempt_dd(L, B); return; }
+    }
+    engine_attempt_c<S, S>(L, B);
+}
+
+template <typename S>
+void engine_neb_attempt(const Launch& L, const RkBuffers& B) {
+    if constexpr (sizeof(S) == 8) {
+        if (L.dd) { engine_neb_attempt_dd(L, B); return; }
+    }
+    engine_neb_attempt_c<S, S>(L, B);
 }
 
 template <typename T>

@@ -21,6 +21,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "ddf.cuh"
+
 #define MM_LOG2_LMAX 13
 #define MM_LMAX (1 << MM_LOG2_LMAX)
 #define MM_THREADS 256
@@ -571,8 +573,13 @@ __host__ __device__ constexpr double dp_e(int j) {
 // Parameters of every pass kernel (passed by value).
 enum { MODE_RHS = 0, MODE_RK = 1, MODE_ENERGY = 2, MODE_NEB = 3 };
 
+// T: the type the transforms compute in (float, double, or dd for FP64
+// contexts); S = StoreT<T>: the type of the state, stage vectors, fields, Ms and
+// per-cell constants in memory (float or double).  The spectrum, tensor and
+// twiddles are stored in T.
 template <typename T>
 struct PassParams {
+    using S = StoreT<T>;
     const SimDesc* __restrict__ desc;
     SimState* state;
     const WorkItem* __restrict__ items;
@@ -582,18 +589,18 @@ struct PassParams {
     int write_y;            // prologue writes the stage state
     double a[7];            // RK coefficients a_{s,j}
     double e[7];            // error coefficients (stage 7)
-    const T* m;             // y_n (MODE_RK) or the evaluated state (other modes)
-    T* ybuf;                // stage state
-    T* const* kvec;         // k_1..k_7 (device array of 7 pointers)
-    T* kout;                // k_s / dm/dt output
-    T* heff;                // optional H_eff output
-    T* errp;                // partial error vector (stage 7)
+    const S* m;             // y_n (MODE_RK) or the evaluated state (other modes)
+    S* ybuf;                // stage state
+    S* const* kvec;         // k_1..k_7 (device array of 7 pointers)
+    S* kout;                // k_s / dm/dt output
+    S* heff;                // optional H_eff output
+    S* errp;                // partial error vector (stage 7)
     long long off_adjust;   // subtracted from SimDesc::off for caller buffers of one simulation
     V2<T>* spec;
     const T* __restrict__ tensor;
-    const T* __restrict__ Ms;
+    const S* __restrict__ Ms;
     const V2<T>* __restrict__ tw;
-    const T* __restrict__ cellp;   // per-cell A and D blocks (SimDesc::cell_off)
+    const S* __restrict__ cellp;   // per-cell A and D blocks (SimDesc::cell_off)
 };
 
 // Asynchronous 16-byte global -> shared copies (cp.async, L2 only): a CTA

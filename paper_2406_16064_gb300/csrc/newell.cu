@@ -243,7 +243,7 @@ __global__ void k_newell_extract(const double2* __restrict__ buf, int c, int Px,
         const double keep = im ? v.y : v.x, drop = im ? v.x : v.y;
         const long long o = Ty > 0 ? (((long long)(kx / Ty) * Pyh + ky) * Ty + kx % Ty) * qp + 6 * kz + c
                                    : (long long)c * tot + id;
-        out[o] = (T)(-keep * scale);
+        out[o] = T(-keep * scale);
         atomicMax(maxim, (unsigned long long)__double_as_longlong(fabs(drop)));
         atomicMax(maxre, (unsigned long long)__double_as_longlong(fabs(keep)));
     }
@@ -252,11 +252,13 @@ template __global__ void k_newell_extract<float>(const double2*, int, int, int, 
                                                   int, int, int, unsigned long long*, unsigned long long*);
 template __global__ void k_newell_extract<double>(const double2*, int, int, int, int, int, int, double, double*,
                                                    int, int, int, unsigned long long*, unsigned long long*);
+template __global__ void k_newell_extract<dd>(const double2*, int, int, int, int, int, int, double, dd*,
+                                               int, int, int, unsigned long long*, unsigned long long*);
 
 // twiddle tables: exp(-2 pi i k / LMAX) for k < LMAX, then the stage tables
 // W_M^(k r) (layout: stw_base in mm_kernels.cuh), all from FP64 sincospi of the
 // exact fraction 2 (k r mod M) / M
-__global__ void k_twiddles(V2<double>* twd, V2<float>* twf) {
+__global__ void k_twiddles(V2<double>* twd, V2<float>* twf, V2<dd>* twdd) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < MM_TW_ENTRIES; i += gridDim.x * blockDim.x) {
         long long num;
         int lM;
@@ -278,6 +280,7 @@ __global__ void k_twiddles(V2<double>* twd, V2<float>* twf) {
         sincospi(2.0 * (double)num / (double)(1LL << lM), &s, &c);
         twd[i].x = c; twd[i].y = -s;
         twf[i].x = (float)c; twf[i].y = (float)-s;
+        if (twdd) { twdd[i].x = dd(c); twdd[i].y = dd(-s); }
     }
 }
 
@@ -317,8 +320,9 @@ void upload_gauss_legendre() {
 }
 
 // ---- launch wrappers ------------------------------------------------------
-void launch_twiddles(cudaStream_t s, void* twd, void* twf) {
-    k_twiddles<<<32, 256, 0, s>>>(reinterpret_cast<V2<double>*>(twd), reinterpret_cast<V2<float>*>(twf));
+void launch_twiddles(cudaStream_t s, void* twd, void* twf, void* twdd) {
+    k_twiddles<<<32, 256, 0, s>>>(reinterpret_cast<V2<double>*>(twd), reinterpret_cast<V2<float>*>(twf),
+                                  reinterpret_cast<V2<dd>*>(twdd));
 }
 
 void launch_newell_octant(cudaStream_t s, int nx, int ny, int nz, double dx, double dy, double dz, double* oct) {
@@ -362,15 +366,18 @@ void launch_fft_axis_f64(cudaStream_t s, void* buf, int Px, int Py, int Pz, int 
 }
 
 void launch_newell_extract(cudaStream_t s, const void* buf, int c, int Px, int Py, int Kx, int Pyh, int nk,
-                           double scale, void* out, int is_f32, int Ty, int qp, int imag_xz,
+                           double scale, void* out, int out_kind, int Ty, int qp, int imag_xz,
                            unsigned long long* maxim, unsigned long long* maxre) {
     const long long n = (long long)Kx * Pyh * nk;
     const long long blocks = (n + 255) / 256;
     const int g = (int)(blocks < 1048576 ? blocks : 1048576);
-    if (is_f32)
+    if (out_kind == 1)
         k_newell_extract<float><<<g, 256, 0, s>>>(reinterpret_cast<const double2*>(buf), c, Px, Py, Kx, Pyh, nk,
                                                    scale, reinterpret_cast<float*>(out), Ty, qp, imag_xz, maxim,
                                                    maxre);
+    else if (out_kind == 2)
+        k_newell_extract<dd><<<g, 256, 0, s>>>(reinterpret_cast<const double2*>(buf), c, Px, Py, Kx, Pyh, nk,
+                                                scale, reinterpret_cast<dd*>(out), Ty, qp, imag_xz, maxim, maxre);
     else
         k_newell_extract<double><<<g, 256, 0, s>>>(reinterpret_cast<const double2*>(buf), c, Px, Py, Kx, Pyh, nk,
                                                     scale, reinterpret_cast<double*>(out), Ty, qp, imag_xz, maxim,

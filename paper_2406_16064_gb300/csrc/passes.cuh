@@ -87,6 +87,7 @@ __device__ __forceinline__ bool sim_inactive(const PassParams<T>& p, int sim) {
 // constants, so zero ones vanish and the stage vectors' loads issue together.
 template <typename T, int S>
 __global__ void __launch_bounds__(MM_XTHREADS_MAX<T>, 1) k_xfwd(PassParams<T> p) {
+    using R = StoreT<T>;                         // the RK prologue runs in the storage type
     extern __shared__ __align__(16) unsigned char smraw[];
     const WorkItem w = p.items[blockIdx.x];
     if (sim_inactive(p, w.sim)) return;
@@ -102,8 +103,8 @@ __global__ void __launch_bounds__(MM_XTHREADS_MAX<T>, 1) k_xfwd(PassParams<T> p)
     const long long base = d.off - p.off_adjust + (long long)row0 * nx;   // first cell of the tile
     const bool demag = (d.flags & F_DEMAG) != 0;
     const bool msarr = (d.flags & F_MSARR) != 0;
-    const T hstep = (T)((p.mode == MODE_RK || p.mode == MODE_NEB) ? p.state[w.sim].h : 0.0);
-    const T* __restrict__ msp = msarr ? p.Ms + d.ms_off + (long long)row0 * nx : nullptr;
+    const R hstep = (R)((p.mode == MODE_RK || p.mode == MODE_NEB) ? p.state[w.sim].h : 0.0);
+    const R* __restrict__ msp = msarr ? p.Ms + d.ms_off + (long long)row0 * nx : nullptr;
     // z[n] = M[2n] + i M[2n+1] is non-zero for n < ceil(nx/2) <= Lh/2 (Lh >= nx): only the
     // lower half of each sequence is stored, the first FFT stage does not read the upper half
     const int lhalf = lLh > 0 ? lLh - 1 : 0;
@@ -118,16 +119,16 @@ __global__ void __launch_bounds__(MM_XTHREADS_MAX<T>, 1) k_xfwd(PassParams<T> p)
             const int x = 2 * n + h2;
             if (x < nx) {
                 const int cell = r * nx + x;                   // within the tile
-                T yv[3];
+                R yv[3];
 #pragma unroll
                 for (int c = 0; c < 3; ++c) yv[c] = p.m[base + c * N + cell];
                 if (S >= 2) {
-                    T acc[3] = {(T)0, (T)0, (T)0};
+                    R acc[3] = {(R)0, (R)0, (R)0};
 #pragma unroll
                     for (int j = 0; j < S - 1; ++j) {
                         if (dp_a(S, j) != 0.0) {
-                            const T aj = (T)dp_a(S, j);
-                            const T* kj = p.kvec[j] + base + cell;
+                            const R aj = (R)dp_a(S, j);
+                            const R* kj = p.kvec[j] + base + cell;
 #pragma unroll
                             for (int c = 0; c < 3; ++c) acc[c] += aj * kj[c * N];
                         }
@@ -137,12 +138,12 @@ __global__ void __launch_bounds__(MM_XTHREADS_MAX<T>, 1) k_xfwd(PassParams<T> p)
 #pragma unroll
                     for (int c = 0; c < 3; ++c) p.ybuf[base + c * N + cell] = yv[c];
                     if (S == 7) {
-                        T ev[3] = {(T)0, (T)0, (T)0};
+                        R ev[3] = {(R)0, (R)0, (R)0};
 #pragma unroll
                         for (int j = 0; j < 6; ++j) {
                             if (dp_e(j) != 0.0) {
-                                const T ej = (T)dp_e(j);
-                                const T* kj = p.kvec[j] + base + cell;
+                                const R ej = (R)dp_e(j);
+                                const R* kj = p.kvec[j] + base + cell;
 #pragma unroll
                                 for (int c = 0; c < 3; ++c) ev[c] += ej * kj[c * N];
                             }
@@ -152,10 +153,11 @@ __global__ void __launch_bounds__(MM_XTHREADS_MAX<T>, 1) k_xfwd(PassParams<T> p)
                     }
                 }
                 if (demag) {
-                    const T ms = msarr ? msp[cell] : coef<T>(d).Ms;
+                    const R ms = msarr ? msp[cell] : coef<R>(d).Ms;
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
-                        if (h2 == 0) val[c].x = ms * yv[c]; else val[c].y = ms * yv[c];
+                        const T mc = to_compute<T>(ms * yv[c]);
+                        if (h2 == 0) val[c].x = mc; else val[c].y = mc;
                     }
                 }
             }
@@ -389,6 +391,16 @@ __device__ __forceinline__ void load_bin(const double* __restrict__ q, double (&
     }
 }
 
+template <int QP>
+__device__ __forceinline__ void load_bin(const dd* __restrict__ q, dd (&v)[QP]) {
+    const float4* q4 = reinterpret_cast<const float4*>(q);
+#pragma unroll
+    for (int i = 0; i < QP / 2; ++i) {
+        const float4 t = __ldg(q4 + i);
+        v[2 * i] = dd(t.x, t.y); v[2 * i + 1] = dd(t.z, t.w);
+    }
+}
+
 // z step of the cluster pass: for every (ky row, kx column) of this CTA's
 // share, gather the NZ planes' values from the cluster's shared memories and
 // convolve along z directly, H(z) = sum_z' N^(kx, ky, z - z') M(z') (Eq. 8 with
@@ -457,6 +469,36 @@ __device__ void yzc_zstep(const PassParams<T>& p, const SimDesc& d, V2<T>* const
             for (int z = 0; z < NZ; ++z) {
 #pragma unroll
                 for (int c = 0; c < 3; ++c) rem[z][o + c * TT] = H[z][c];
+            }
+            continue;
+        }
+        if constexpr (sizeof(T) == 8) {
+            // 8-byte types (FP64, double-float): one output plane at a time, each offset's
+            // six tensor values loaded where they are used (L1), so the NZ planes of M and
+            // one plane of accumulators are what stays in registers (the plane loop is not
+            // unrolled, so no other plane's tensor loads are hoisted next to it)
+#pragma unroll 1
+            for (int z = 0; z < NZ; ++z) {
+                V2<T> H0 = mk<T>((T)0, (T)0), H1 = H0, H2 = H0;
+#pragma unroll
+                for (int z2 = 0; z2 < NZ; ++z2) {
+                    const int dz = z - z2 >= 0 ? z - z2 : z2 - z;
+                    const T so = z - z2 >= 0 ? (T)1 : (T)-1;    // xz, yz odd in z
+                    T t[6];
+                    load_bin<6>(tq + 6 * dz, t);
+                    const T xx = t[0], yy = t[1], zz = t[2], xy = sy * t[3];
+                    const T xz = so * t[4], yz = so * sy * t[5];
+                    const V2<T> a = M[z2][0], bb = M[z2][1], c = M[z2][2];
+                    H0.x += xx * a.x + xy * bb.x - xz * c.y;
+                    H0.y += xx * a.y + xy * bb.y + xz * c.x;
+                    H1.x += xy * a.x + yy * bb.x - yz * c.y;
+                    H1.y += xy * a.y + yy * bb.y + yz * c.x;
+                    H2.x += zz * c.x - xz * a.y - yz * bb.y;
+                    H2.y += zz * c.y + xz * a.x + yz * bb.x;
+                }
+                rem[z][o] = H0;
+                rem[z][o + TT] = H1;
+                rem[z][o + 2 * TT] = H2;
             }
             continue;
         }
@@ -577,7 +619,8 @@ __device__ __forceinline__ unsigned long long block_max_u64(unsigned long long v
 // EXT: the extended variant, launched when some simulation of the batch has
 // F_EXT (ext_terms.cuh); its other simulations take the standard path.
 template <typename T, bool ENERGY, bool EXT>
-__global__ void __launch_bounds__(MM_XTHREADS_MAX<T>, 1) k_xinv(PassParams<T> p, const T* __restrict__ ys) {
+__global__ void __launch_bounds__(MM_XTHREADS_MAX<T>, 1) k_xinv(PassParams<T> p, const StoreT<T>* __restrict__ ys) {
+    using R = StoreT<T>;                         // the epilogue runs in the storage type
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ unsigned long long red_u[32];
     __shared__ double red_e[ENERGY ? 6 * 32 : 1];
@@ -655,65 +698,65 @@ __global__ void __launch_bounds__(MM_XTHREADS_MAX<T>, 1) k_xinv(PassParams<T> p,
 
     // per-cell local fields and torque; coefficients precomputed in the context
     // precision (no FP64 arithmetic per thread in an FP32 context)
-    const Coef<T>& cf = coef<T>(d);
-    const T mu0 = cf.mu0, inv_u = cf.inv_u;
-    const T ex_x = cf.ex[0], ex_y = cf.ex[1], ex_z = cf.ex[2];
-    const T dm_x = cf.dm[0], dm_y = cf.dm[1];
-    const T cA = cf.cA, cD = cf.cD, cK = cf.cK, cC = cf.cC;
-    const T ux = cf.u[0], uy = cf.u[1], uz = cf.u[2];
-    const T Hx0 = cf.H[0], Hy0 = cf.H[1], Hz0 = cf.H[2];
-    const T gt = cf.gt, agt = cf.agt, Msu = cf.Ms;
+    const Coef<R>& cf = coef<R>(d);
+    const R mu0 = cf.mu0, inv_u = cf.inv_u;
+    const R ex_x = cf.ex[0], ex_y = cf.ex[1], ex_z = cf.ex[2];
+    const R dm_x = cf.dm[0], dm_y = cf.dm[1];
+    const R cA = cf.cA, cD = cf.cD, cK = cf.cK, cC = cf.cC;
+    const R ux = cf.u[0], uy = cf.u[1], uz = cf.u[2];
+    const R Hx0 = cf.H[0], Hy0 = cf.H[1], Hz0 = cf.H[2];
+    const R gt = cf.gt, agt = cf.agt, Msu = cf.Ms;
     const bool prec = (d.flags & F_PREC) != 0;
     const bool dmi = (d.flags & F_DMI) != 0;
     const bool do_ex = (d.flags & F_EX) != 0, do_uni = (d.flags & F_UNI) != 0, do_cub = (d.flags & F_CUB) != 0;
     const bool write_k = !ENERGY;
-    const T* __restrict__ m0p = ys + tile;
-    const T* __restrict__ m1p = m0p + N;
-    const T* __restrict__ m2p = m1p + N;
+    const R* __restrict__ m0p = ys + tile;
+    const R* __restrict__ m1p = m0p + N;
+    const R* __restrict__ m2p = m1p + N;
     const int sz = nx * ny;
-    const T* __restrict__ msp = msarr ? p.Ms + d.ms_off + (long long)row0 * nx : nullptr;
+    const R* __restrict__ msp = msarr ? p.Ms + d.ms_off + (long long)row0 * nx : nullptr;
     const bool ext = EXT && (d.flags & F_EXT) != 0;
-    const T* __restrict__ acp = (ext && (d.eflags & E_CELL)) ? p.cellp + d.cell_off + (long long)row0 * nx : nullptr;
-    const T* __restrict__ dcp = acp ? acp + N : nullptr;
-    const T e7 = (T)dp_e(6);
+    const R* __restrict__ acp = (ext && (d.eflags & E_CELL)) ? p.cellp + d.cell_off + (long long)row0 * nx : nullptr;
+    const R* __restrict__ dcp = acp ? acp + N : nullptr;
+    const R e7 = (R)dp_e(6);
     const bool red1 = !ENERGY && p.mode == MODE_RK && p.stage == 1;
     const bool red7 = !ENERGY && p.mode == MODE_RK && p.stage == 7;
     unsigned long long vmax = 0ull;
-    CSum<T> esum[6];
+    CSum<R> esum[6];
     for (int r = 0; r < nrows; ++r) {
         const int y = y0 + r, z = z0;
         for (int x = threadIdx.x; x < nx; x += blockDim.x) {
             const int cell = r * nx + x;                     // within the tile
-            const T m0 = m0p[cell], m1 = m1p[cell], m2 = m2p[cell];
-            const T ms = msarr ? msp[cell] : Msu;
-            T H0 = 0, H1 = 0, H2 = 0, k0 = 0, k1 = 0, k2 = 0;
-            if (ms > (T)0) {
-                const T inv = msarr ? (T)1 / (mu0 * ms) : inv_u;
-                T hd0 = 0, hd1 = 0, hd2 = 0;
+            const R m0 = m0p[cell], m1 = m1p[cell], m2 = m2p[cell];
+            const R ms = msarr ? msp[cell] : Msu;
+            R H0 = 0, H1 = 0, H2 = 0, k0 = 0, k1 = 0, k2 = 0;
+            if (ms > (R)0) {
+                const R inv = msarr ? (R)1 / (mu0 * ms) : inv_u;
+                R hd0 = 0, hd1 = 0, hd2 = 0;
                 if (demag) {
                     const int pos = ix<true>(x >> 1, 1);
                     const V2<T> v0 = Hd[(3 * r + 0) * SK + pos];
                     const V2<T> v1 = Hd[(3 * r + 1) * SK + pos];
                     const V2<T> v2 = Hd[(3 * r + 2) * SK + pos];
-                    hd0 = (x & 1) ? v0.y : v0.x;
-                    hd1 = (x & 1) ? v1.y : v1.x;
-                    hd2 = (x & 1) ? v2.y : v2.x;
+                    hd0 = to_store<T>((x & 1) ? v0.y : v0.x);
+                    hd1 = to_store<T>((x & 1) ? v1.y : v1.x);
+                    hd2 = to_store<T>((x & 1) ? v2.y : v2.x);
                 }
                 // exchange (Eq. 5) and interfacial DMI (Eq. 14), free boundaries.  The six
                 // neighbours are loaded unconditionally (a missing one reads the cell
                 // itself) and masked afterwards, so all loads can be in flight together.
-                T ex0 = 0, ex1 = 0, ex2 = 0, dm0 = 0, dm1 = 0, dm2 = 0;
-                T gv[3] = {(T)0, (T)0, (T)0};                 // (u.grad)m, extended terms
+                R ex0 = 0, ex1 = 0, ex2 = 0, dm0 = 0, dm1 = 0, dm2 = 0;
+                R gv[3] = {(R)0, (R)0, (R)0};                 // (u.grad)m, extended terms
                 if (ext) {
-                    T exv[3] = {(T)0, (T)0, (T)0}, dmv[3] = {(T)0, (T)0, (T)0};
-                    ext_local<T>(d, cf, ext_coef<T>(d), m0p, m1p, m2p, msp, acp, dcp, cell, x, y, z, m0, m1, m2,
+                    R exv[3] = {(R)0, (R)0, (R)0}, dmv[3] = {(R)0, (R)0, (R)0};
+                    ext_local<R>(d, cf, ext_coef<R>(d), m0p, m1p, m2p, msp, acp, dcp, cell, x, y, z, m0, m1, m2,
                                  inv, exv, dmv, gv);
                     ex0 = exv[0]; ex1 = exv[1]; ex2 = exv[2];
                     dm0 = dmv[0]; dm1 = dmv[1]; dm2 = dmv[2];
                 } else if (do_ex || dmi) {
                     bool ok[6] = {x > 0, x < nx - 1, y > 0, y < ny - 1, z > 0, z < nz - 1};
                     const int off[6] = {-1, 1, -nx, nx, -sz, sz};
-                    T j0[6], j1[6], j2[6];
+                    R j0[6], j1[6], j2[6];
 #pragma unroll
                     for (int nb = 0; nb < 6; ++nb) {
                         const int o = cell + (ok[nb] ? off[nb] : 0);
@@ -721,13 +764,13 @@ __global__ void __launch_bounds__(MM_XTHREADS_MAX<T>, 1) k_xinv(PassParams<T> p,
                     }
                     if (msarr) {
 #pragma unroll
-                        for (int nb = 0; nb < 6; ++nb) ok[nb] = ok[nb] && msp[cell + (ok[nb] ? off[nb] : 0)] > (T)0;
+                        for (int nb = 0; nb < 6; ++nb) ok[nb] = ok[nb] && msp[cell + (ok[nb] ? off[nb] : 0)] > (R)0;
                     }
                     if (do_ex) {
-                        const T fe[6] = {ex_x, ex_x, ex_y, ex_y, ex_z, ex_z};
+                        const R fe[6] = {ex_x, ex_x, ex_y, ex_y, ex_z, ex_z};
 #pragma unroll
                         for (int nb = 0; nb < 6; ++nb) {
-                            const T f = ok[nb] ? fe[nb] : (T)0;
+                            const R f = ok[nb] ? fe[nb] : (R)0;
                             ex0 += f * (j0[nb] - m0); ex1 += f * (j1[nb] - m1); ex2 += f * (j2[nb] - m2);
                         }
                         ex0 *= cA * inv; ex1 *= cA * inv; ex2 *= cA * inv;
@@ -735,22 +778,22 @@ __global__ void __launch_bounds__(MM_XTHREADS_MAX<T>, 1) k_xinv(PassParams<T> p,
                     if (dmi) {
                         // sum_j e_ij x m_j / Delta: -x:-e_y, +x:+e_y, -y:+e_x, +y:-e_x;
                         // e_y x m = (mz, 0, -mx), e_x x m = (0, -mz, my)
-                        const T sxm = ok[0] ? -dm_x : (T)0, sxp = ok[1] ? dm_x : (T)0;
-                        const T sym = ok[2] ? dm_y : (T)0, syp = ok[3] ? -dm_y : (T)0;
+                        const R sxm = ok[0] ? -dm_x : (R)0, sxp = ok[1] ? dm_x : (R)0;
+                        const R sym = ok[2] ? dm_y : (R)0, syp = ok[3] ? -dm_y : (R)0;
                         dm0 = sxm * j2[0] + sxp * j2[1];
                         dm2 = -(sxm * j0[0] + sxp * j0[1]) + sym * j1[2] + syp * j1[3];
                         dm1 = -(sym * j2[2] + syp * j2[3]);
                         dm0 *= -cD * inv; dm1 *= -cD * inv; dm2 *= -cD * inv;
                     }
                 }
-                T un0 = 0, un1 = 0, un2 = 0, cu0 = 0, cu1 = 0, cu2 = 0;
+                R un0 = 0, un1 = 0, un2 = 0, cu0 = 0, cu1 = 0, cu2 = 0;
                 if (do_uni) {
-                    const T mu = m0 * ux + m1 * uy + m2 * uz;
-                    const T f = cK * inv * mu;
+                    const R mu = m0 * ux + m1 * uy + m2 * uz;
+                    const R f = cK * inv * mu;
                     un0 = f * ux; un1 = f * uy; un2 = f * uz;
                 }
                 if (do_cub) {
-                    const T f = -cC * inv;
+                    const R f = -cC * inv;
                     cu0 = f * m0 * m0 * m0; cu1 = f * m1 * m1 * m1; cu2 = f * m2 * m2 * m2;
                 }
                 H0 = hd0 + ex0 + dm0 + un0 + cu0 + Hx0;
@@ -762,19 +805,19 @@ __global__ void __launch_bounds__(MM_XTHREADS_MAX<T>, 1) k_xinv(PassParams<T> p,
                     // threads in FP64; the constant factors are applied once per CTA
                     esum[0].add(ms * (m0 * ex0 + m1 * ex1 + m2 * ex2));
                     esum[1].add(ms * (m0 * dm0 + m1 * dm1 + m2 * dm2));
-                    const T mu = m0 * ux + m1 * uy + m2 * uz;
+                    const R mu = m0 * ux + m1 * uy + m2 * uz;
                     esum[2].add(mu * mu);
-                    const T q0 = m0 * m0, q1 = m1 * m1, q2 = m2 * m2;
+                    const R q0 = m0 * m0, q1 = m1 * m1, q2 = m2 * m2;
                     esum[3].add(q0 * q0 + q1 * q1 + q2 * q2);
                     esum[4].add(ms * (m0 * Hx0 + m1 * Hy0 + m2 * Hz0));
                     esum[5].add(ms * (m0 * hd0 + m1 * hd1 + m2 * hd2));
                 }
                 // LL form: dm/dt = -g~ m x H - alpha g~ m x (m x H)
-                const T c0 = m1 * H2 - m2 * H1, c1 = m2 * H0 - m0 * H2, c2 = m0 * H1 - m1 * H0;
-                const T dd0 = m1 * c2 - m2 * c1, dd1 = m2 * c0 - m0 * c2, dd2 = m0 * c1 - m1 * c0;
+                const R c0 = m1 * H2 - m2 * H1, c1 = m2 * H0 - m0 * H2, c2 = m0 * H1 - m1 * H0;
+                const R dd0 = m1 * c2 - m2 * c1, dd1 = m2 * c0 - m0 * c2, dd2 = m0 * c1 - m1 * c0;
                 k0 = -agt * dd0; k1 = -agt * dd1; k2 = -agt * dd2;
                 if (prec) { k0 -= gt * c0; k1 -= gt * c1; k2 -= gt * c2; }
-                if (ext && (d.eflags & (E_STT | E_SOT))) ext_torque<T>(d, ext_coef<T>(d), m0, m1, m2, gv, k0, k1, k2);
+                if (ext && (d.eflags & (E_STT | E_SOT))) ext_torque<R>(d, ext_coef<R>(d), m0, m1, m2, gv, k0, k1, k2);
             }
             const long long o = tile + cell;
             if (write_k) {
@@ -792,7 +835,7 @@ __global__ void __launch_bounds__(MM_XTHREADS_MAX<T>, 1) k_xinv(PassParams<T> p,
                 // prologue, plus e_7 k_7 in one correctly rounded FMA; h is applied
                 // after the max (rounded scaling by h > 0 is monotone, so
                 // max_i h|v_i| = h max_i |v_i| exactly)
-                const T* ep = p.errp + o;
+                const R* ep = p.errp + o;
                 vmax = umax64(vmax, obits(fabs(fma(e7, k0, ep[0]))));
                 vmax = umax64(vmax, obits(fabs(fma(e7, k1, ep[N]))));
                 vmax = umax64(vmax, obits(fabs(fma(e7, k2, ep[2 * N]))));
@@ -803,7 +846,7 @@ __global__ void __launch_bounds__(MM_XTHREADS_MAX<T>, 1) k_xinv(PassParams<T> p,
         const unsigned long long rr = block_max_u64(vmax, red_u);
         if (threadIdx.x == 0) {
             // FP64 from here on: the CTA maximum, scaled by h at stage 7
-            const double v = obits_to_double<T>(rr);
+            const double v = obits_to_double<R>(rr);
             const double vs = red7 ? fabs(p.state[w.sim].h * v) : v;
             atomicMax(red1 ? &p.state[w.sim].maxk_bits : &p.state[w.sim].err_bits,
                       (unsigned long long)__double_as_longlong(vs));

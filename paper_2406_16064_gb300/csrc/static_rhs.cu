@@ -224,7 +224,7 @@ extern "C" int mm_rhs_eval_static(const mm_mesh* mesh, const mm_material* mat, i
     SCK(up(o_z, P.z));
     SCK(up(o_y2, P.y2));
     SCK(up(o_yz, yzv));
-    launch_twiddles(s, base + o_twd, base + o_twf);
+    launch_twiddles(s, base + o_twd, base + o_twf, nullptr);   // native FP64 / FP32 transforms here
     upload_gauss_legendre();
     engine_set_attributes();
     SCK(cudaGetLastError());

@@ -17,7 +17,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libmm.so")
 
 MM_OK, MM_EINVAL, MM_ENOMEM, MM_ECUDA, MM_ENAN, MM_ESTEP, MM_ETIMEOUT, MM_EBOUNDS = 0, -1, -2, -3, -4, -5, -6, -7
-MM_F64, MM_F32 = 0, 1
+MM_F64, MM_F32, MM_F64_NATIVE = 0, 1, 2
+PRECISIONS = {"f64": MM_F64, "f32": MM_F32, "f64_native": MM_F64_NATIVE}
 MM_HOST, MM_DEVICE = 0, 1
 ENERGY_TERMS = ("exchange", "dmi", "uniaxial", "cubic", "zeeman", "demag", "total")
 
@@ -134,9 +135,12 @@ class Context:
     def __init__(self, precision="f64", device=0, stream=None):
         self.L = lib()
         self.precision = precision
-        self.dtype = np.float64 if precision == "f64" else np.float32
+        if precision not in PRECISIONS:
+            raise ValueError(f"precision must be one of {sorted(PRECISIONS)}")
+        # f64: FP64 state, double-float transforms; f64_native: FP64 arithmetic throughout
+        self.dtype = np.float32 if precision == "f32" else np.float64
         h = _P()
-        rc = self.L.mm_create(C.byref(h), device, MM_F64 if precision == "f64" else MM_F32,
+        rc = self.L.mm_create(C.byref(h), device, PRECISIONS[precision],
                               _P(stream) if stream else None)
         if rc != MM_OK:
             raise MMError(rc, self.L.mm_last_error(None).decode())
