@@ -19,6 +19,9 @@ It is plain, slow and written to be checked by eye against the paper
              descent energy minimization")
   cayley     fixed-step classical Runge-Kutta with projection and on the
              Cayley-transform variable (Sec. "Cayley transform")
+  potential  the demag field through the magnetic scalar potential (the
+             three-forward, one-inverse transform variant named in Sec.
+             "Magnetostatic energy")
 
 All arithmetic is float64.  Parity status of every function is listed in
 its module header.
