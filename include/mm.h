@@ -136,9 +136,10 @@ int mm_num_sims(const mm_ctx *ctx);
  *               than 8 planes (same limits)
  *   col_group   cluster pass (2..8 planes): column FFT stages per register
  *               group, 1 = 16-point groups, 2 = 32-point groups
- *   col_occ     cluster pass: CTAs per SM its kernel is built for, 3 (FP32 up
- *               to 4 planes, column tiles small enough for three CTAs' shared
- *               memory; fewer registers a thread) or 0 / 2 (the rule)
+ *   col_occ     cluster pass: CTAs per SM its kernel is built for, 3 or 4 (FP32
+ *               up to 4 planes, column tiles small enough for that many CTAs'
+ *               shared memory; fewer registers a thread, and 8-point column
+ *               groups at 4) or 0 / 2 (the rule)
  * The two CTA widths act per launch, which covers the whole batch: they apply
  * when every simulation of the context has the same value (else the rule). */
 typedef struct { int Ty, Rx, x_threads, col_threads, col_group, col_occ; } mm_tuning;

@@ -615,7 +615,7 @@ Tuning from_abi(const mm_tuning& t) {
 int apply_tuning(mm_ctx* C, SimHost& s, const Tuning& t) {
     const bool f32 = C->precision == MM_F32;
     if (t.Ty < 0 || t.Rx < 0 || t.x_threads < 0 || t.col_threads < 0 || t.col_group < 0 || t.col_group > 2 ||
-        (t.col_occ != 0 && t.col_occ != 2 && t.col_occ != 3))
+        (t.col_occ != 0 && t.col_occ != 2 && t.col_occ != 3 && t.col_occ != 4))
         return fail(C, MM_EINVAL, "mm_set_tuning: negative or unknown value");
     if (t.Ty > 32 || (t.Ty & (t.Ty - 1))) return fail(C, MM_EINVAL, "mm_set_tuning: Ty must be a power of two <= 32");
     SimDesc d = s.d;
@@ -643,7 +643,7 @@ mm_tuning resolved_tuning(const mm_ctx* C, const SimHost& s) {
     const size_t sc = std::max(P.smem_y13, std::max(P.smem_z, P.smem_y2));
     r.col_threads = s.tune.col_threads ? s.tune.col_threads : (sc ? plan_wide_threads(sc, maxth) : 0);
     r.col_group = plan_uses_yzc(s.d) ? (plan_yzc_wide(plan_yzc_list(s.d, f32)) ? 2 : 1) : 0;
-    r.col_occ = (plan_uses_yzc(s.d) && s.d.yzcocc == 3) ? 3 : 0;
+    r.col_occ = plan_uses_yzc(s.d) ? s.d.yzcocc : 0;
     return r;
 }
 

@@ -35,14 +35,21 @@ static int wide_threads(size_t smem, int tuned = 0) {
 }
 
 // The cluster kernel for nz planes (2..8), the column group width and the CTAs
-// per SM it is built for (3: FP32 up to kYzcOcc3MaxPlanes planes).
+// per SM it is built for (occ 3 or 4: FP32 up to kYzcOcc3MaxPlanes planes).
 template <typename T>
-static void (*yzc_kernel(int nz, bool wide, bool occ3 = false))(PassParams<T>) {
-    if (occ3 && sizeof(T) == 4 && nz <= kYzcOcc3MaxPlanes) {
+static void (*yzc_kernel(int nz, bool wide, int occ = 2))(PassParams<T>) {
+    if (occ == 3 && sizeof(T) == 4 && nz <= kYzcOcc3MaxPlanes) {
         switch (nz) {
             case 2: return wide ? k_yzc<T, 2, true, 3> : k_yzc<T, 2, false, 3>;
             case 3: return wide ? k_yzc<T, 3, true, 3> : k_yzc<T, 3, false, 3>;
             default: return wide ? k_yzc<T, 4, true, 3> : k_yzc<T, 4, false, 3>;
+        }
+    }
+    if (occ == 4 && sizeof(T) == 4 && nz <= kYzcOcc3MaxPlanes) {
+        switch (nz) {
+            case 2: return wide ? k_yzc<T, 2, true, 4> : k_yzc<T, 2, false, 4>;
+            case 3: return wide ? k_yzc<T, 3, true, 4> : k_yzc<T, 3, false, 4>;
+            default: return wide ? k_yzc<T, 4, true, 4> : k_yzc<T, 4, false, 4>;
         }
     }
     switch (nz) {
@@ -95,7 +102,8 @@ static void issue_passes(const Launch& L, PassParams<T> p, const StoreT<T>* ys, 
     for (int li = 0; li < kYzcListCount; ++li) {
         if (!L.yzc[li].count) continue;
         const int nz = li % kYzcLists;
-        const bool wide = ((li / kYzcLists) & 1) != 0, occ3 = li >= 2 * kYzcLists;
+        const bool wide = ((li / kYzcLists) & 1) != 0;
+        const int occ = 2 + li / (2 * kYzcLists);
         p.items = L.yzc[li].dev;
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)(L.yzc[li].count * nz), 1, 1);
@@ -110,7 +118,7 @@ static void issue_passes(const Launch& L, PassParams<T> p, const StoreT<T>* ys, 
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         // one instantiation per plane count; wide: 32-point column groups
-        cudaLaunchKernelEx(&cfg, yzc_kernel<T>(nz, wide, occ3), p);
+        cudaLaunchKernelEx(&cfg, yzc_kernel<T>(nz, wide, occ), p);
         if (hk) hk->mark(KIND_YZC);
         ++n;
     }
@@ -275,9 +283,9 @@ static void set_attrs() {
     cudaFuncSetAttribute(k_ycol<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     cudaFuncSetAttribute(k_zcol<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     for (int nz = 2; nz <= 8; ++nz)
-        for (int v = 0; v < 4; ++v)
-            cudaFuncSetAttribute(yzc_kernel<T>(nz, (v & 1) != 0, v >= 2), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 mx);
+        for (int v = 0; v < 6; ++v)
+            cudaFuncSetAttribute(yzc_kernel<T>(nz, (v & 1) != 0, 2 + v / 2),
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
 }
 
 }  // namespace mm

@@ -28,11 +28,12 @@
 #define MM_THREADS 256
 // Cluster-fused y/z pass: largest plane count (portable cluster size) and its
 // work lists, one per (planes, column group width, CTAs per SM):
-// list = nz + kYzcLists * wide + 2 kYzcLists * (3 CTAs per SM).
+// list = nz + kYzcLists * (wide + 2 occ), occ 0 for the rule's build, 1 for the
+// one bounded for 3 CTAs per SM, 2 for 4 CTAs per SM.
 constexpr int kMaxClusterPlanes = 8;
 constexpr int kYzcLists = kMaxClusterPlanes + 1;
-constexpr int kYzcListCount = 4 * kYzcLists;
-// Plane counts with a 3-CTA-per-SM build of the FP32 cluster kernel.
+constexpr int kYzcListCount = 6 * kYzcLists;
+// Plane counts with 3- and 4-CTA-per-SM builds of the FP32 cluster kernel.
 constexpr int kYzcOcc3MaxPlanes = 4;
 // Largest x-pass CTA (threads) per precision; as launch bounds with one CTA
 // per SM it caps the x kernels at 64 (FP32) / 128 (FP64) registers a thread.
@@ -103,7 +104,7 @@ struct SimDesc {
     int group_begin, group_end;   // NEB chain members [begin, end), -1 if none
     int neb_index;                // image index in its chain
     int colgroup;                 // cluster-pass column register groups: 0 rule, 1 16-point, 2 32-point
-    int yzcocc;                   // cluster-pass CTAs per SM the kernel is compiled for: 0 rule (2), 3
+    int yzcocc;                   // cluster-pass CTAs per SM the kernel is compiled for: 0 rule (2), 3, 4
     int pad0;
     long long off;           // element offset of the [3][N] state block
     long long spec_off;      // complex offset of the spectrum block

@@ -109,54 +109,75 @@ __global__ void __launch_bounds__(MM_XTHREADS_MAX<T>, 1) k_xfwd(PassParams<T> p)
     // lower half of each sequence is stored, the first FFT stage does not read the upper half
     const int lhalf = lLh > 0 ? lLh - 1 : 0;
     const int tot = nrows << lhalf;
+    const R* __restrict__ mp = p.m + base;
+    R* __restrict__ yp = p.ybuf + base;
+    R* __restrict__ ep = p.errp + base;
     for (int id = threadIdx.x; id < tot; id += blockDim.x) {
         const int r = id >> lhalf, n = id & ((1 << lhalf) - 1);
         V2<T> val[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) val[c] = mk<T>((T)0, (T)0);
+        // both cells' state and stage vectors are loaded before any is combined or stored,
+        // so all loads of the item are in flight together; a stage vector the stage's
+        // coefficients or (stage 7) error weights use is loaded once for both
+        R yv[2][3];
+        R kv[6][2][3];
 #pragma unroll
         for (int h2 = 0; h2 < 2; ++h2) {
             const int x = 2 * n + h2;
             if (x < nx) {
                 const int cell = r * nx + x;                   // within the tile
-                R yv[3];
 #pragma unroll
-                for (int c = 0; c < 3; ++c) yv[c] = p.m[base + c * N + cell];
+                for (int c = 0; c < 3; ++c) yv[h2][c] = mp[c * N + cell];
+#pragma unroll
+                for (int j = 0; j < 6; ++j) {
+                    if (j < S - 1 && (dp_a(S, j) != 0.0 || (S == 7 && dp_e(j) != 0.0))) {
+                        const R* __restrict__ kj = p.kvec[j] + base + cell;
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) kv[j][h2][c] = kj[c * N];
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int h2 = 0; h2 < 2; ++h2) {
+            const int x = 2 * n + h2;
+            if (x < nx) {
+                const int cell = r * nx + x;                   // within the tile
+                R yvv[3] = {yv[h2][0], yv[h2][1], yv[h2][2]};
                 if (S >= 2) {
                     R acc[3] = {(R)0, (R)0, (R)0};
 #pragma unroll
                     for (int j = 0; j < S - 1; ++j) {
                         if (dp_a(S, j) != 0.0) {
                             const R aj = (R)dp_a(S, j);
-                            const R* kj = p.kvec[j] + base + cell;
 #pragma unroll
-                            for (int c = 0; c < 3; ++c) acc[c] += aj * kj[c * N];
+                            for (int c = 0; c < 3; ++c) acc[c] += aj * kv[j][h2][c];
                         }
                     }
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) yv[c] += hstep * acc[c];
+                    for (int c = 0; c < 3; ++c) yvv[c] += hstep * acc[c];
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) p.ybuf[base + c * N + cell] = yv[c];
+                    for (int c = 0; c < 3; ++c) yp[c * N + cell] = yvv[c];
                     if (S == 7) {
                         R ev[3] = {(R)0, (R)0, (R)0};
 #pragma unroll
                         for (int j = 0; j < 6; ++j) {
                             if (dp_e(j) != 0.0) {
                                 const R ej = (R)dp_e(j);
-                                const R* kj = p.kvec[j] + base + cell;
 #pragma unroll
-                                for (int c = 0; c < 3; ++c) ev[c] += ej * kj[c * N];
+                                for (int c = 0; c < 3; ++c) ev[c] += ej * kv[j][h2][c];
                             }
                         }
 #pragma unroll
-                        for (int c = 0; c < 3; ++c) p.errp[base + c * N + cell] = ev[c];
+                        for (int c = 0; c < 3; ++c) ep[c * N + cell] = ev[c];
                     }
                 }
                 if (demag) {
                     const R ms = msarr ? msp[cell] : coef<R>(d).Ms;
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
-                        const T mc = to_compute<T>(ms * yv[c]);
+                        const T mc = to_compute<T>(ms * yvv[c]);
                         if (h2 == 0) val[c].x = mc; else val[c].y = mc;
                     }
                 }
@@ -409,7 +430,9 @@ __device__ __forceinline__ void load_bin(const dd* __restrict__ q, dd (&v)[QP]) 
 // The stored tensor holds dz >= 0; negative offsets follow from the z parities
 // (xz, yz odd); xz and yz are imaginary in (kx, ky, dz) and stored as t with
 // N^ = i t; the ky fold flips xy and yz.
-template <typename T, int NZ>
+// LOWREG: the per-plane form below also for 4-byte types (the builds bounded for 3 or
+// 4 CTAs per SM).
+template <typename T, int NZ, bool LOWREG = false>
 __device__ void yzc_zstep(const PassParams<T>& p, const SimDesc& d, V2<T>* const (&rem)[8], int rank, int es,
                           int b, int ncols) {
     constexpr int QP = yzc_qp(NZ);
@@ -472,7 +495,7 @@ __device__ void yzc_zstep(const PassParams<T>& p, const SimDesc& d, V2<T>* const
             }
             continue;
         }
-        if constexpr (sizeof(T) == 8) {
+        if constexpr (sizeof(T) == 8 || LOWREG) {
             // 8-byte types (FP64, double-float): one output plane at a time, each offset's
             // six tensor values loaded where they are used (L1), so the NZ planes of M and
             // one plane of accumulators are what stays in registers (the plane loop is not
@@ -534,8 +557,9 @@ __device__ void yzc_zstep(const PassParams<T>& p, const SimDesc& d, V2<T>* const
 // 512x512x4 film); FP64 with more planes keeps the registers it needs.
 // NZ: planes (= cluster size); WIDE: 32-point register groups for the y columns
 // (FP32; see plan_yzc_list); MINB: CTAs per SM the build is bounded for (0: the
-// rule above; 3: 85 registers a thread, for narrow column tiles whose shared
-// memory lets three CTAs share an SM).
+// rule above; 3: 85 registers a thread, 4: 64 registers and 8-point column
+// groups, for narrow column tiles whose shared memory lets that many CTAs share
+// an SM).
 template <typename T, int NZ, bool WIDE, int MINB = 0>
 __global__ void __launch_bounds__(MM_THREADS, MINB ? MINB : ((sizeof(T) == 4 || NZ <= 4) ? 2 : 1))
     k_yzc(PassParams<T> p) {
@@ -556,7 +580,10 @@ __global__ void __launch_bounds__(MM_THREADS, MINB ? MINB : ((sizeof(T) == 4 || 
     long long gb[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) gb[c] = spec_block<T>(d, c, z, b);
-    for (int b0 = threadIdx.x; b0 < (L << lT); b0 += 4 * blockDim.x) {   // 12 loads in flight
+    // rows y < ny from the spectrum, ny <= y < L/2 zero; the upper half (L >= 2 ny) is not
+    // stored: the forward's first register group does not read it
+    const int nld = (L >> 1) << lT;
+    for (int b0 = threadIdx.x; b0 < nld; b0 += 4 * blockDim.x) {   // 12 loads in flight
         V2<T> v[3][4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
@@ -564,12 +591,12 @@ __global__ void __launch_bounds__(MM_THREADS, MINB ? MINB : ((sizeof(T) == 4 || 
             const int y = id >> lT;
 #pragma unroll
             for (int c = 0; c < 3; ++c)
-                v[c][u] = (id < (L << lT) && y < ny) ? p.spec[gb[c] + id] : mk<T>((T)0, (T)0);
+                v[c][u] = (id < nld && y < ny) ? p.spec[gb[c] + id] : mk<T>((T)0, (T)0);
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int id = b0 + u * blockDim.x;
-            if (id < (L << lT)) {
+            if (id < nld) {
                 const int col = id & (TT - 1), y = id >> lT;
 #pragma unroll
                 for (int c = 0; c < 3; ++c) sm[y * es + c * TT + col] = v[c][u];
@@ -577,13 +604,13 @@ __global__ void __launch_bounds__(MM_THREADS, MINB ? MINB : ((sizeof(T) == 4 || 
         }
     }
     __syncthreads();
-    constexpr int GMC = (WIDE && sizeof(T) == 4) ? 5 : kGroupMax<T>;
+    constexpr int GMC = MINB >= 4 ? 3 : (WIDE && sizeof(T) == 4) ? 5 : kGroupMax<T>;
     fft_dif<T, false, false, true, GMC>(sm, lL, es, 1, es, p.tw);   // rows leave in bit-reversed order
     cl.sync();                                  // every plane transformed along y
     V2<T>* rem[8];
 #pragma unroll
     for (int zz = 0; zz < 8; ++zz) rem[zz] = zz < nz ? cl.map_shared_rank(sm, zz) : sm;
-    yzc_zstep<T, NZ>(p, d, rem, rank, es, b, ncols);   // NZ == d.nz, fixed per launch
+    yzc_zstep<T, NZ, (MINB >= 3)>(p, d, rem, rank, es, b, ncols);   // NZ == d.nz, fixed per launch
     cl.sync();                                  // every row back in its owner's plane
     fft_dit<T, true, false, true, GMC>(sm, lL, es, 1, es, p.tw);    // bit-reversed in, natural out
 #pragma unroll

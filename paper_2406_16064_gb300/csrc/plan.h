@@ -38,8 +38,9 @@ inline int plan_pad_len(int n, bool min2) {
 //   x_threads   threads of an x-pass CTA (multiple of 32; launch-wide)
 //   col_threads threads of a column-pass CTA outside the cluster pass (launch-wide)
 //   col_group   cluster-pass column register groups: 1 16-point, 2 32-point
-//   col_occ     cluster-pass CTAs per SM its kernel is built for: 3 (FP32, up to
-//               kYzcOcc3MaxPlanes planes; fewer registers a thread), else the rule (2)
+//   col_occ     cluster-pass CTAs per SM its kernel is built for: 3 or 4 (FP32, up
+//               to kYzcOcc3MaxPlanes planes; fewer registers a thread, 8-point
+//               column groups at 4), else the rule (2)
 struct Tuning {
     int Ty = 0, Rx = 0, x_threads = 0, col_threads = 0, col_group = 0, col_occ = 0;
 };
@@ -73,7 +74,7 @@ inline void plan_geometry(SimDesc& d, bool f32, const Tuning& t = Tuning()) {
     d.lTy = plan_ilog2(d.Ty);
     d.NBx = (d.Kx + d.Ty - 1) >> d.lTy;
     d.colgroup = (t.col_group == 1 || t.col_group == 2) ? t.col_group : 0;
-    d.yzcocc = t.col_occ == 3 ? 3 : 0;
+    d.yzcocc = (t.col_occ == 3 || t.col_occ == 4) ? t.col_occ : 0;
 }
 
 template <typename T>
@@ -161,11 +162,13 @@ inline bool plan_uses_yzc(const SimDesc& d) { return d.Pz > 1 && d.Py > 1 && d.n
 // measured faster as (4,3,3) than as (5,5)).
 inline int plan_yzc_list(const SimDesc& d, bool f32) {
     const bool wide = d.colgroup ? d.colgroup == 2 : f32 && (d.lPy == 5 || d.lPy == 9 || d.lPy == 13);
-    return d.nz + kYzcLists * (wide ? 1 : 0) + 2 * kYzcLists * (d.yzcocc == 3 ? 1 : 0);
+    const int occ = d.yzcocc == 3 ? 1 : d.yzcocc == 4 ? 2 : 0;
+    return d.nz + kYzcLists * ((wide ? 1 : 0) + 2 * occ);
 }
 inline int plan_yzc_nz(int li) { return li % kYzcLists; }
 inline bool plan_yzc_wide(int li) { return ((li / kYzcLists) & 1) != 0; }
-inline bool plan_yzc_occ3(int li) { return li >= 2 * kYzcLists; }
+// CTAs per SM of list li's kernel build (2: the rule's)
+inline int plan_yzc_occ(int li) { return 2 + li / (2 * kYzcLists); }
 
 // Elements of a geometry's stored tensor:
 //   standard [ncomp][Pz/2+1][Py/2+1][Kx];
@@ -227,8 +230,8 @@ namespace mm {
 // launch bound).  vsz = bytes of one complex value.
 inline bool plan_tuning_valid(const SimDesc& d, size_t vsz, const Tuning& t, int maxthreads) {
     if (d.Ty < 1 || d.Ty > 32 || (d.Ty & (d.Ty - 1)) || d.Rx < 1 || d.Rx > d.ny) return false;
-    if (d.yzcocc == 3 && !(vsz == 8 && plan_uses_yzc(d) && d.nz <= kYzcOcc3MaxPlanes &&
-                           3 * ((size_t)3 * d.Py * d.Ty * vsz + 1024) <= 233472))
+    if (d.yzcocc && !(vsz == 8 && plan_uses_yzc(d) && d.nz <= kYzcOcc3MaxPlanes &&
+                      d.yzcocc * ((size_t)3 * d.Py * d.Ty * vsz + 1024) <= 233472))
         return false;
     for (int th : {t.x_threads, t.col_threads})
         if (th != 0 && (th < 32 || th > maxthreads || th % 32)) return false;
@@ -271,7 +274,7 @@ inline std::vector<Tuning> plan_tuning_candidates(const SimDesc& d0, bool f32, i
         const bool groups = f32 && plan_uses_yzc(r);
         const int g0 = plan_yzc_wide(plan_yzc_list(r, f32)) ? 2 : 1;
         for (int ty : {r.Ty / 2, r.Ty, 2 * r.Ty, r.Ty / 4})
-            for (int occ : {0, 3}) {
+            for (int occ : {0, 3, 4}) {
                 if (ty < 1 || ty > tymax || (occ && !groups)) continue;
                 for (int g : {g0, 3 - g0}) {
                     if (!groups && g != g0) continue;

@@ -26,9 +26,9 @@ MESHES = [(40, 24, 3), (48, 40, 1), (20, 12, 10)]
 
 def _tunings(nz):
     """Every kx block width, one or two row tiles, three CTA widths, both column groups and
-    both cluster-kernel builds (2 or 3 CTAs per SM)."""
+    every cluster-kernel build (2, 3 or 4 CTAs per SM)."""
     for ty, rx, xt in itertools.product((1, 2, 4, 8, 16, 32), (1, 3), (0, 128, 512)):
-        for g, occ in (itertools.product((1, 2), (0, 3)) if 1 < nz <= 8 else ((0, 0),)):
+        for g, occ in (itertools.product((1, 2), (0, 3, 4)) if 1 < nz <= 8 else ((0, 0),)):
             yield {"Ty": ty, "Rx": rx, "x_threads": xt, "col_threads": xt if nz == 1 or nz > 8 else 0,
                    "col_group": g, "col_occ": occ}
 
