@@ -198,20 +198,29 @@ __global__ void __launch_bounds__(MM_XTHREADS_MAX<T>, 1) k_xfwd(PassParams<T> p)
     V2<T>* sp = p.spec + d.spec_off;
     const int lT = d.lTy, TT = d.Ty;
     const int plane = d.NBx * (d.Py << lT);               // elements of one (c, z) plane
-    const int tot2 = nseq << lLh;
-    for (int id = threadIdx.x; id < tot2 + nseq; id += blockDim.x) {
+    // X_k and X_{Lh-k} come from the same two half-length bins: with E_k, O_k the even
+    // and odd parts at k, E_{Lh-k} = conj(E_k) and O_{Lh-k} = conj(O_k), so one work
+    // item loads Z_k and Z_{Lh-k} once and writes both outputs (k = 0..Lh/2)
+    const int lhl = lLh > 0 ? lLh - 1 : 0;
+    const int hl = lLh > 0 ? 1 << lhl : 0;
+    const int totp = lLh > 0 ? nseq << lhl : 0;
+    for (int id = threadIdx.x; id < totp + nseq; id += blockDim.x) {
         int q, k;
-        if (id < tot2) { q = id >> lLh; k = id & (Lh - 1); } else { q = id - tot2; k = Lh; }
+        if (id < totp) { q = id >> lhl; k = id & (hl - 1); } else { q = id - totp; k = hl; }
+        const int kp = Lh - k;
         const int r = q / 3, c = q - 3 * r;
         const int y = y0 + r, z = z0;
         const V2<T>* s = Z + q * SL;
         const V2<T> Zk = s[ix<true>(k & (Lh - 1), 1)];
-        const V2<T> Zm = cconj(s[ix<true>((Lh - k) & (Lh - 1), 1)]);
+        const V2<T> Zm = cconj(s[ix<true>(kp & (Lh - 1), 1)]);
         const V2<T> E = cscale(Zk + Zm, (T)0.5);
         const V2<T> Dd = Zk - Zm;
         const V2<T> O = mk<T>(Dd.y * (T)0.5, -Dd.x * (T)0.5);
-        const int o = (c * d.nz + z) * plane + (((k >> lT) * d.Py + y) << lT) + (k & (TT - 1));
-        sp[o] = E + cmul(k < Lh ? wsplit[k] : mk<T>((T)-1, (T)0), O);
+        V2<T>* so = sp + (c * d.nz + z) * plane + (y << lT);
+        so[((k >> lT) * d.Py << lT) + (k & (TT - 1))] = E + cmul(k < Lh ? wsplit[k] : mk<T>((T)-1, (T)0), O);
+        if (kp != k)
+            so[((kp >> lT) * d.Py << lT) + (kp & (TT - 1))] =
+                cconj(E) + cmul(kp < Lh ? wsplit[kp] : mk<T>((T)-1, (T)0), cconj(O));
     }
 }
 
@@ -393,8 +402,10 @@ __global__ void __launch_bounds__(MM_XTHREADS_MAX<T>, 1) k_zcol(PassParams<T> p)
 
 // ------------------------------------------------ y + z fused, cluster per block
 // QP tensor values of one (column, ky) bin of the blocked layout, as 16-byte loads
+// (q must be 16-byte aligned: a bin's first value, or an offset of 16 bytes from it)
 template <int QP>
 __device__ __forceinline__ void load_bin(const float* __restrict__ q, float (&v)[QP]) {
+    static_assert(QP % 4 == 0, "FP32 bins are loaded as whole float4s");
     const float4* q4 = reinterpret_cast<const float4*>(q);
 #pragma unroll
     for (int i = 0; i < QP / 4; ++i) {
@@ -404,6 +415,7 @@ __device__ __forceinline__ void load_bin(const float* __restrict__ q, float (&v)
 }
 template <int QP>
 __device__ __forceinline__ void load_bin(const double* __restrict__ q, double (&v)[QP]) {
+    static_assert(QP % 2 == 0, "FP64 bins are loaded as whole double2s");
     const double2* q2 = reinterpret_cast<const double2*>(q);
 #pragma unroll
     for (int i = 0; i < QP / 2; ++i) {
@@ -414,6 +426,7 @@ __device__ __forceinline__ void load_bin(const double* __restrict__ q, double (&
 
 template <int QP>
 __device__ __forceinline__ void load_bin(const dd* __restrict__ q, dd (&v)[QP]) {
+    static_assert(QP % 2 == 0, "double-float bins are loaded as whole float4s");
     const float4* q4 = reinterpret_cast<const float4*>(q);
 #pragma unroll
     for (int i = 0; i < QP / 2; ++i) {
@@ -508,7 +521,12 @@ __device__ void yzc_zstep(const PassParams<T>& p, const SimDesc& d, V2<T>* const
                     const int dz = z - z2 >= 0 ? z - z2 : z2 - z;
                     const T so = z - z2 >= 0 ? (T)1 : (T)-1;    // xz, yz odd in z
                     T t[6];
-                    load_bin<6>(tq + 6 * dz, t);
+                    if constexpr (sizeof(T) == 8) {
+                        load_bin<6>(tq + 6 * dz, t);            // 48-byte offsets: 16-byte aligned
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 6; ++i) t[i] = __ldg(tq + 6 * dz + i);   // 24-byte offsets
+                    }
                     const T xx = t[0], yy = t[1], zz = t[2], xy = sy * t[3];
                     const T xz = so * t[4], yz = so * sy * t[5];
                     const V2<T> a = M[z2][0], bb = M[z2][1], c = M[z2][2];
