@@ -140,9 +140,13 @@ int mm_num_sims(const mm_ctx *ctx);
  *               up to 4 planes, column tiles small enough for that many CTAs'
  *               shared memory; fewer registers a thread, and 8-point column
  *               groups at 4) or 0 / 2 (the rule)
+ *   x_stage     1: the x-inverse pass stages its tile's state rows, with their
+ *               +-y and +-z neighbours, in shared memory by bulk copies
+ *               (cp.async.bulk, completed on an mbarrier) that overlap its
+ *               inverse FFT; 0 / 2: the rule (the epilogue loads them directly)
  * The two CTA widths act per launch, which covers the whole batch: they apply
  * when every simulation of the context has the same value (else the rule). */
-typedef struct { int Ty, Rx, x_threads, col_threads, col_group, col_occ; } mm_tuning;
+typedef struct { int Ty, Rx, x_threads, col_threads, col_group, col_occ, x_stage; } mm_tuning;
 
 /* Set the tuning of one simulation (sim_id = -1: every simulation); must
  * precede mm_precompute_demag.  MM_EINVAL if the tiles do not fit the kernels

@@ -230,6 +230,9 @@ int validate_items(mm_ctx* C) {
         const SimDesc& d = C->sims[w.sim].d;
         if (w.a < 0 || w.b < 1 || w.a + w.b > d.ny * d.nz) return fail(C, MM_EBOUNDS, "x item rows");
         if (2 * 3ULL * w.b * padded_len(d.Kx) * vsz > P.smem_x) return fail(C, MM_EBOUNDS, "x item smem");
+        if ((d.flags & F_XSTAGE) &&
+            xinv_stage_offset(3 * w.b, padded_len(d.Kx), vsz) + xinv_stage_bytes(w.b, d.nx, C->esz) > P.smem_xi)
+            return fail(C, MM_EBOUNDS, "x-inverse staged rows smem");
         if ((w.a % d.ny) + w.b > d.ny) return fail(C, MM_EBOUNDS, "x item crosses a plane");
         if (plan_spec_elems(d) >= (1LL << 31) || 3LL * d.ncells >= (1LL << 31))
             return fail(C, MM_EINVAL, "simulation too large for 32-bit per-simulation offsets");
@@ -491,7 +494,10 @@ int first_error(mm_ctx* C, const std::vector<SimState>& st) {
         if (st[i].status < 0) {
             const int s = st[i].status;
             return fail(C, s, "simulation %zu: %s", i,
-                        s == MM_ENAN ? "non-finite error norm" : (s == MM_ESTEP ? "step size underflow" : "error"));
+                        s == MM_ENAN ? "non-finite error norm"
+                        : s == MM_ESTEP ? "step size underflow"
+                        : s == MM_ETIMEOUT ? "a staged copy into shared memory did not complete (bounded wait)"
+                                           : "error");
         }
     }
     return MM_OK;
@@ -608,6 +614,7 @@ Tuning from_abi(const mm_tuning& t) {
     Tuning u;
     u.Ty = t.Ty; u.Rx = t.Rx; u.x_threads = t.x_threads; u.col_threads = t.col_threads; u.col_group = t.col_group;
     u.col_occ = t.col_occ;
+    u.x_stage = t.x_stage;
     return u;
 }
 
@@ -615,7 +622,7 @@ Tuning from_abi(const mm_tuning& t) {
 int apply_tuning(mm_ctx* C, SimHost& s, const Tuning& t) {
     const bool f32 = C->precision == MM_F32;
     if (t.Ty < 0 || t.Rx < 0 || t.x_threads < 0 || t.col_threads < 0 || t.col_group < 0 || t.col_group > 2 ||
-        (t.col_occ != 0 && t.col_occ != 2 && t.col_occ != 3 && t.col_occ != 4))
+        (t.col_occ != 0 && t.col_occ != 2 && t.col_occ != 3 && t.col_occ != 4) || t.x_stage < 0 || t.x_stage > 2)
         return fail(C, MM_EINVAL, "mm_set_tuning: negative or unknown value");
     if (t.Ty > 32 || (t.Ty & (t.Ty - 1))) return fail(C, MM_EINVAL, "mm_set_tuning: Ty must be a power of two <= 32");
     SimDesc d = s.d;
@@ -644,6 +651,7 @@ mm_tuning resolved_tuning(const mm_ctx* C, const SimHost& s) {
     r.col_threads = s.tune.col_threads ? s.tune.col_threads : (sc ? plan_wide_threads(sc, maxth) : 0);
     r.col_group = plan_uses_yzc(s.d) ? (plan_yzc_wide(plan_yzc_list(s.d, f32)) ? 2 : 1) : 0;
     r.col_occ = plan_uses_yzc(s.d) ? s.d.yzcocc : 0;
+    r.x_stage = (s.d.flags & F_XSTAGE) ? 1 : 0;
     return r;
 }
 
@@ -767,6 +775,7 @@ int mm_autotune(mm_ctx* C, int sim, int reps, mm_tuning* best_out, double* best_
         best_out->Ty = best.Ty; best_out->Rx = best.Rx; best_out->x_threads = best.x_threads;
         best_out->col_threads = best.col_threads; best_out->col_group = best.col_group;
         best_out->col_occ = best.col_occ;
+        best_out->x_stage = best.x_stage;
     }
     if (best_ms) *best_ms = tbest;
     if (rule_ms) *rule_ms = trule;

@@ -56,7 +56,10 @@ inline int plan_wide_threads(size_t smem, int maxthreads) {
 // spin torques; SimDesc::eflags), evaluated by the extended x-inverse kernel;
 // there F_DMI means DMI of the simulation's class with a non-zero constant and
 // F_EX exchange with a non-zero uniform or per-cell constant.
-enum { F_DEMAG = 1, F_DMI = 2, F_PREC = 4, F_MSARR = 8, F_EX = 16, F_UNI = 32, F_CUB = 64, F_EXT = 128 };
+// F_XSTAGE: the x-inverse pass stages the tile's state rows (with their +-y and
+// +-z neighbours) into shared memory by bulk copies (the planner reserved room).
+enum { F_DEMAG = 1, F_DMI = 2, F_PREC = 4, F_MSARR = 8, F_EX = 16, F_UNI = 32, F_CUB = 64, F_EXT = 128,
+       F_XSTAGE = 256 };
 // extended terms: per-cell A and D, Zhang-Li torque, Slonczewski / spin-orbit torque
 enum { E_CELL = 1, E_STT = 2, E_SOT = 4 };
 
@@ -613,6 +616,54 @@ __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src)
 }
 __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+// Staged state rows of the x-inverse pass (F_XSTAGE): after its two FFT buffers
+// (nseq padded sequences of SK complex values each, vsz bytes a value), rounded up
+// to 16 bytes, the three components' rows y0-1 .. y0+nrows (those in the mesh),
+// then the nrows rows of the plane below and of the plane above, esz bytes a value.
+__host__ __device__ constexpr size_t xinv_stage_offset(int nseq, int SK, size_t vsz) {
+    return ((2 * (size_t)nseq * SK * vsz) + 15) & ~(size_t)15;
+}
+__host__ __device__ constexpr size_t xinv_stage_bytes(int nrows, int nx, size_t esz) {
+    return 3 * (size_t)(3 * nrows + 2) * nx * esz;
+}
+
+// Bulk copies (the copy engine of sm_90+, cp.async.bulk) of contiguous global
+// ranges into shared memory, completed on an mbarrier by transaction count.
+// Addresses 16-byte aligned, sizes multiples of 16 bytes.
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* smem_dst, const void* gmem_src, unsigned bytes,
+                                         unsigned long long* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+            smem_u32(smem_dst)),
+        "l"(gmem_src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+// One bounded probe of the barrier's phase; true once phase `parity` has completed.
+__device__ __forceinline__ bool mbar_test(unsigned long long* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Wait for phase `parity` with at most `limit` probes; false if it ran out.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity, int limit) {
+    for (int i = 0; i < limit; ++i)
+        if (mbar_test(bar, parity)) return true;
+    return false;
 }
 
 __device__ __forceinline__ double bits_to_double(unsigned long long b) { return __longlong_as_double((long long)b); }

@@ -684,6 +684,39 @@ __global__ void __launch_bounds__(MM_XTHREADS_MAX<T>, 1) k_xinv(PassParams<T> p,
     const bool msarr = (d.flags & F_MSARR) != 0;
     const int z0 = row0 / ny, y0 = row0 - z0 * ny;      // a tile never crosses a plane
     const long long tile = d.off - p.off_adjust + (long long)row0 * nx;
+    const bool ext = EXT && (d.flags & F_EXT) != 0;
+    // Staged state rows (F_XSTAGE): the tile's rows y0-1 .. y0+nrows of its plane and its
+    // rows of the planes below and above, as bulk copies issued now and completed on an
+    // mbarrier while the inverse FFT runs; the epilogue then reads m and its six
+    // neighbours from shared memory.  Taken only where every run starts on a 16-byte
+    // boundary and is a multiple of 16 bytes (rows of nx * sizeof(R) bytes), uniformly
+    // for the CTA; otherwise the epilogue loads them from global memory.
+    __shared__ __align__(8) unsigned long long xbar;
+    const int ylo = y0 > 0 ? y0 - 1 : 0, yhi = y0 + nrows < ny ? y0 + nrows : ny - 1;
+    const int prow = yhi - ylo + 1;
+    const bool zlo = z0 > 0, zhi = z0 + 1 < nz;
+    const size_t rowb = (size_t)nx * sizeof(R);
+    const R* __restrict__ gstate = ys + (d.off - p.off_adjust);
+    R* stg = reinterpret_cast<R*>(smraw + xinv_stage_offset(nseq, SK, sizeof(V2<T>)));
+    const bool staged = (d.flags & F_XSTAGE) != 0 && !ext && rowb % 16 == 0 &&
+                        reinterpret_cast<uintptr_t>(gstate) % 16 == 0;
+    if (staged) {
+        if (threadIdx.x == 0) mbar_init(&xbar, 1);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            // per component: its prow plane rows, then nrows rows below, nrows rows above
+            const unsigned pb = (unsigned)(prow * rowb), zb = (unsigned)(nrows * rowb);
+            mbar_expect_tx(&xbar, 3 * pb + (zlo ? 3 * zb : 0) + (zhi ? 3 * zb : 0));
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const R* gc = gstate + c * N;
+                R* sc = stg + c * (prow + 2 * nrows) * nx;
+                bulk_g2s(sc, gc + ((long long)z0 * ny + ylo) * nx, pb, &xbar);
+                if (zlo) bulk_g2s(sc + prow * nx, gc + ((long long)(z0 - 1) * ny + y0) * nx, zb, &xbar);
+                if (zhi) bulk_g2s(sc + (prow + nrows) * nx, gc + ((long long)(z0 + 1) * ny + y0) * nx, zb, &xbar);
+            }
+        }
+    }
     const V2<T>* Hd = nullptr;
     if (demag) {
         const V2<T>* sp = p.spec + d.spec_off;
@@ -755,12 +788,29 @@ __global__ void __launch_bounds__(MM_XTHREADS_MAX<T>, 1) k_xinv(PassParams<T> p,
     const bool dmi = (d.flags & F_DMI) != 0;
     const bool do_ex = (d.flags & F_EX) != 0, do_uni = (d.flags & F_UNI) != 0, do_cub = (d.flags & F_CUB) != 0;
     const bool write_k = !ENERGY;
-    const R* __restrict__ m0p = ys + tile;
-    const R* __restrict__ m1p = m0p + N;
-    const R* __restrict__ m2p = m1p + N;
     const int sz = nx * ny;
+    // m of the tile's cells (index r nx + x) and of their +-z neighbours: the staged rows,
+    // or the state in global memory
+    const R* __restrict__ m0p = ys + tile;
+    long long cs = N;                            // component stride
+    int dzb = -sz, dza = sz;                     // offsets of the -z and +z neighbours
+    if (staged) {
+        // a copy that has not landed after a bounded wait is reported (MM_ETIMEOUT),
+        // waited for once more (it writes this CTA's shared memory) and the tile skipped
+        const bool late = !mbar_wait_bounded(&xbar, 0, 1 << 20);
+        if (__syncthreads_or(late)) {
+            if (threadIdx.x == 0) atomicExch(&p.state[w.sim].status, -6);
+            mbar_wait_bounded(&xbar, 0, 1 << 20);
+            return;
+        }
+        m0p = stg + (y0 - ylo) * nx;
+        cs = (long long)(prow + 2 * nrows) * nx;
+        dzb = (prow - (y0 - ylo)) * nx;
+        dza = dzb + nrows * nx;
+    }
+    const R* __restrict__ m1p = m0p + cs;
+    const R* __restrict__ m2p = m1p + cs;
     const R* __restrict__ msp = msarr ? p.Ms + d.ms_off + (long long)row0 * nx : nullptr;
-    const bool ext = EXT && (d.flags & F_EXT) != 0;
     const R* __restrict__ acp = (ext && (d.eflags & E_CELL)) ? p.cellp + d.cell_off + (long long)row0 * nx : nullptr;
     const R* __restrict__ dcp = acp ? acp + N : nullptr;
     const R e7 = (R)dp_e(6);
@@ -800,7 +850,7 @@ __global__ void __launch_bounds__(MM_XTHREADS_MAX<T>, 1) k_xinv(PassParams<T> p,
                     dm0 = dmv[0]; dm1 = dmv[1]; dm2 = dmv[2];
                 } else if (do_ex || dmi) {
                     bool ok[6] = {x > 0, x < nx - 1, y > 0, y < ny - 1, z > 0, z < nz - 1};
-                    const int off[6] = {-1, 1, -nx, nx, -sz, sz};
+                    const int off[6] = {-1, 1, -nx, nx, dzb, dza};
                     R j0[6], j1[6], j2[6];
 #pragma unroll
                     for (int nb = 0; nb < 6; ++nb) {
@@ -808,8 +858,9 @@ __global__ void __launch_bounds__(MM_XTHREADS_MAX<T>, 1) k_xinv(PassParams<T> p,
                         j0[nb] = m0p[o]; j1[nb] = m1p[o]; j2[nb] = m2p[o];
                     }
                     if (msarr) {
+                        const int moff[6] = {-1, 1, -nx, nx, -sz, sz};   // Ms stays in global memory
 #pragma unroll
-                        for (int nb = 0; nb < 6; ++nb) ok[nb] = ok[nb] && msp[cell + (ok[nb] ? off[nb] : 0)] > (R)0;
+                        for (int nb = 0; nb < 6; ++nb) ok[nb] = ok[nb] && msp[cell + (ok[nb] ? moff[nb] : 0)] > (R)0;
                     }
                     if (do_ex) {
                         const R fe[6] = {ex_x, ex_x, ex_y, ex_y, ex_z, ex_z};

@@ -41,8 +41,10 @@ inline int plan_pad_len(int n, bool min2) {
 //   col_occ     cluster-pass CTAs per SM its kernel is built for: 3 or 4 (FP32, up
 //               to kYzcOcc3MaxPlanes planes; fewer registers a thread, 8-point
 //               column groups at 4), else the rule (2)
+//   x_stage     1: the x-inverse pass stages its tile's state rows (and their +-y,
+//               +-z neighbours) in shared memory by bulk copies; else the rule (loads)
 struct Tuning {
-    int Ty = 0, Rx = 0, x_threads = 0, col_threads = 0, col_group = 0, col_occ = 0;
+    int Ty = 0, Rx = 0, x_threads = 0, col_threads = 0, col_group = 0, col_occ = 0, x_stage = 0;
 };
 
 // Fill the padded sizes, tensor bins and tile shapes of d from d.nx, d.ny, d.nz
@@ -75,6 +77,7 @@ inline void plan_geometry(SimDesc& d, bool f32, const Tuning& t = Tuning()) {
     d.NBx = (d.Kx + d.Ty - 1) >> d.lTy;
     d.colgroup = (t.col_group == 1 || t.col_group == 2) ? t.col_group : 0;
     d.yzcocc = (t.col_occ == 3 || t.col_occ == 4) ? t.col_occ : 0;
+    d.flags = (d.flags & ~F_XSTAGE) | (t.x_stage == 1 ? F_XSTAGE : 0);
 }
 
 template <typename T>
@@ -182,9 +185,12 @@ inline long long plan_tens_elems(const SimDesc& d) {
 
 inline long long plan_spec_elems(const SimDesc& d) { return 3LL * d.nz * d.NBx * d.Py * d.Ty; }
 
-// x-inverse shared memory: two FFT buffers of 3*Rx padded rows.
+// x-inverse shared memory: two FFT buffers of 3*Rx padded rows, then (F_XSTAGE)
+// the staged state rows.
 inline size_t plan_xinv_smem(const SimDesc& d, size_t vsz) {
-    return 2 * 3 * (size_t)d.Rx * padded_len(d.Kx) * vsz;
+    size_t b = 2 * 3 * (size_t)d.Rx * padded_len(d.Kx) * vsz;
+    if (d.flags & F_XSTAGE) b = xinv_stage_offset(3 * d.Rx, padded_len(d.Kx), vsz) + xinv_stage_bytes(d.Rx, d.nx, vsz / 2);
+    return b;
 }
 
 struct PlanItems {
@@ -248,7 +254,7 @@ inline bool plan_tuning_valid(const SimDesc& d, size_t vsz, const Tuning& t, int
 //   phase 0  kx block width Ty in {rule/2, rule, 2 rule} (at most the next power of
 //            two above Kx) x, for FP32 cluster-pass films, both column group widths;
 //   phase 1  with `fixed`'s Ty and groups: rows per x tile in {rule/2, rule, 2 rule}
-//            x x-pass CTA width in {rule, 2 rule};
+//            x x-pass CTA width in {rule, 2 rule} x staged x-inverse rows off / on;
 //   phase 2  with `fixed`'s other values: column-pass CTA width in {rule, 2 rule}
 //            (meshes with column passes outside the cluster pass only).
 // Every candidate passes plan_tuning_valid; the first is `fixed` itself.
@@ -262,7 +268,7 @@ inline std::vector<Tuning> plan_tuning_candidates(const SimDesc& d0, bool f32, i
         if (!plan_tuning_valid(d, vsz, t, maxthreads)) return;
         for (const Tuning& u : out)
             if (u.Ty == t.Ty && u.Rx == t.Rx && u.x_threads == t.x_threads && u.col_threads == t.col_threads &&
-                u.col_group == t.col_group && u.col_occ == t.col_occ)
+                u.col_group == t.col_group && u.col_occ == t.col_occ && u.x_stage == t.x_stage)
                 return;
         out.push_back(t);
     };
@@ -292,13 +298,15 @@ inline std::vector<Tuning> plan_tuning_candidates(const SimDesc& d0, bool f32, i
         plan_items(e, 0, vsz, P);
         const int nt0 = plan_wide_threads(P.smem_x, maxthreads);
         for (int rx : {r.Rx / 2, r.Rx, 2 * r.Rx})
-            for (int nt : {0, 2 * nt0}) {
-                if (rx < 1) continue;
-                Tuning t = fixed;
-                t.Rx = rx;
-                t.x_threads = nt;
-                add(t);
-            }
+            for (int nt : {0, 2 * nt0})
+                for (int st : {0, 1}) {
+                    if (rx < 1) continue;
+                    Tuning t = fixed;
+                    t.Rx = rx;
+                    t.x_threads = nt;
+                    t.x_stage = st;
+                    add(t);
+                }
     } else if (phase == 2) {
         PlanItems P;
         SimDesc e = r;

@@ -48,10 +48,10 @@ class mm_status(C.Structure):
 
 class mm_tuning(C.Structure):
     _fields_ = [("Ty", C.c_int), ("Rx", C.c_int), ("x_threads", C.c_int), ("col_threads", C.c_int),
-                ("col_group", C.c_int), ("col_occ", C.c_int)]
+                ("col_group", C.c_int), ("col_occ", C.c_int), ("x_stage", C.c_int)]
 
 
-TUNING_FIELDS = ("Ty", "Rx", "x_threads", "col_threads", "col_group", "col_occ")
+TUNING_FIELDS = ("Ty", "Rx", "x_threads", "col_threads", "col_group", "col_occ", "x_stage")
 
 _P = C.c_void_p
 _D = C.POINTER(C.c_double)

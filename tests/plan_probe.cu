@@ -55,9 +55,9 @@ int main() {
                 plan_geometry(e, f32 != 0, c[i]);
                 PlanItems Q;
                 plan_items(e, 0, vsz, Q);
-                printf("%s{\"Ty\": %d, \"Rx\": %d, \"xt\": %d, \"ct\": %d, \"g\": %d, \"occ\": %d, \"pTy\": %d, \"pRx\": %d, "
+                printf("%s{\"Ty\": %d, \"Rx\": %d, \"xt\": %d, \"ct\": %d, \"g\": %d, \"occ\": %d, \"st\": %d, \"pTy\": %d, \"pRx\": %d, "
                        "\"smem\": [%zu,%zu,%zu,%zu,%zu,%zu], \"list\": %d}",
-                       i ? "," : "", c[i].Ty, c[i].Rx, c[i].x_threads, c[i].col_threads, c[i].col_group, c[i].col_occ, e.Ty, e.Rx,
+                       i ? "," : "", c[i].Ty, c[i].Rx, c[i].x_threads, c[i].col_threads, c[i].col_group, c[i].col_occ, c[i].x_stage, e.Ty, e.Rx,
                        Q.smem_x, Q.smem_xi, Q.smem_y13, Q.smem_z, Q.smem_y2, Q.smem_yzc,
                        plan_uses_yzc(e) ? plan_yzc_list(e, f32 != 0) : -1);
             }

@@ -30,7 +30,7 @@ def _tunings(nz):
     for ty, rx, xt in itertools.product((1, 2, 4, 8, 16, 32), (1, 3), (0, 128, 512)):
         for g, occ in (itertools.product((1, 2), (0, 3, 4)) if 1 < nz <= 8 else ((0, 0),)):
             yield {"Ty": ty, "Rx": rx, "x_threads": xt, "col_threads": xt if nz == 1 or nz > 8 else 0,
-                   "col_group": g, "col_occ": occ}
+                   "col_group": g, "col_occ": occ, "x_stage": (ty + rx) % 2}
 
 
 @pytest.mark.parametrize("precision", ["f32", "f64"])
@@ -103,3 +103,41 @@ def test_tuning_cache_round_trip(tmp_path):
     again = tuning.tune_context(ctx, [mesh], "gpu", reps=3, path=path)
     assert again[k]["cached"] is True and ctx.get_tuning(0) == t0
     ctx.close()
+
+
+@pytest.mark.parametrize("precision", ["f32", "f64"])
+@pytest.mark.parametrize("dims", [(64, 48, 3), (64, 40, 1), (32, 16, 12), (33, 17, 2), (48, 5, 4)])
+def test_staged_x_inverse_rows_are_bitwise_the_loaded_ones(precision, dims):
+    """The x-inverse pass with its state rows staged by bulk copies (x_stage = 1) computes
+    exactly what the direct loads give: right-hand side, energies and three RK45 attempts
+    bit for bit, and the oracle's field.  (33 cells a row in FP32 is 132 bytes, not a
+    multiple of 16: that mesh takes the direct loads whatever the tuning says.)"""
+    mesh = synth.Mesh(*dims, 2e-9, 2e-9, 1e-9)
+    sim = synth.Sim(mesh, _mat(), synth.random_state(19, mesh))
+    out = {}
+    for stage in (0, 1):
+        for rx in (1, 2, 5):
+            if rx > mesh.ny:
+                continue
+            ctx = mm.Context(precision)
+            ctx.add_sim(mesh, sim.mat)
+            ctx.set_tuning(0, {"Rx": rx, "x_stage": stage})
+            ctx.precompute()
+            assert ctx.get_tuning(0)["x_stage"] == stage
+            dmdt, heff = ctx.rhs_host(sim.m0.ravel())
+            ctx.set_m(sim.m0.ravel())
+            E = ctx.energy(0)
+            ctx.reset_time()
+            ctx.rk45_setup(1e-5 if precision == "f32" else 1e-6)
+            ctx.rk45_attempts(3)
+            out[(stage, rx)] = (dmdt, heff, E, ctx.get_m(0), ctx.status(0)["n_accepted"])
+            ctx.close()
+    ref_k, ref_H = oracle_rhs(sim, method="direct")
+    for (stage, rx), (dmdt, heff, E, m, nacc) in out.items():
+        base = out[(0, rx)]
+        assert np.array_equal(dmdt, base[0]) and np.array_equal(heff, base[1])
+        assert E == base[2] and np.array_equal(m, base[3]) and nacc == base[4]
+        if precision == "f64":
+            assert max_rel(heff, ref_H) < 1e-10
+        else:
+            assert rms_rel(heff, ref_H) < 1e-5

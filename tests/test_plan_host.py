@@ -151,6 +151,7 @@ def test_autotuner_candidates(probe):
             assert 1 <= Rx <= r["mesh"][1]
             sx, sxi, sy13, sz, sy2, syzc = c["smem"]
             assert max(sx, sxi) <= cap - 4096 and max(sy13, sz, sy2, syzc) <= cap
+            assert c["st"] in (0, 1)
             for th in (c["xt"], c["ct"]):
                 assert th == 0 or (th % 32 == 0 and 32 <= th <= maxth)
             if c["g"]:
