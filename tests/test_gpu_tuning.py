@@ -109,8 +109,8 @@ def test_tuning_cache_round_trip(tmp_path):
 @pytest.mark.parametrize("dims", [(64, 48, 3), (64, 40, 1), (32, 16, 12), (33, 17, 2), (48, 5, 4)])
 def test_staged_x_inverse_rows_are_bitwise_the_loaded_ones(precision, dims):
     """The x-inverse pass with its state rows staged by bulk copies (x_stage = 1) computes
-    exactly what the direct loads give: right-hand side, energies and three RK45 attempts
-    bit for bit, and the oracle's field.  (33 cells a row in FP32 is 132 bytes, not a
+    exactly what the direct loads give: right-hand side and three RK45 attempts bit for
+    bit, energies up to the order of their atomic FP64 sums, and the oracle's field.  (33 cells a row in FP32 is 132 bytes, not a
     multiple of 16: that mesh takes the direct loads whatever the tuning says.)"""
     mesh = synth.Mesh(*dims, 2e-9, 2e-9, 1e-9)
     sim = synth.Sim(mesh, _mat(), synth.random_state(19, mesh))
@@ -136,7 +136,10 @@ def test_staged_x_inverse_rows_are_bitwise_the_loaded_ones(precision, dims):
     for (stage, rx), (dmdt, heff, E, m, nacc) in out.items():
         base = out[(0, rx)]
         assert np.array_equal(dmdt, base[0]) and np.array_equal(heff, base[1])
-        assert E == base[2] and np.array_equal(m, base[3]) and nacc == base[4]
+        assert np.array_equal(m, base[3]) and nacc == base[4]
+        # energies are FP64 sums combined across CTAs by atomics: equal up to summation order
+        for k in E:
+            assert abs(E[k] - base[2][k]) <= 1e-12 * max(abs(v) for v in base[2].values())
         if precision == "f64":
             assert max_rel(heff, ref_H) < 1e-10
         else:
