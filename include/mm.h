@@ -171,6 +171,27 @@ int mm_get_tuning(const mm_ctx *ctx, int sim_id, mm_tuning *out);
  * scratch context allocates and frees device memory. */
 int mm_autotune(mm_ctx *ctx, int sim_id, int reps, mm_tuning *best, double *best_ms, double *rule_ms);
 
+/* Which kernels run the RK45 attempts of mm_rk45_attempts, mm_rk45_step and
+ * mm_relax (an implementation choice: the paper's integrator has no
+ * counterpart).  MM_ATTEMPT_AUTO (the default): when every simulation of the
+ * context has one plane and padded FFT lengths Px, Py <= 64 (at most 32 x 32
+ * cells), no extended terms (bulk / D_2d DMI, per-cell A or D, spin torques)
+ * and no NEB chain, the attempts run in ONE launch per call: one thread-block
+ * cluster per simulation keeps y_n, the stage vectors and both transform
+ * stages in shared memory and runs all n attempts of the call, with the same
+ * stage, error-norm, controller and projection arithmetic as the pass
+ * kernels; otherwise, and with MM_ATTEMPT_PASSES, every attempt replays the
+ * pass kernels from a CUDA graph.  kind = 2, 4, 8 or 16 chooses the single
+ * launch (where it applies) on a cluster of that many CTAs per simulation
+ * instead of the largest the device co-schedules (a tuning choice).  May be
+ * called at any time after mm_create; MM_EINVAL for another kind. */
+enum { MM_ATTEMPT_AUTO = 0, MM_ATTEMPT_PASSES = 1 };
+int mm_set_attempt_kernel(mm_ctx *ctx, int kind);
+/* The path the next attempt takes (after mm_precompute_demag): *single = 1 for
+ * the single launch (cluster: its CTAs per simulation), 0 for the pass kernels
+ * (cluster: 0).  Either pointer may be NULL. */
+int mm_get_attempt_kernel(mm_ctx *ctx, int *single, int *cluster);
+
 /* Applied field of one simulation (field sweeps, Listing 2), A/m. */
 int mm_set_field(mm_ctx *ctx, int sim_id, const double H[3]);
 

@@ -14,6 +14,7 @@
 #include <tuple>
 #include <vector>
 
+#include "attempt_small.h"
 #include "cayley.h"
 #include "engine.cuh"
 #include "minimize.h"
@@ -99,6 +100,11 @@ struct mm_ctx {
     long long launches = 0;
     bool neb = false;
     double tensor_imag_ratio = 0.0;
+    // single-launch attempts of small single-plane meshes (attempt_small.cu):
+    // MM_ATTEMPT_AUTO or MM_ATTEMPT_PASSES, and the resolved cluster and shared memory
+    int attempt_kernel = MM_ATTEMPT_AUTO;
+    int small_nc = -1;          // -1 not resolved yet, 0 not eligible
+    size_t small_smem = 0;
 };
 
 namespace {
@@ -271,6 +277,7 @@ int validate_items(mm_ctx* C) {
 }
 
 int upload_descs(mm_ctx* C) {
+    C->small_nc = -1;           // term flags may have changed: resolve the attempt path again
     std::vector<SimDesc> h(C->sims.size());
     for (size_t i = 0; i < C->sims.size(); ++i) h[i] = C->sims[i].d;
     CK(cudaMemcpyAsync(C->desc_d, h.data(), h.size() * sizeof(SimDesc), cudaMemcpyHostToDevice, C->stream));
@@ -412,7 +419,57 @@ int build_graph(mm_ctx* C) {
     return MM_OK;
 }
 
+// Whether every simulation can run its attempts in one launch (attempt_small.cu),
+// and on which cluster: the largest of 16, 8, 4, 2, 1 CTAs a simulation that the
+// device co-schedules.  When the whole batch fits on the SMs at one CTA each, the
+// dynamic shared memory is raised so that no two CTAs share an SM (the FP64
+// epilogue is bound by each SM's FP64 rate).
+void small_resolve(mm_ctx* C) {
+    C->small_nc = 0;
+    if (C->attempt_kernel == MM_ATTEMPT_PASSES || C->neb || C->sims.empty()) return;
+    for (const SimHost& s : C->sims)
+        if (!small_eligible(s.d)) return;
+    const int kind = C->precision == MM_F32 ? 0 : (C->dd ? 2 : 1);
+    const size_t ssz = C->esz, csz = C->precision == MM_F32 ? 4 : 8;
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, C->device);
+    const int top = C->attempt_kernel >= 2 ? C->attempt_kernel : kSmallMaxCluster;
+    for (int nc = top; nc >= 1; nc >>= 1) {
+        size_t smem = 0;
+        for (const SimHost& s : C->sims) smem = std::max(smem, small_smem_bytes(s.d, nc, ssz, csz));
+        if ((long long)C->sims.size() * nc <= sms) smem = std::max<size_t>(smem, 116 * 1024);
+        if (small_cluster_fits(kind, smem, nc)) {
+            C->small_nc = nc;
+            C->small_smem = smem;
+            return;
+        }
+    }
+}
+
 int launch_attempts(mm_ctx* C, long long n) {
+    if (C->small_nc < 0) small_resolve(C);
+    if (C->small_nc > 0 && !C->neb) {
+        SmallLaunch S;
+        S.stream = C->stream;
+        S.desc = C->desc_d;
+        S.state = C->state_d;
+        S.nsims = (int)C->sims.size();
+        S.m = C->m;
+        S.tensor = C->tens;
+        S.Ms = C->Msd;
+        S.tw = C->precision == MM_F32 ? C->twf : (C->dd ? C->twdd : C->twd);
+        S.kind = C->precision == MM_F32 ? 0 : (C->dd ? 2 : 1);
+        S.cluster = C->small_nc;
+        S.smem = C->small_smem;
+        for (long long done = 0; done < n;) {
+            const long long chunk = std::min<long long>(n - done, 1 << 30);
+            S.n_attempts = (int)chunk;
+            CK(small_attempts(S));
+            C->launches += 1;
+            done += chunk;
+        }
+        return MM_OK;
+    }
     int rc = build_graph(C);
     if (rc) return rc;
     for (long long i = 0; i < n; ++i) {
@@ -790,6 +847,25 @@ int mm_batch_layout(const mm_ctx* C, long long* offsets, long long* total) {
         off += 3LL * C->sims[i].d.ncells;
     }
     if (total) *total = off;
+    return MM_OK;
+}
+
+int mm_set_attempt_kernel(mm_ctx* C, int kind) {
+    if (!C) return MM_EINVAL;
+    if (kind != MM_ATTEMPT_AUTO && kind != MM_ATTEMPT_PASSES && kind != 2 && kind != 4 && kind != 8 && kind != 16)
+        return fail(C, MM_EINVAL, "attempt kernel must be MM_ATTEMPT_AUTO, MM_ATTEMPT_PASSES or 2, 4, 8, 16 CTAs");
+    C->attempt_kernel = kind;
+    C->small_nc = -1;
+    return MM_OK;
+}
+
+int mm_get_attempt_kernel(mm_ctx* C, int* single, int* cluster) {
+    int rc = check_ready(C);
+    if (rc) return rc;
+    if (C->small_nc < 0) small_resolve(C);
+    const bool one = C->small_nc > 0 && !C->neb;
+    if (single) *single = one ? 1 : 0;
+    if (cluster) *cluster = one ? C->small_nc : 0;
     return MM_OK;
 }
 

@@ -20,6 +20,7 @@ MM_OK, MM_EINVAL, MM_ENOMEM, MM_ECUDA, MM_ENAN, MM_ESTEP, MM_ETIMEOUT, MM_EBOUND
 MM_F64, MM_F32, MM_F64_NATIVE = 0, 1, 2
 PRECISIONS = {"f64": MM_F64, "f32": MM_F32, "f64_native": MM_F64_NATIVE}
 MM_HOST, MM_DEVICE = 0, 1
+MM_ATTEMPT_AUTO, MM_ATTEMPT_PASSES = 0, 1
 ENERGY_TERMS = ("exchange", "dmi", "uniaxial", "cubic", "zeeman", "demag", "total")
 
 
@@ -94,6 +95,8 @@ SIGNATURES = {
     "mm_set_tuning": (C.c_int, [_P, C.c_int, C.POINTER(mm_tuning)]),
     "mm_get_tuning": (C.c_int, [_P, C.c_int, C.POINTER(mm_tuning)]),
     "mm_autotune": (C.c_int, [_P, C.c_int, C.c_int, C.POINTER(mm_tuning), _D, _D]),
+    "mm_set_attempt_kernel": (C.c_int, [_P, C.c_int]),
+    "mm_get_attempt_kernel": (C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
 }
 
 _lib = None
@@ -269,6 +272,19 @@ class Context:
                                        _P(heff.data_ptr()) if heff is not None else None))
 
     # ---- integration
+    def set_attempt_kernel(self, passes=False, cluster=0):
+        """passes=True: every RK45 attempt runs the pass kernels; False: the library's rule
+        (one launch per call for small single-plane meshes), on `cluster` CTAs per
+        simulation (2, 4, 8 or 16; 0 = the largest the device co-schedules)."""
+        kind = MM_ATTEMPT_PASSES if passes else (cluster if cluster else MM_ATTEMPT_AUTO)
+        self._check(self.L.mm_set_attempt_kernel(self.h, kind))
+
+    def attempt_kernel(self):
+        """(single_launch, cluster CTAs per simulation) of the next attempt."""
+        one, nc = C.c_int(), C.c_int()
+        self._check(self.L.mm_get_attempt_kernel(self.h, C.byref(one), C.byref(nc)))
+        return bool(one.value), nc.value
+
     def rk45_setup(self, rtol, t_end=0.0, max_dmdt=0.0):
         self._check(self.L.mm_rk45_setup(self.h, rtol, t_end, max_dmdt))
 
