@@ -86,11 +86,90 @@ __device__ __forceinline__ void small_prologue(const S* yn, const S* kv, S* ys, 
     }
 }
 
+// Warp-level radix-2 FFTs over groups of L = 2^l <= 32 lanes (lane j of a group
+// holds element j): shuffles exchange the butterfly partners and w64 holds
+// W_64^q = exp(-2 pi i q / 64), so W_{2s}^r = w64[r 32 / s].  Unnormalised.
+template <typename C>
+__device__ __forceinline__ C shfl_xor_v(C v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
+template <>
+__device__ __forceinline__ dd shfl_xor_v<dd>(dd v, int m) {
+    return dd(__shfl_xor_sync(0xffffffffu, v.hi, m), __shfl_xor_sync(0xffffffffu, v.lo, m));
+}
+template <typename C>
+__device__ __forceinline__ C shfl_idx_v(C v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+template <>
+__device__ __forceinline__ dd shfl_idx_v<dd>(dd v, int src) {
+    return dd(__shfl_sync(0xffffffffu, v.hi, src), __shfl_sync(0xffffffffu, v.lo, src));
+}
+template <typename C, bool INV>
+__device__ __forceinline__ V2<C> w64_get(const V2<C>* w64, int q) {
+    V2<C> w = w64[q & 63];
+    if (INV) w.y = -w.y;
+    return w;
+}
+
+// Decimation in frequency: natural order in, bit-reversed order out, NV
+// independent sequences per lane advanced stage by stage (their shuffles and
+// products overlap).
+template <typename C, bool INV, int NV>
+__device__ __forceinline__ void warp_dif(V2<C> (&v)[NV], int l, int j, const V2<C>* w64) {
+    for (int t = l - 1; t >= 0; --t) {
+        const int s = 1 << t;
+        const bool up = (j & s) != 0;
+        const V2<C> w = w64_get<C, INV>(w64, (j & (s - 1)) << (5 - t));
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+            const V2<C> u = mk<C>(shfl_xor_v(v[i].x, s), shfl_xor_v(v[i].y, s));
+            v[i] = up ? cmul(u - v[i], w) : v[i] + u;
+        }
+    }
+}
+
+// Decimation in time: bit-reversed order in, natural order out.
+template <typename C, bool INV, int NV>
+__device__ __forceinline__ void warp_dit(V2<C> (&v)[NV], int l, int j, const V2<C>* w64) {
+    for (int t = 0; t < l; ++t) {
+        const int s = 1 << t;
+        const bool up = (j & s) != 0;
+        const V2<C> w = w64_get<C, INV>(w64, (j & (s - 1)) << (5 - t));
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+            const V2<C> u = mk<C>(shfl_xor_v(v[i].x, s), shfl_xor_v(v[i].y, s));
+            const V2<C> b = cmul(up ? v[i] : u, w);
+            const V2<C> a = up ? u : v[i];
+            v[i] = up ? a - b : a + b;
+        }
+    }
+}
+
+// H^ = -N^ M^ at bin (kx, ky) of a single-plane mesh (xz = yz = 0) from the
+// CTA's tensor columns ts[c][j][ky'] (c = xx, yy, zz, xy; ky' <= Py/2; xy odd in ky)
+template <typename C>
+__device__ __forceinline__ void small_tensor(const C* ts, int cb, int pyh, int j, int ky, int Py, V2<C>& a,
+                                             V2<C>& b, V2<C>& c) {
+    int kyh = ky;
+    bool neg = false;
+    if (ky > (Py >> 1)) { kyh = Py - ky; neg = true; }
+    const C xx = ts[(0 * cb + j) * pyh + kyh], yy = ts[(1 * cb + j) * pyh + kyh];
+    const C zz = ts[(2 * cb + j) * pyh + kyh];
+    C xy = ts[(3 * cb + j) * pyh + kyh];
+    if (neg) xy = -xy;
+    const V2<C> mx = a, my = b;
+    a = mk<C>(xx * mx.x + xy * my.x, xx * mx.y + xy * my.y);
+    b = mk<C>(xy * mx.x + yy * my.x, xy * mx.y + yy * my.y);
+    c = mk<C>(zz * c.x, zz * c.y);
+}
+
+// Column transforms per CTA: the items (kx column j, component c, half hf) --
+// hf < 2 for 64-point columns, whose even and odd bins are two 32-point
+// transforms, X[2k] = F32(x)[k] and X[2k+1] = F32(x W_64^n)[k] -- are spread over
+// all warps, kNV per lane group.
+constexpr int kNV = 3;
+
 template <typename C>
 __global__ void __launch_bounds__(kSmallThreads, 1) k_small_rk(SmallParams<C> p) {
     using S = StoreT<C>;
     using C2 = V2<C>;
-    constexpr int MLR = 3;                                // largest Stockham radix (log2): 8
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ unsigned long long red_u[32];
     __shared__ unsigned long long slot[2];                // this CTA's maxima as FP64 bits
@@ -98,26 +177,40 @@ __global__ void __launch_bounds__(kSmallThreads, 1) k_small_rk(SmallParams<C> p)
     const int nc = (int)cl.num_blocks(), rank = (int)cl.block_rank();
     const int sim = blockIdx.x / nc;
     const SimDesc& d = p.desc[sim];
-    const int nx = d.nx, ny = d.ny, Kx = d.Kx, lPy = d.lPy, Py = d.Py;
-    const int lLh = d.lPx - 1, Lh = 1 << lLh;
+    const int nx = d.nx, ny = d.ny, Kx = d.Kx, lPy = d.lPy, Py = d.Py, lPx = d.lPx;
+    const int lX = lPx - 1, LX = 1 << lX;                 // half-length x sequences
     const int RB = small_rows_per_cta(d, nc), CB = small_cols_per_cta(d, nc);
     const int r0 = rank * RB, nr = max(0, min(ny, r0 + RB) - r0);
     const int k0 = rank * CB, nk = max(0, min(Kx, k0 + CB) - k0);
     const int cs = RB * nx, slice = 3 * cs, ncell = nr * nx;
-    const int SK = padded_len(Kx), SP = padded_len(Py);
+    const int pyh = Py / 2 + 1;
+    const SmallLayout lay = small_layout(d, nc, sizeof(S), sizeof(C));
     S* yn = reinterpret_cast<S*>(smraw);
     S* kv = yn + slice;
     S* ysb = kv + 7 * slice;
     S* ep = ysb + 2 * slice;
-    C2* ra = reinterpret_cast<C2*>(smraw + ((13 * (size_t)slice * sizeof(S) + 15) & ~(size_t)15));
-    C2* rbuf = ra + 3 * RB * SK;
-    C2* ca = rbuf + 3 * RB * SK;
-    C2* cbuf = ca + 3 * CB * SP;
+    S* hd = ep + slice;
+    C2* rowX = reinterpret_cast<C2*>(smraw + lay.rows);   // [3 RB][Kx]
+    C2* colH = reinterpret_cast<C2*>(smraw + lay.cols);   // [3 CB][ny]
+    C2* colS = reinterpret_cast<C2*>(smraw + lay.spec);   // [3 CB][Py]
+    C2* colI = reinterpret_cast<C2*>(smraw + lay.half);   // [3 CB][2][32]
+    C2* w64 = reinterpret_cast<C2*>(smraw + lay.w64);
+    C* ts = reinterpret_cast<C*>(smraw + lay.tens);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     const long long N = d.ncells;
     S* gm = p.m + d.off + (long long)r0 * nx;
     for (int i = threadIdx.x; i < ncell; i += blockDim.x) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) yn[c * cs + i] = gm[c * N + i];
+    }
+    for (int q = threadIdx.x; q < 64; q += blockDim.x) w64[q] = p.tw[q << (MM_LOG2_LMAX - 6)];
+    const bool demag = (d.flags & F_DEMAG) != 0;
+    if (demag) {
+        const long long plane = (long long)d.Pzh * d.Pyh * d.Kx;
+        for (int i = threadIdx.x; i < 4 * nk * pyh; i += blockDim.x) {
+            const int c = i / (nk * pyh), rem = i - c * nk * pyh, j = rem / pyh, ky = rem - j * pyh;
+            ts[(c * CB + j) * pyh + ky] = p.tensor[d.tens_off + c * plane + (long long)ky * d.Kx + k0 + j];
+        }
     }
     SimState& G = p.state[sim];
     double t = G.t, h = G.h;
@@ -126,9 +219,8 @@ __global__ void __launch_bounds__(kSmallThreads, 1) k_small_rk(SmallParams<C> p)
     int status = G.status, accepted = 0;
     double err = G.err, maxk = G.maxk;
     unsigned long long err_bits = G.err_bits;
-    cl.sync();                                  // every CTA has read the state (and its y_n)
+    cl.sync();                                  // every CTA has read the state (and its tables)
 
-    const bool demag = (d.flags & F_DEMAG) != 0;
     const bool msarr = (d.flags & F_MSARR) != 0;
     const S* __restrict__ msg = msarr ? p.Ms + d.ms_off : nullptr;
     const Coef<S>& cf = coef<S>(d);
@@ -141,7 +233,15 @@ __global__ void __launch_bounds__(kSmallThreads, 1) k_small_rk(SmallParams<C> p)
     const bool prec = (d.flags & F_PREC) != 0, dmi = (d.flags & F_DMI) != 0;
     const bool do_ex = (d.flags & F_EX) != 0, do_uni = (d.flags & F_UNI) != 0, do_cub = (d.flags & F_CUB) != 0;
     const S e7 = (S)dp_e(6);
-    const C2* __restrict__ wsplit = p.tw + MM_LMAX + stw_base(1, d.lPx);   // W_Px^k, k < Lh
+    // lane groups of the x sequences (LX lanes each)
+    const int GX = 32 >> lX, gx = lane >> lX, jx = lane & (LX - 1);
+    const int nseqR = 3 * nr;
+    // column items: H halves of lY-point transforms, GY groups of LY lanes per warp
+    const int H = lPy == 6 ? 2 : 1;
+    const int lY = lPy == 6 ? 5 : lPy, LY = 1 << lY;
+    const int GY = 32 >> lY, gy = lane >> lY, jy = lane & (LY - 1);
+    const int nit = 3 * H * nk, nslot = (nit + GY - 1) / GY;
+    const int kyb = bitrev(jy, lY);             // the bin index (within its half) lane jy holds
     bool ran = false;
     int q = 0;                                  // right-hand sides evaluated: stage-state parity
 
@@ -161,110 +261,139 @@ __global__ void __launch_bounds__(kSmallThreads, 1) k_small_rk(SmallParams<C> p)
                 default: small_prologue<S, 7>(yn, kv, ys, ep, cs, ncell, hs); break;
             }
             __syncthreads();
-            // ---- 1. M = Ms y_s, zero-padded R2C along x of the CTA's rows
-            C2* Z = ra;
+            // ---- 1. M = Ms y_s, zero-padded R2C along x of the CTA's rows: lane n of a
+            // group packs z[n] = M[2n] + i M[2n+1] (zero for 2n >= nx, so the upper half
+            // is zero), FFT of length LX = Px/2, split into X_k, k = 0..LX
             if (demag) {
-                // z[n] = M[2n] + i M[2n+1], non-zero for n < Lh/2 only (the first
-                // Stockham stage does not read the upper half)
-                const int lhalf = lLh > 0 ? lLh - 1 : 0;
-                for (int id = threadIdx.x; id < (nr << lhalf); id += blockDim.x) {
-                    const int r = id >> lhalf, n = id & ((1 << lhalf) - 1);
-                    C2 val[3];
+                for (int base = warp * GX; base < nseqR; base += nwarp * GX) {     // warp-uniform
+                    const int qs = base + gx;
+                    const bool valid = qs < nseqR;
+                    const int r = valid ? qs / 3 : 0, c = valid ? qs - 3 * r : 0;
+                    C2 z[1] = {mk<C>((C)0, (C)0)};
+                    if (valid) {
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) val[c] = mk<C>((C)0, (C)0);
-#pragma unroll
-                    for (int h2 = 0; h2 < 2; ++h2) {
-                        const int x = 2 * n + h2;
-                        if (x < nx) {
-                            const int i = r * nx + x;
-                            const S ms = msarr ? msg[(long long)(r0 + r) * nx + x] : Msu;
-#pragma unroll
-                            for (int c = 0; c < 3; ++c) {
-                                const C mc = to_compute<C>(ms * ys[c * cs + i]);
-                                if (h2 == 0) val[c].x = mc; else val[c].y = mc;
+                        for (int h2 = 0; h2 < 2; ++h2) {
+                            const int x = 2 * jx + h2;
+                            if (x < nx) {
+                                const S ms = msarr ? msg[(long long)(r0 + r) * nx + x] : Msu;
+                                const C mc = to_compute<C>(ms * ys[c * cs + r * nx + x]);
+                                if (h2 == 0) z[0].x = mc; else z[0].y = mc;
                             }
                         }
                     }
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) ra[(3 * r + c) * SK + ix<true>(n, 1)] = val[c];
-                }
-                __syncthreads();
-                Z = stockham_fft<C, false, MLR, true, false>(ra, rbuf, lLh, 3 * nr, SK, p.tw);
-                // split into X_k, k = 0..Lh, in place: the item of k reads Z_k and Z_{Lh-k}
-                // and writes X_k and X_{Lh-k} (and X_Lh for k = 0), so items never overlap
-                const int lhl = lLh > 0 ? lLh - 1 : 0;
-                const int hl = lLh > 0 ? 1 << lhl : 0;
-                const int nseq = 3 * nr;
-                const int totp = lLh > 0 ? nseq << lhl : 0;
-                for (int id = threadIdx.x; id < totp + nseq; id += blockDim.x) {
-                    int qq, k;
-                    if (id < totp) { qq = id >> lhl; k = id & (hl - 1); } else { qq = id - totp; k = hl; }
-                    const int kp = Lh - k;
-                    C2* s = Z + qq * SK;
-                    const C2 Zk = s[ix<true>(k & (Lh - 1), 1)];
-                    const C2 Zm = cconj(s[ix<true>(kp & (Lh - 1), 1)]);
-                    const C2 E = cscale(Zk + Zm, (C)0.5);
-                    const C2 Dd = Zk - Zm;
+                    warp_dif<C, false, 1>(z, lX, jx, w64);          // lane jx: Z_k, k = bitrev(jx)
+                    const int k = bitrev(jx, lX);
+                    const int src = (gx << lX) + bitrev((LX - k) & (LX - 1), lX);
+                    const C2 Zm = cconj(mk<C>(shfl_idx_v(z[0].x, src), shfl_idx_v(z[0].y, src)));
+                    const C2 E = cscale(z[0] + Zm, (C)0.5);
+                    const C2 Dd = z[0] - Zm;
                     const C2 O = mk<C>(Dd.y * (C)0.5, -Dd.x * (C)0.5);
-                    const C2 xk = E + cmul(k < Lh ? wsplit[k] : mk<C>((C)-1, (C)0), O);
-                    if (kp != k) s[ix<true>(kp, 1)] = cconj(E) + cmul(kp < Lh ? wsplit[kp] : mk<C>((C)-1, (C)0), cconj(O));
-                    s[ix<true>(k, 1)] = xk;
+                    if (valid) {
+                        C2* row = rowX + qs * Kx;
+                        row[k] = E + cmul(w64_get<C, false>(w64, k << (6 - lPx)), O);
+                        if (k == 0) row[LX] = E - O;
+                    }
                 }
             }
             cl.sync();                          // A: every row spectrum in place
-            // ---- 2. columns: FFT along y, tensor product, inverse along y
-            C2* Hc = ca;
+            // ---- 2. columns: FFT along y of the ny non-zero rows, H^ = -N^ M^ per bin,
+            // inverse along y, the ny rows kept
             if (demag) {
-                const int nld = Py > 1 ? Py >> 1 : 1;
-                const int tot = 3 * nk * nld;
-                for (int id = threadIdx.x; id < tot; id += blockDim.x) {
-                    const int qc = id / nld, y = id - qc * nld;   // qc = 3 j + c
-                    const int j = qc / 3, c = qc - 3 * j;
-                    C2 v = mk<C>((C)0, (C)0);
-                    if (y < ny) {
-                        const int ow = y / RB;
-                        const C2* src = cl.map_shared_rank(Z, ow);
-                        v = src[(3 * (y - ow * RB) + c) * SK + ix<true>(k0 + j, 1)];
+                for (int b0 = warp * kNV; b0 < nslot; b0 += nwarp * kNV) {           // warp-uniform
+                    C2 v[kNV];
+                    int it[kNV];
+#pragma unroll
+                    for (int u = 0; u < kNV; ++u) {
+                        it[u] = (b0 + u) * GY + gy;
+                        v[u] = mk<C>((C)0, (C)0);
+                        if (it[u] < nit && jy < ny) {
+                            const int j = it[u] / (3 * H), c = (it[u] / H) % 3, hf = it[u] % H;
+                            const int ow = jy / RB;
+                            v[u] = cl.map_shared_rank(rowX, ow)[(3 * (jy - ow * RB) + c) * Kx + k0 + j];
+                            if (hf) v[u] = cmul(v[u], w64_get<C, false>(w64, jy));
+                        }
                     }
-                    ca[qc * SP + ix<true>(y, 1)] = v;
+                    warp_dif<C, false, kNV>(v, lY, jy, w64);
+#pragma unroll
+                    for (int u = 0; u < kNV; ++u) {
+                        if (it[u] < nit) {
+                            const int j = it[u] / (3 * H), c = (it[u] / H) % 3, hf = it[u] % H;
+                            colS[(3 * j + c) * Py + H * kyb + hf] = v[u];
+                        }
+                    }
                 }
                 __syncthreads();
-                C2* Y = stockham_fft<C, false, MLR, true, false>(ca, cbuf, lPy, 3 * nk, SP, p.tw);
-                for (int id = threadIdx.x; id < nk * Py; id += blockDim.x) {
-                    const int j = id / Py, ky = id - j * Py;
-                    const int pk = ix<true>(ky, 1);
-                    C2* s0 = Y + (3 * j) * SP;
-                    C2 a = s0[pk], b = s0[SP + pk], c = s0[2 * SP + pk];
-                    tensor_apply<C>(d, p.tensor, k0 + j, ky, 0, a, b, c);
-                    s0[pk] = a; s0[SP + pk] = b; s0[2 * SP + pk] = c;
+                for (int b = threadIdx.x; b < nk * Py; b += blockDim.x) {
+                    const int j = b / Py, ky = b - j * Py;
+                    C2* s0 = colS + 3 * j * Py + ky;
+                    C2 a = s0[0], bb = s0[Py], cc = s0[2 * Py];
+                    small_tensor<C>(ts, CB, pyh, j, ky, Py, a, bb, cc);
+                    s0[0] = a; s0[Py] = bb; s0[2 * Py] = cc;
                 }
                 __syncthreads();
-                Hc = stockham_fft<C, true, MLR, false, true>(Y, Y == ca ? cbuf : ca, lPy, 3 * nk, SP, p.tw);
+                for (int b0 = warp * kNV; b0 < nslot; b0 += nwarp * kNV) {
+                    C2 v[kNV];
+                    int it[kNV];
+#pragma unroll
+                    for (int u = 0; u < kNV; ++u) {
+                        it[u] = (b0 + u) * GY + gy;
+                        v[u] = mk<C>((C)0, (C)0);
+                        if (it[u] < nit) {
+                            const int j = it[u] / (3 * H), c = (it[u] / H) % 3, hf = it[u] % H;
+                            v[u] = colS[(3 * j + c) * Py + H * kyb + hf];   // bit-reversed order in
+                        }
+                    }
+                    warp_dit<C, true, kNV>(v, lY, jy, w64);                 // natural order out
+#pragma unroll
+                    for (int u = 0; u < kNV; ++u) {
+                        if (it[u] < nit) {
+                            const int j = it[u] / (3 * H), c = (it[u] / H) % 3, hf = it[u] % H;
+                            if (H == 1) {
+                                if (jy < ny) colH[(3 * j + c) * ny + jy] = v[u];
+                            } else {
+                                colI[((3 * j + c) * 2 + hf) * 32 + jy] = v[u];
+                            }
+                        }
+                    }
+                }
+                if (H == 2) {
+                    // x[n] = F32^-1(X[2k])[n] + W_64^-n F32^-1(X[2k+1])[n], n < ny <= 32
+                    __syncthreads();
+                    for (int b = threadIdx.x; b < 3 * nk * ny; b += blockDim.x) {
+                        const int qc = b / ny, n = b - qc * ny;
+                        colH[qc * ny + n] = colI[(2 * qc) * 32 + n] +
+                                            cmul(colI[(2 * qc + 1) * 32 + n], w64_get<C, true>(w64, n));
+                    }
+                }
             }
             cl.sync();                          // B: every column transformed back
-            // ---- 3. rows: inverse C2R along x, local fields, torque
-            const C2* Hd = ra;
+            // ---- 3. rows: Hermitian split and inverse C2R along x (lane j of a group
+            // forms Z_k, k = bitrev(j), from the column owners' X_k and X_{LX-k}, so the
+            // decimation-in-time inverse leaves z[n] in lane n: cells 2n and 2n + 1)
             if (demag) {
-                for (int id = threadIdx.x; id < 3 * nr * Kx; id += blockDim.x) {
-                    const int qq = id / Kx, k = id - qq * Kx;
-                    const int r = qq / 3, c = qq - 3 * r;
-                    const int ow = k / CB;
-                    const C2* src = cl.map_shared_rank(Hc, ow);
-                    ra[qq * SK + ix<true>(k, 1)] = src[(3 * (k - ow * CB) + c) * SP + ix<true>(r0 + r, 1)];
+                for (int base = warp * GX; base < nseqR; base += nwarp * GX) {
+                    const int qs = base + gx;
+                    const bool valid = qs < nseqR;
+                    const int r = valid ? qs / 3 : 0, c = valid ? qs - 3 * r : 0;
+                    C2 z[1] = {mk<C>((C)0, (C)0)};
+                    const int k = bitrev(jx, lX);
+                    if (valid) {
+                        const int ka = k, kb = LX - k;
+                        const int oa = ka / CB, ob = kb / CB;
+                        const C2 Xa = cl.map_shared_rank(colH, oa)[(3 * (ka - oa * CB) + c) * ny + r0 + r];
+                        const C2 Xb = cconj(cl.map_shared_rank(colH, ob)[(3 * (kb - ob * CB) + c) * ny + r0 + r]);
+                        const C2 e = Xa + Xb;
+                        const C2 tq = cmul(w64_get<C, true>(w64, k << (6 - lPx)), Xa - Xb);
+                        z[0] = mk<C>(e.x - tq.y, e.y + tq.x);
+                    }
+                    warp_dit<C, true, 1>(z, lX, jx, w64);
+                    if (valid) {
+                        const int x = 2 * jx;
+                        if (x < nx) hd[c * cs + r * nx + x] = to_store<C>(z[0].x);
+                        if (x + 1 < nx) hd[c * cs + r * nx + x + 1] = to_store<C>(z[0].y);
+                    }
                 }
                 __syncthreads();
-                // Hermitian split: Z_k = (X_k + X*_{Lh-k}) + i W^{-k} (X_k - X*_{Lh-k}), k < Lh
-                for (int id = threadIdx.x; id < ((3 * nr) << lLh); id += blockDim.x) {
-                    const int qq = id >> lLh, k = id & (Lh - 1);
-                    const C2* s = ra + qq * SK;
-                    const C2 Xa = s[ix<true>(k, 1)], Xb = cconj(s[ix<true>(Lh - k, 1)]);
-                    const C2 e = Xa + Xb;
-                    const C2 tq = cmul(stw_get<C, true>(wsplit, k), Xa - Xb);
-                    rbuf[qq * SK + ix<true>(k, 1)] = mk<C>(e.x - tq.y, e.y + tq.x);
-                }
-                __syncthreads();
-                // only z[n], n < ceil(nx/2) <= Lh/2, is read: half-output last stage
-                Hd = stockham_fft<C, true, MLR, false, true>(rbuf, ra, lLh, 3 * nr, SK, p.tw);
             }
             S* ko = kv + (st - 1) * slice;
             unsigned long long vmax = 0ull;
@@ -276,15 +405,7 @@ __global__ void __launch_bounds__(kSmallThreads, 1) k_small_rk(SmallParams<C> p)
                 if (ms > (S)0) {
                     const S inv = msarr ? (S)1 / (mu0 * ms) : inv_u;
                     S hd0 = 0, hd1 = 0, hd2 = 0;
-                    if (demag) {
-                        const int pos = ix<true>(x >> 1, 1);
-                        const C2 v0 = Hd[(3 * r + 0) * SK + pos];
-                        const C2 v1 = Hd[(3 * r + 1) * SK + pos];
-                        const C2 v2 = Hd[(3 * r + 2) * SK + pos];
-                        hd0 = to_store<C>((x & 1) ? v0.y : v0.x);
-                        hd1 = to_store<C>((x & 1) ? v1.y : v1.x);
-                        hd2 = to_store<C>((x & 1) ? v2.y : v2.x);
-                    }
+                    if (demag) { hd0 = hd[i]; hd1 = hd[cs + i]; hd2 = hd[2 * cs + i]; }
                     S ex0 = 0, ex1 = 0, ex2 = 0, dm0 = 0, dm1 = 0, dm2 = 0;
                     if (do_ex || dmi) {
                         // neighbours -x, +x, -y, +y (one plane: no z neighbours); a missing

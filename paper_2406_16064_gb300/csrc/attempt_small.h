@@ -25,16 +25,39 @@ inline bool small_eligible(const SimDesc& d) {
 __host__ __device__ inline int small_rows_per_cta(const SimDesc& d, int nc) { return (d.ny + nc - 1) / nc; }
 __host__ __device__ inline int small_cols_per_cta(const SimDesc& d, int nc) { return (d.Kx + nc - 1) / nc; }
 
-// Dynamic shared memory of one CTA (element sizes of the storage and of the
-// compute type): 13 state slices [3][rb nx] (y_n, k_1..k_7, two stage states,
-// the stage-7 error sum), then two row buffers of 3 rb padded sequences of Kx
-// complex values and two column buffers of 3 cb padded sequences of Py.
-inline size_t small_smem_bytes(const SimDesc& d, int nc, size_t ssz, size_t csz) {
+// Shared-memory layout of one CTA of a cluster of nc CTAs (element sizes of the
+// storage and of the compute type), identical in every CTA of the cluster: 14
+// state slices [3][rb nx] of the storage type (y_n, k_1..k_7, two stage states,
+// the stage-7 error sum, the demagnetising field), then (complex) the
+// x-transformed rows [3 rb][Kx], the y-inverse-transformed columns [3 cb][ny],
+// the y spectra of the CTA's columns [3 cb][Py], the two half-length inverses
+// of 64-point columns [3 cb][2][32], the table W_64^q, and (real) the tensor of
+// the CTA's kx columns [4][cb][Py/2 + 1].
+struct SmallLayout {
+    size_t rows, cols, spec, half, w64, tens, total;    // byte offsets and the total
+};
+__host__ __device__ inline SmallLayout small_layout(const SimDesc& d, int nc, size_t ssz, size_t csz) {
     const int rb = small_rows_per_cta(d, nc), cb = small_cols_per_cta(d, nc);
-    size_t b = ((13 * 3 * (size_t)rb * d.nx * ssz) + 15) & ~(size_t)15;
-    b += 2 * 3 * (size_t)rb * padded_len(d.Kx) * 2 * csz;
-    b += 2 * 3 * (size_t)cb * padded_len(d.Py) * 2 * csz;
-    return b;
+    const size_t z = 2 * csz;
+    SmallLayout L;
+    size_t b = ((14 * 3 * (size_t)rb * d.nx * ssz) + 15) & ~(size_t)15;
+    L.rows = b;
+    b += 3 * (size_t)rb * d.Kx * z;
+    L.cols = b;
+    b += 3 * (size_t)cb * d.ny * z;
+    L.spec = b;
+    b += 3 * (size_t)cb * d.Py * z;
+    L.half = b;
+    b += (d.Py == 64 ? 3 * (size_t)cb * 64 : 0) * z;
+    L.w64 = b;
+    b += 64 * z;
+    L.tens = b;
+    b += 4 * (size_t)cb * (d.Py / 2 + 1) * csz;
+    L.total = (b + 15) & ~(size_t)15;
+    return L;
+}
+inline size_t small_smem_bytes(const SimDesc& d, int nc, size_t ssz, size_t csz) {
+    return small_layout(d, nc, ssz, csz).total;
 }
 
 struct SmallLaunch {
