@@ -243,6 +243,24 @@ int mm_get_m(mm_ctx *ctx, int sim_id, void *m, int where);
  * spin torques are not fields).  Asynchronous on the context stream. */
 int mm_rhs_eval(mm_ctx *ctx, int sim_id, const void *m_dev, void *dmdt_dev, void *heff_dev);
 
+/* Demagnetising field of one simulation through the magnetic scalar potential
+ * (Sec. "Magnetostatic energy": with the scalar potential the three inverse
+ * transforms reduce to one): u_i = sum_j S(r_i - r_j) . Ms_j m_j with S_c the
+ * exact potential of a cell magnetised along c (the potential of its two
+ * charged c-faces), evaluated by zero-padded FFTs on a grid padded to the
+ * smallest power of two >= 2n + 1 per axis (three forward transforms of M,
+ * one inverse of u), then H_d = -grad u by central differences, u taken one
+ * cell outside the mesh where a neighbour lies outside.  This is a different
+ * discretisation from the Newell field of mm_rhs_eval: the two agree inside
+ * smooth magnetisation to second order in the cell size and differ by tens of
+ * percent of Ms at charged surfaces.  m_dev in, hd_dev out, caller-owned
+ * device buffers [3][nz][ny][nx] in the context precision (FP64 contexts
+ * compute in FP64); asynchronous on the context stream.  The kernel spectrum
+ * is computed (FP64) and kept on the first call for each geometry, which
+ * allocates device memory.  MM_EINVAL for a padded length above 2048 (an axis
+ * of more than 1023 cells). */
+int mm_demag_potential(mm_ctx *ctx, int sim_id, const void *m_dev, void *hd_dev);
+
 /* The same evaluation with host double buffers (copies inside the call). */
 int mm_rhs_eval_host(mm_ctx *ctx, int sim_id, const double *m_host, double *dmdt_host,
                      double *heff_host);

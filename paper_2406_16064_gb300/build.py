@@ -18,7 +18,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmm.so")
 SOURCES = ["api.cu", "engine_f32.cu", "engine_f64.cu", "engine_dd.cu", "newell.cu", "static_rhs.cu", "minimize.cu",
            "cayley.cu", "attempt_small_f32.cu",
-           "attempt_small_f64.cu", "attempt_small_dd.cu"]
+           "attempt_small_f64.cu", "attempt_small_dd.cu", "potential.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

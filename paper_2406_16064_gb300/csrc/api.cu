@@ -18,6 +18,7 @@
 #include "cayley.h"
 #include "engine.cuh"
 #include "minimize.h"
+#include "potential.h"
 #include "mm.h"
 #include "plan.h"
 
@@ -105,6 +106,9 @@ struct mm_ctx {
     int attempt_kernel = MM_ATTEMPT_AUTO;
     int small_nc = -1;          // -1 not resolved yet, 0 not eligible
     size_t small_smem = 0;
+    // scalar-potential demag (potential.cu): kernel spectrum and work buffers per geometry
+    struct PotPlan { PotGeom g; PotBuffers b; };
+    std::vector<PotPlan> pot;
 };
 
 namespace {
@@ -608,6 +612,10 @@ int mm_destroy(mm_ctx* C) {
                     C->zi, C->y2i, C->flag_d, C->status_d, C->diag_d, C->sd_H, C->sd_mprev, C->sd_g,
                     C->sd_d};
     for (void* p : ptrs) if (p) cudaFree(p);
+    for (auto& pp : C->pot) {
+        void* pb[] = {pp.b.Shat, pp.b.Mhat, pp.b.U, pp.b.u};
+        for (void* p : pb) if (p) cudaFree(p);
+    }
     if (C->host_stage) cudaFreeHost(C->host_stage);
     for (int j = 0; j < 7; ++j) if (C->k[j]) cudaFree(C->k[j]);
     for (int li = 0; li < kYzcListCount; ++li) if (C->yzci[li]) cudaFree(C->yzci[li]);
@@ -1168,6 +1176,58 @@ int mm_rhs_eval(mm_ctx* C, int sim, const void* m_dev, void* dmdt_dev, void* hef
     else
         engine_rhs<double>(L, 0, (const double*)m_dev, (double*)dmdt_dev, (double*)heff_dev, adj);
     CK(cudaGetLastError());
+    return MM_OK;
+}
+
+int mm_demag_potential(mm_ctx* C, int sim, const void* m_dev, void* hd_dev) {
+    int rc = check_ready(C);
+    if (rc) return rc;
+    if (!m_dev || !hd_dev || sim < 0 || sim >= (int)C->sims.size()) return fail(C, MM_EINVAL, "bad arguments");
+    const SimHost& S = C->sims[sim];
+    const PotGeom g = pot_geometry(S.mesh.nx, S.mesh.ny, S.mesh.nz, S.mesh.dx, S.mesh.dy, S.mesh.dz);
+    if (g.Px > kPotMaxP || g.Py > kPotMaxP || g.Pz > kPotMaxP)
+        return fail(C, MM_EINVAL, "scalar-potential demag: padded length %d x %d x %d above %d (mesh axes <= %d cells)",
+                    g.Px, g.Py, g.Pz, kPotMaxP, kPotMaxP / 2 - 1);
+    const bool f32 = C->precision == MM_F32;
+    const size_t cz = 2 * C->esz;             // complex value in the context precision
+    mm_ctx::PotPlan* P = nullptr;
+    for (auto& pp : C->pot)
+        if (pp.g.nx == g.nx && pp.g.ny == g.ny && pp.g.nz == g.nz && pp.g.dx == g.dx && pp.g.dy == g.dy &&
+            pp.g.dz == g.dz)
+            P = &pp;
+    if (!P) {
+        mm_ctx::PotPlan np;
+        np.g = g;
+        const long long nb = pot_bins(g);
+        if ((rc = dalloc(C, &np.b.Shat, 3 * nb * cz))) return rc;
+        if ((rc = dalloc(C, &np.b.Mhat, 3 * nb * cz)) || (rc = dalloc(C, &np.b.U, nb * cz)) ||
+            (rc = dalloc(C, &np.b.u, pot_ext_cells(g) * C->esz))) {
+            void* pb[] = {np.b.Shat, np.b.Mhat, np.b.U, np.b.u};
+            for (void* p : pb) if (p) cudaFree(p);
+            return rc;
+        }
+        void* s64 = nullptr;
+        if ((rc = dalloc(C, &s64, 3 * nb * 16))) {
+            void* pb[] = {np.b.Shat, np.b.Mhat, np.b.U, np.b.u};
+            for (void* p : pb) if (p) cudaFree(p);
+            return rc;
+        }
+        cudaError_t e = pot_precompute(C->stream, g, np.b.Shat, f32, s64, C->twd, &C->launches);
+        cudaStreamSynchronize(C->stream);
+        cudaFree(s64);
+        if (e != cudaSuccess) {
+            void* pb[] = {np.b.Shat, np.b.Mhat, np.b.U, np.b.u};
+            for (void* p : pb) if (p) cudaFree(p);
+            return fail(C, MM_ECUDA, "scalar-potential kernel spectrum: %s", cudaGetErrorString(e));
+        }
+        C->pot.push_back(np);
+        P = &C->pot.back();
+    }
+    const SimDesc& d = S.d;
+    const void* Ms = (d.flags & F_MSARR) ? (const char*)C->Msd + d.ms_off * C->esz : nullptr;
+    const void* tw = f32 ? C->twf : C->twd;
+    cudaError_t e = pot_field(C->stream, P->g, P->b, f32, m_dev, Ms, d.Ms, hd_dev, tw, &C->launches);
+    if (e != cudaSuccess) return fail(C, MM_ECUDA, "scalar-potential demag: %s", cudaGetErrorString(e));
     return MM_OK;
 }
 

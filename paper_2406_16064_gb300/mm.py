@@ -96,6 +96,7 @@ SIGNATURES = {
     "mm_get_tuning": (C.c_int, [_P, C.c_int, C.POINTER(mm_tuning)]),
     "mm_autotune": (C.c_int, [_P, C.c_int, C.c_int, C.POINTER(mm_tuning), _D, _D]),
     "mm_set_attempt_kernel": (C.c_int, [_P, C.c_int]),
+    "mm_demag_potential": (C.c_int, [_P, C.c_int, _P, _P]),
     "mm_get_attempt_kernel": (C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
 }
 
@@ -270,6 +271,11 @@ class Context:
     def rhs_device(self, m, dmdt, heff=None, sim=-1):
         self._check(self.L.mm_rhs_eval(self.h, sim, _P(m.data_ptr()), _P(dmdt.data_ptr()),
                                        _P(heff.data_ptr()) if heff is not None else None))
+
+    def demag_potential(self, m, hd, sim):
+        """Scalar-potential demag field of simulation sim: torch CUDA tensors m (in) and hd
+        (out), [3][N] in the context precision."""
+        self._check(self.L.mm_demag_potential(self.h, sim, _P(m.data_ptr()), _P(hd.data_ptr())))
 
     # ---- integration
     def set_attempt_kernel(self, passes=False, cluster=0):
