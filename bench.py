@@ -837,6 +837,56 @@ def run_cufft_compare(args, rank, world, dist):
             "ours_vs_cufft_conv": t_conv / t_ours, "gpu_launches": launches}
 
 
+def run_potential(args, rank, world, dist):
+    """The demagnetising field through the magnetic scalar potential (mm_demag_potential:
+    three forward transforms of M, one inverse of u, on a grid padded to 2^k >= 2n + 1)
+    against the Newell right-hand side (mm_rhs_eval: three forward, tensor product,
+    three inverse on 2^k >= 2n - 1, plus every local term and the torque) on the
+    workload's first simulation; cell-updates/s of each."""
+    import torch
+    from paper_2406_16064_gb300 import mm
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    w = workload(args.workload, world)
+    prec = args.precision or ("f64" if args.workload == "film_relax_32" else "f32")
+    s = w.sims[0]
+    rdt = torch.float32 if prec == "f32" else torch.float64
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    ctx = mm.Context(prec, stream=stream.cuda_stream)
+    ctx.add_sim(s.mesh, s.mat, s.Ms_cells)
+    ctx.precompute()
+    mt = torch.tensor(s.m0.ravel(), dtype=rdt, device="cuda")
+    a, b = torch.empty_like(mt), torch.empty_like(mt)
+    ctx.demag_potential(mt, a, 0)               # first call: kernel spectrum (FP64)
+    torch.cuda.synchronize()
+
+    def timed(fn, reps):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        st, en = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        st.record(stream)
+        for _ in range(reps):
+            fn()
+        en.record(stream)
+        en.synchronize()
+        return st.elapsed_time(en) / reps
+
+    reps = max(10, args.steps)
+    n0 = ctx.launches()
+    t_pot = timed(lambda: ctx.demag_potential(mt, a, 0), reps)
+    lp = (ctx.launches() - n0) / (reps + 3)
+    t_newell = timed(lambda: ctx.rhs_device(mt, b, None), reps)
+    n = s.mesh.ncells
+    P = [1 << (2 * v).bit_length() for v in (s.mesh.nx, s.mesh.ny, s.mesh.nz)]
+    ctx.close()
+    return {"metric": "demag field evaluations, scalar potential vs Newell right-hand side", "unit": "cell-updates/s",
+            "higher_is_better": True, "n_gpus": 1, "dtype": prec, "data": "synthetic",
+            "config": {"workload": w.name, "cells": n, "potential_padded_grid_xyz": P},
+            "value": n / (t_pot / 1e3), "potential_ms": t_pot, "potential_launches": lp,
+            "newell_rhs_ms": t_newell, "newell_rhs_value": n / (t_newell / 1e3)}
+
+
 def run_relax_compare(args, rank, world, dist):
     """Wall time to relax the workload from its start below --max-dmdt (rad/s): RK45
     (mm_relax, the workload's rtol) against steepest descent (mm_minimize)."""
@@ -891,7 +941,7 @@ def main():
     ap.add_argument("--sweep-n", default=None, help="comma-separated N for --workload sweep")
     ap.add_argument("--driver", default="rk45",
                     help="rk45 (default), sd (steepest-descent steps), relax-compare, rk4-cayley, "
-                         "rk4-proj, cayley-error or cufft-compare")
+                         "rk4-proj, cayley-error, cufft-compare or potential")
     ap.add_argument("--max-dmdt", type=float, default=1e7, help="relax-compare threshold, rad/s")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the fixed tile rules instead of the autotuned (cached) tiles")
@@ -920,6 +970,8 @@ def main():
             line = run_relax_compare(args, rank, world, dist) if rank == 0 else None
         elif args.driver == "cufft-compare":
             line = run_cufft_compare(args, rank, world, dist) if rank == 0 else None
+        elif args.driver == "potential":
+            line = run_potential(args, rank, world, dist) if rank == 0 else None
         else:
             line = (run_sweep if args.workload == "sweep" else run_gpu)(args, rank, world, dist)
         if dist:

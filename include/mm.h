@@ -179,8 +179,10 @@ int mm_autotune(mm_ctx *ctx, int sim_id, int reps, mm_tuning *best, double *best
  * and no NEB chain, the attempts run in ONE launch per call: one thread-block
  * cluster per simulation keeps y_n, the stage vectors and both transform
  * stages in shared memory and runs all n attempts of the call, with the same
- * stage, error-norm, controller and projection arithmetic as the pass
- * kernels; otherwise, and with MM_ATTEMPT_PASSES, every attempt replays the
+ * stage, error-norm, controller and projection arithmetic as the pass kernels
+ * (the controller's err^-1/5 from a Newton-refined fifth root, within two ulps
+ * of pow) and its transforms as warp-shuffle FFTs in the context's transform
+ * precision; otherwise, and with MM_ATTEMPT_PASSES, every attempt replays the
  * pass kernels from a CUDA graph.  kind = 2, 4, 8 or 16 chooses the single
  * launch (where it applies) on a cluster of that many CTAs per simulation
  * instead of the largest the device co-schedules (a tuning choice).  May be

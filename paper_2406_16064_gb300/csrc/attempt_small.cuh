@@ -6,36 +6,45 @@
 // memory of one thread-block cluster, so one cluster per simulation runs n
 // attempts of the adaptive Dormand-Prince RK45 (Sec. "LLG equation") without
 // leaving the chip.  CTA b of the cluster owns a block of rows and a block of
-// kx columns.  Per right-hand side:
+// column units (a kx column, or for 64-point columns one half of it: the even
+// or the odd ky bins, each a 32-point transform).  Per right-hand side:
 //   1. RK prologue y_s = y_n + h sum_j a_sj k_j on its rows (stage 7 also the
-//      error sum sum_{j<7} e_j k_j), M = Ms y_s, zero-padded R2C along x
-//      (half-length complex FFT + split, the zero upper half never read);
-//   2. cluster barrier; its kx columns gathered from the peers' row spectra
-//      (distributed shared memory), FFT along y (zero upper half skipped),
-//      H^ = -N^ M^ per bin (Eq. 8 in Fourier space), inverse along y with
-//      only the ny output rows formed;
-//   3. cluster barrier; its rows gathered back from the column owners,
-//      inverse C2R along x (only the nx outputs), then exchange (Eq. 5),
-//      interfacial DMI (Eq. 14), uniaxial and cubic anisotropy, Zeeman and the
-//      LL torque per cell, the stencil's +-y neighbours read from the peers'
-//      stage states.
+//      error sum sum_{j<7} e_j k_j); the block's first and last rows stored
+//      into the neighbouring CTAs' halo rows; M = Ms y_s and the zero-padded
+//      R2C along x (half-length complex FFT + split), each X_k stored into the
+//      shared memory of the owners of its column units (distributed shared
+//      memory);
+//   2. cluster barrier; per unit the FFT along y of the ny non-zero rows,
+//      H^ = -N^ M^ per bin (Eq. 8 in Fourier space), the inverse along y,
+//      its ny rows stored into their owners;
+//   3. cluster barrier; per row the inverse C2R along x (only the nx outputs),
+//      then exchange (Eq. 5), interfacial DMI (Eq. 14), uniaxial and cubic
+//      anisotropy, Zeeman and the LL torque per cell, the stencil's +-y
+//      neighbours from the block or its halo rows.
+// Every exchange between CTAs is a store into the consumer's shared memory
+// before a barrier, so every read after it is local.  The transforms are
+// warp-level radix-2 FFTs: a row or column lives in the registers of a lane
+// group, partners exchange by shuffles, forward transforms leave bit-reversed
+// order and inverse ones take it, so no permutation is ever formed.
 // The stage-1 max |dm/dt|^2 and the stage-7 error norm max |h sum e_j k_j|
-// are exact maxima over ordered bits: each CTA publishes its maximum in
-// shared memory and, after a barrier, every thread of every CTA reduces the
-// same values in the same order, so the whole cluster takes the same
-// decisions (initial step, relaxation stop, accept / reject, next h) with
-// the arithmetic of k_after_stage1 and k_controller; accepted steps project
+// are exact maxima over ordered bits: each CTA stores its maximum into every
+// CTA; after a barrier one thread per CTA reduces the same values in the same
+// order and takes the decisions (initial step, relaxation stop, accept /
+// reject, next h) with the arithmetic of k_after_stage1 and k_controller, so
+// every CTA of the cluster takes the same ones; accepted steps project
 // m = y5 / |y5| per cell.  y_n and the integration state go back to global
 // memory when the launch ends.
 //
 // Hazards between the cluster's CTAs are ordered by the two barriers of each
-// right-hand side: row spectra are read by peers only between barrier A and
-// B, column spectra only between B and the next A, and the stage states
-// alternate between two buffers, so a CTA overwrites the buffer its
-// neighbours read only after they passed the next barrier A; a last barrier
-// keeps every CTA resident until no peer reads its shared memory.  There are no
-// spin waits: every barrier is the hardware cluster barrier, reached the same
-// number of times by every CTA since their control decisions are identical.
+// right-hand side: a CTA stores into a peer's column inputs only after the
+// barrier B that follows the peer's reads of them, into its row inputs only
+// after the next barrier A, and the stage states and halo rows alternate
+// between two buffers by right-hand-side parity, so a buffer a neighbour reads
+// is overwritten only after that neighbour passed the next barrier A; a last
+// barrier keeps every CTA resident until no peer accesses its shared memory.
+// There are no spin waits: every barrier is the hardware cluster barrier,
+// reached the same number of times by every CTA since their control decisions
+// are identical.
 #pragma once
 #include <cooperative_groups.h>
 
@@ -142,29 +151,27 @@ __device__ __forceinline__ void warp_dit(V2<C> (&v)[NV], int l, int j, const V2<
     }
 }
 
-// H^ = -N^ M^ at bin (kx, ky) of a single-plane mesh (xz = yz = 0) from the
-// CTA's tensor columns ts[c][j][ky'] (c = xx, yy, zz, xy; ky' <= Py/2; xy odd in ky)
-template <typename C>
-__device__ __forceinline__ void small_tensor(const C* ts, int cb, int pyh, int j, int ky, int Py, V2<C>& a,
-                                             V2<C>& b, V2<C>& c) {
-    int kyh = ky;
-    bool neg = false;
-    if (ky > (Py >> 1)) { kyh = Py - ky; neg = true; }
-    const C xx = ts[(0 * cb + j) * pyh + kyh], yy = ts[(1 * cb + j) * pyh + kyh];
-    const C zz = ts[(2 * cb + j) * pyh + kyh];
-    C xy = ts[(3 * cb + j) * pyh + kyh];
-    if (neg) xy = -xy;
-    const V2<C> mx = a, my = b;
-    a = mk<C>(xx * mx.x + xy * my.x, xx * mx.y + xy * my.y);
-    b = mk<C>(xy * mx.x + yy * my.x, xy * mx.y + yy * my.y);
-    c = mk<C>(zz * c.x, zz * c.y);
+// The step-size factor clamp(0.9 err^-1/5, 0.2, 5) of the controller, with
+// err^-1/5 the root of y^-5 = err from an FP32 seed (relative error ~1e-7) by two
+// Newton steps y <- y (6 - err y^5) / 5, each squaring the relative error: within
+// an ulp or two of pow(err, -0.2) at a fraction of its FP64 instructions, which
+// run on the FP64 pipe of one thread between two cluster barriers.  Far outside
+// [(0.9/5)^5, (0.9/0.2)^5], where the clamp decides, the FP32 seed is not formed.
+__device__ __forceinline__ double step_factor(double err) {
+    if (err < 1e-30) return 5.0;
+    if (err > 1e30) return 0.2;
+    double y = (double)exp2f(-0.2f * log2f((float)err));
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+        const double y2 = y * y, y5 = y2 * y2 * y;
+        y = y * (6.0 - err * y5) * 0.2;
+    }
+    return fmin(5.0, fmax(0.2, 0.9 * y));
 }
 
-// Column transforms per CTA: the items (kx column j, component c, half hf) --
-// hf < 2 for 64-point columns, whose even and odd bins are two 32-point
-// transforms, X[2k] = F32(x)[k] and X[2k+1] = F32(x W_64^n)[k] -- are spread over
+// Column transforms per CTA: the items (unit j, component c) are spread over
 // all warps, kNV per lane group.
-constexpr int kNV = 3;
+constexpr int kNV = 2;
 
 template <typename C>
 __global__ void __launch_bounds__(kSmallThreads, 1) k_small_rk(SmallParams<C> p) {
@@ -172,30 +179,37 @@ __global__ void __launch_bounds__(kSmallThreads, 1) k_small_rk(SmallParams<C> p)
     using C2 = V2<C>;
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ unsigned long long red_u[32];
-    __shared__ unsigned long long slot[2];                // this CTA's maxima as FP64 bits
+    __shared__ unsigned long long slots[2][kSmallMaxCluster];   // every CTA's maxima, pushed by each CTA
+    __shared__ struct {
+        double t, h, err, maxk;
+        unsigned long long err_bits;
+        long long n_acc, n_rej;
+        int status, accepted;
+    } dec;                                                      // the step decision of thread 0
     cg::cluster_group cl = cg::this_cluster();
     const int nc = (int)cl.num_blocks(), rank = (int)cl.block_rank();
     const int sim = blockIdx.x / nc;
     const SimDesc& d = p.desc[sim];
-    const int nx = d.nx, ny = d.ny, Kx = d.Kx, lPy = d.lPy, Py = d.Py, lPx = d.lPx;
+    const int nx = d.nx, ny = d.ny, Kx = d.Kx, Py = d.Py, lPx = d.lPx;
     const int lX = lPx - 1, LX = 1 << lX;                 // half-length x sequences
-    const int RB = small_rows_per_cta(d, nc), CB = small_cols_per_cta(d, nc);
+    const int H = small_halves(d), LYh = Py / H;          // column units: halves of LYh points
+    const int lY = H == 2 ? 5 : d.lPy;
+    const int RB = small_rows_per_cta(d, nc), CU = small_units_per_cta(d, nc);
     const int r0 = rank * RB, nr = max(0, min(ny, r0 + RB) - r0);
-    const int k0 = rank * CB, nk = max(0, min(Kx, k0 + CB) - k0);
+    const int u0 = rank * CU, nu = max(0, min(Kx * H, u0 + CU) - u0);
     const int cs = RB * nx, slice = 3 * cs, ncell = nr * nx;
-    const int pyh = Py / 2 + 1;
     const SmallLayout lay = small_layout(d, nc, sizeof(S), sizeof(C));
     S* yn = reinterpret_cast<S*>(smraw);
     S* kv = yn + slice;
     S* ysb = kv + 7 * slice;
     S* ep = ysb + 2 * slice;
     S* hd = ep + slice;
-    C2* rowX = reinterpret_cast<C2*>(smraw + lay.rows);   // [3 RB][Kx]
-    C2* colH = reinterpret_cast<C2*>(smraw + lay.cols);   // [3 CB][ny]
-    C2* colS = reinterpret_cast<C2*>(smraw + lay.spec);   // [3 CB][Py]
-    C2* colI = reinterpret_cast<C2*>(smraw + lay.half);   // [3 CB][2][32]
+    S* halo = reinterpret_cast<S*>(smraw + lay.halo);     // [parity][lo, hi][3][nx]
+    C2* colIn = reinterpret_cast<C2*>(smraw + lay.colin); // [3 CU][ny]
+    C2* colS = reinterpret_cast<C2*>(smraw + lay.spec);   // [3 CU][LYh]
+    C2* rowIn = reinterpret_cast<C2*>(smraw + lay.rowin); // [3 RB][Kx][H]
     C2* w64 = reinterpret_cast<C2*>(smraw + lay.w64);
-    C* ts = reinterpret_cast<C*>(smraw + lay.tens);
+    C* ts = reinterpret_cast<C*>(smraw + lay.tens);       // [4][CU][LYh]
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     const long long N = d.ncells;
     S* gm = p.m + d.off + (long long)r0 * nx;
@@ -206,10 +220,17 @@ __global__ void __launch_bounds__(kSmallThreads, 1) k_small_rk(SmallParams<C> p)
     for (int q = threadIdx.x; q < 64; q += blockDim.x) w64[q] = p.tw[q << (MM_LOG2_LMAX - 6)];
     const bool demag = (d.flags & F_DEMAG) != 0;
     if (demag) {
+        // tensor at the bins of the CTA's units: unit kx H + hf, bin ky = H k' + hf;
+        // stored values at ky' = min(ky, Py - ky), xy odd in ky
         const long long plane = (long long)d.Pzh * d.Pyh * d.Kx;
-        for (int i = threadIdx.x; i < 4 * nk * pyh; i += blockDim.x) {
-            const int c = i / (nk * pyh), rem = i - c * nk * pyh, j = rem / pyh, ky = rem - j * pyh;
-            ts[(c * CB + j) * pyh + ky] = p.tensor[d.tens_off + c * plane + (long long)ky * d.Kx + k0 + j];
+        for (int i = threadIdx.x; i < 4 * nu * LYh; i += blockDim.x) {
+            const int c = i / (nu * LYh), rem = i - c * nu * LYh, j = rem / LYh, kk = rem - j * LYh;
+            const int u = u0 + j, kx = u / H, hf = u - kx * H;
+            const int ky = H * kk + hf;
+            const int kyh = ky > (Py >> 1) ? Py - ky : ky;
+            C v = p.tensor[d.tens_off + c * plane + (long long)kyh * d.Kx + kx];
+            if (c == 3 && ky > (Py >> 1)) v = -v;
+            ts[(c * CU + j) * LYh + kk] = v;
         }
     }
     SimState& G = p.state[sim];
@@ -233,15 +254,12 @@ __global__ void __launch_bounds__(kSmallThreads, 1) k_small_rk(SmallParams<C> p)
     const bool prec = (d.flags & F_PREC) != 0, dmi = (d.flags & F_DMI) != 0;
     const bool do_ex = (d.flags & F_EX) != 0, do_uni = (d.flags & F_UNI) != 0, do_cub = (d.flags & F_CUB) != 0;
     const S e7 = (S)dp_e(6);
-    // lane groups of the x sequences (LX lanes each)
+    // lane groups of the x sequences (LX lanes each) and of the column items (LYh lanes)
     const int GX = 32 >> lX, gx = lane >> lX, jx = lane & (LX - 1);
     const int nseqR = 3 * nr;
-    // column items: H halves of lY-point transforms, GY groups of LY lanes per warp
-    const int H = lPy == 6 ? 2 : 1;
-    const int lY = lPy == 6 ? 5 : lPy, LY = 1 << lY;
-    const int GY = 32 >> lY, gy = lane >> lY, jy = lane & (LY - 1);
-    const int nit = 3 * H * nk, nslot = (nit + GY - 1) / GY;
-    const int kyb = bitrev(jy, lY);             // the bin index (within its half) lane jy holds
+    const int GY = 32 >> lY, gy = lane >> lY, jy = lane & (LYh - 1);
+    const int nit = 3 * nu, nslot = (nit + GY - 1) / GY;
+    const int kyb = bitrev(jy, lY);             // the bin (within its unit) lane jy holds
     bool ran = false;
     int q = 0;                                  // right-hand sides evaluated: stage-state parity
 
@@ -249,7 +267,9 @@ __global__ void __launch_bounds__(kSmallThreads, 1) k_small_rk(SmallParams<C> p)
         ran = true;
         bool stop = false;
         for (int st = 1; st <= 7 && !stop; ++st) {
-            S* ys = ysb + (q & 1) * slice;
+            const int par = q & 1;
+            S* ys = ysb + par * slice;
+            S* hl = halo + par * 2 * 3 * nx;    // this parity's halo rows: [lo, hi][3][nx]
             const S hs = (S)h;
             switch (st) {
                 case 1: small_prologue<S, 1>(yn, kv, ys, ep, cs, ncell, hs); break;
@@ -261,9 +281,25 @@ __global__ void __launch_bounds__(kSmallThreads, 1) k_small_rk(SmallParams<C> p)
                 default: small_prologue<S, 7>(yn, kv, ys, ep, cs, ncell, hs); break;
             }
             __syncthreads();
+            // the block's first and last rows into the neighbouring CTAs' halos (the
+            // row above the lower neighbour's block, the row below the upper one's)
+            if ((do_ex || dmi) && nr > 0) {
+                for (int i = threadIdx.x; i < 2 * 3 * nx; i += blockDim.x) {
+                    const int side = i / (3 * nx), c = (i / nx) % 3, x = i % nx;
+                    const int y = side == 0 ? r0 : r0 + nr - 1;           // row sent
+                    const int yt = side == 0 ? y - 1 : y + 1;             // the receiver's row
+                    if (yt >= 0 && yt < ny) {
+                        const int ow = yt / RB;
+                        // received as the receiver's hi halo (side 0) or lo halo (side 1)
+                        cl.map_shared_rank(hl, ow)[((side == 0 ? 1 : 0) * 3 + c) * nx + x] =
+                            ys[c * cs + (y - r0) * nx + x];
+                    }
+                }
+            }
             // ---- 1. M = Ms y_s, zero-padded R2C along x of the CTA's rows: lane n of a
             // group packs z[n] = M[2n] + i M[2n+1] (zero for 2n >= nx, so the upper half
-            // is zero), FFT of length LX = Px/2, split into X_k, k = 0..LX
+            // is zero), FFT of length LX = Px/2, split into X_k, k = 0..LX, each pushed to
+            // the owners of its column units
             if (demag) {
                 for (int base = warp * GX; base < nseqR; base += nwarp * GX) {     // warp-uniform
                     const int qs = base + gx;
@@ -289,106 +325,110 @@ __global__ void __launch_bounds__(kSmallThreads, 1) k_small_rk(SmallParams<C> p)
                     const C2 Dd = z[0] - Zm;
                     const C2 O = mk<C>(Dd.y * (C)0.5, -Dd.x * (C)0.5);
                     if (valid) {
-                        C2* row = rowX + qs * Kx;
-                        row[k] = E + cmul(w64_get<C, false>(w64, k << (6 - lPx)), O);
-                        if (k == 0) row[LX] = E - O;
+                        const C2 Xk = E + cmul(w64_get<C, false>(w64, k << (6 - lPx)), O);
+                        const C2 XL = E - O;                                // X_LX (from k = 0)
+                        const int y = r0 + r;
+#pragma unroll
+                        for (int hf = 0; hf < 2; ++hf) {
+                            if (hf < H) {
+                                int u = k * H + hf, ou = u / CU;
+                                cl.map_shared_rank(colIn, ou)[(3 * (u - ou * CU) + c) * ny + y] = Xk;
+                                if (k == 0) {
+                                    u = LX * H + hf;
+                                    ou = u / CU;
+                                    cl.map_shared_rank(colIn, ou)[(3 * (u - ou * CU) + c) * ny + y] = XL;
+                                }
+                            }
+                        }
                     }
                 }
             }
-            cl.sync();                          // A: every row spectrum in place
-            // ---- 2. columns: FFT along y of the ny non-zero rows, H^ = -N^ M^ per bin,
-            // inverse along y, the ny rows kept
+            cl.sync();                          // A: rows in the column owners, halos in place
+            // ---- 2. column units: FFT along y of the ny non-zero rows (the odd half
+            // of a 64-point column weighted by W_64^y), H^ = -N^ M^ per bin, inverse,
+            // the ny rows pushed to their owners
             if (demag) {
-                for (int b0 = warp * kNV; b0 < nslot; b0 += nwarp * kNV) {           // warp-uniform
+                for (int b0 = warp * kNV; b0 < nslot; b0 += nwarp * kNV) {         // warp-uniform
                     C2 v[kNV];
                     int it[kNV];
 #pragma unroll
-                    for (int u = 0; u < kNV; ++u) {
-                        it[u] = (b0 + u) * GY + gy;
-                        v[u] = mk<C>((C)0, (C)0);
-                        if (it[u] < nit && jy < ny) {
-                            const int j = it[u] / (3 * H), c = (it[u] / H) % 3, hf = it[u] % H;
-                            const int ow = jy / RB;
-                            v[u] = cl.map_shared_rank(rowX, ow)[(3 * (jy - ow * RB) + c) * Kx + k0 + j];
-                            if (hf) v[u] = cmul(v[u], w64_get<C, false>(w64, jy));
+                    for (int uu = 0; uu < kNV; ++uu) {
+                        it[uu] = (b0 + uu) * GY + gy;
+                        v[uu] = mk<C>((C)0, (C)0);
+                        if (it[uu] < nit && jy < ny) {
+                            const int j = it[uu] / 3, c = it[uu] - 3 * j;
+                            v[uu] = colIn[(3 * j + c) * ny + jy];
+                            if ((u0 + j) % H) v[uu] = cmul(v[uu], w64_get<C, false>(w64, jy));
                         }
                     }
                     warp_dif<C, false, kNV>(v, lY, jy, w64);
 #pragma unroll
-                    for (int u = 0; u < kNV; ++u) {
-                        if (it[u] < nit) {
-                            const int j = it[u] / (3 * H), c = (it[u] / H) % 3, hf = it[u] % H;
-                            colS[(3 * j + c) * Py + H * kyb + hf] = v[u];
-                        }
-                    }
+                    for (int uu = 0; uu < kNV; ++uu)
+                        if (it[uu] < nit) colS[it[uu] * LYh + kyb] = v[uu];
                 }
                 __syncthreads();
-                for (int b = threadIdx.x; b < nk * Py; b += blockDim.x) {
-                    const int j = b / Py, ky = b - j * Py;
-                    C2* s0 = colS + 3 * j * Py + ky;
-                    C2 a = s0[0], bb = s0[Py], cc = s0[2 * Py];
-                    small_tensor<C>(ts, CB, pyh, j, ky, Py, a, bb, cc);
-                    s0[0] = a; s0[Py] = bb; s0[2 * Py] = cc;
+                for (int b = threadIdx.x; b < nu * LYh; b += blockDim.x) {
+                    const int j = b / LYh, kk = b - j * LYh;
+                    C2* s0 = colS + 3 * j * LYh + kk;
+                    const C xx = ts[(0 * CU + j) * LYh + kk], yy = ts[(1 * CU + j) * LYh + kk];
+                    const C zz = ts[(2 * CU + j) * LYh + kk], xy = ts[(3 * CU + j) * LYh + kk];
+                    const C2 mx = s0[0], my = s0[LYh], mz = s0[2 * LYh];
+                    s0[0] = mk<C>(xx * mx.x + xy * my.x, xx * mx.y + xy * my.y);
+                    s0[LYh] = mk<C>(xy * mx.x + yy * my.x, xy * mx.y + yy * my.y);
+                    s0[2 * LYh] = mk<C>(zz * mz.x, zz * mz.y);
                 }
                 __syncthreads();
                 for (int b0 = warp * kNV; b0 < nslot; b0 += nwarp * kNV) {
                     C2 v[kNV];
                     int it[kNV];
 #pragma unroll
-                    for (int u = 0; u < kNV; ++u) {
-                        it[u] = (b0 + u) * GY + gy;
-                        v[u] = mk<C>((C)0, (C)0);
-                        if (it[u] < nit) {
-                            const int j = it[u] / (3 * H), c = (it[u] / H) % 3, hf = it[u] % H;
-                            v[u] = colS[(3 * j + c) * Py + H * kyb + hf];   // bit-reversed order in
-                        }
+                    for (int uu = 0; uu < kNV; ++uu) {
+                        it[uu] = (b0 + uu) * GY + gy;
+                        v[uu] = it[uu] < nit ? colS[it[uu] * LYh + kyb] : mk<C>((C)0, (C)0);   // bit-reversed in
                     }
                     warp_dit<C, true, kNV>(v, lY, jy, w64);                 // natural order out
 #pragma unroll
-                    for (int u = 0; u < kNV; ++u) {
-                        if (it[u] < nit) {
-                            const int j = it[u] / (3 * H), c = (it[u] / H) % 3, hf = it[u] % H;
-                            if (H == 1) {
-                                if (jy < ny) colH[(3 * j + c) * ny + jy] = v[u];
-                            } else {
-                                colI[((3 * j + c) * 2 + hf) * 32 + jy] = v[u];
-                            }
+                    for (int uu = 0; uu < kNV; ++uu) {
+                        if (it[uu] < nit && jy < ny) {
+                            const int j = it[uu] / 3, c = it[uu] - 3 * j;
+                            const int u = u0 + j, kx = u / H, hf = u - kx * H;
+                            const int ow = jy / RB;
+                            cl.map_shared_rank(rowIn, ow)[((3 * (jy - ow * RB) + c) * Kx + kx) * H + hf] = v[uu];
                         }
                     }
                 }
-                if (H == 2) {
-                    // x[n] = F32^-1(X[2k])[n] + W_64^-n F32^-1(X[2k+1])[n], n < ny <= 32
-                    __syncthreads();
-                    for (int b = threadIdx.x; b < 3 * nk * ny; b += blockDim.x) {
-                        const int qc = b / ny, n = b - qc * ny;
-                        colH[qc * ny + n] = colI[(2 * qc) * 32 + n] +
-                                            cmul(colI[(2 * qc + 1) * 32 + n], w64_get<C, true>(w64, n));
-                    }
-                }
             }
-            cl.sync();                          // B: every column transformed back
-            // ---- 3. rows: Hermitian split and inverse C2R along x (lane j of a group
-            // forms Z_k, k = bitrev(j), from the column owners' X_k and X_{LX-k}, so the
-            // decimation-in-time inverse leaves z[n] in lane n: cells 2n and 2n + 1)
+            cl.sync();                          // B: every column result in its row owner
+            // ---- 3. rows: X(kx) = the units' results (the odd half weighted by W_64^-y),
+            // Hermitian split and inverse C2R along x (lane j of a group forms Z_k,
+            // k = bitrev(j), so the decimation-in-time inverse leaves z[n] in lane n:
+            // cells 2n and 2n + 1)
             if (demag) {
                 for (int base = warp * GX; base < nseqR; base += nwarp * GX) {
                     const int qs = base + gx;
                     const bool valid = qs < nseqR;
-                    const int r = valid ? qs / 3 : 0, c = valid ? qs - 3 * r : 0;
+                    const int r = valid ? qs / 3 : 0;
                     C2 z[1] = {mk<C>((C)0, (C)0)};
                     const int k = bitrev(jx, lX);
                     if (valid) {
-                        const int ka = k, kb = LX - k;
-                        const int oa = ka / CB, ob = kb / CB;
-                        const C2 Xa = cl.map_shared_rank(colH, oa)[(3 * (ka - oa * CB) + c) * ny + r0 + r];
-                        const C2 Xb = cconj(cl.map_shared_rank(colH, ob)[(3 * (kb - ob * CB) + c) * ny + r0 + r]);
+                        const C2* ri = rowIn + qs * Kx * H;
+                        C2 Xa, Xb;
+                        if (H == 2) {
+                            const C2 wy = w64_get<C, true>(w64, r0 + r);
+                            Xa = ri[2 * k] + cmul(ri[2 * k + 1], wy);
+                            Xb = ri[2 * (LX - k)] + cmul(ri[2 * (LX - k) + 1], wy);
+                        } else {
+                            Xa = ri[k];
+                            Xb = ri[LX - k];
+                        }
+                        Xb = cconj(Xb);
                         const C2 e = Xa + Xb;
                         const C2 tq = cmul(w64_get<C, true>(w64, k << (6 - lPx)), Xa - Xb);
                         z[0] = mk<C>(e.x - tq.y, e.y + tq.x);
                     }
                     warp_dit<C, true, 1>(z, lX, jx, w64);
                     if (valid) {
-                        const int x = 2 * jx;
+                        const int c = qs - 3 * r, x = 2 * jx;
                         if (x < nx) hd[c * cs + r * nx + x] = to_store<C>(z[0].x);
                         if (x + 1 < nx) hd[c * cs + r * nx + x + 1] = to_store<C>(z[0].y);
                     }
@@ -408,28 +448,31 @@ __global__ void __launch_bounds__(kSmallThreads, 1) k_small_rk(SmallParams<C> p)
                     if (demag) { hd0 = hd[i]; hd1 = hd[cs + i]; hd2 = hd[2 * cs + i]; }
                     S ex0 = 0, ex1 = 0, ex2 = 0, dm0 = 0, dm1 = 0, dm2 = 0;
                     if (do_ex || dmi) {
-                        // neighbours -x, +x, -y, +y (one plane: no z neighbours); a missing
-                        // one reads the cell itself and is masked
+                        // neighbours -x, +x, -y, +y (one plane: no z neighbours) from the
+                        // CTA's rows or its halo rows; a missing one reads the cell itself and
+                        // is masked.  Component stride: cs in the block, nx in a halo.
                         bool ok[4] = {x > 0, x < nx - 1, y > 0, y < ny - 1};
                         const S* rowm = ys + r * nx;
                         const S* rowl = rowm;
                         const S* rowh = rowm;
+                        int csl = cs, csh = cs;
                         if (ok[2]) {
-                            const int ow = (y - 1) / RB;
-                            rowl = (ow == rank ? ys : cl.map_shared_rank(ys, ow)) + (y - 1 - ow * RB) * nx;
+                            if (r > 0) rowl = rowm - nx;
+                            else { rowl = hl; csl = nx; }
                         }
                         if (ok[3]) {
-                            const int ow = (y + 1) / RB;
-                            rowh = (ow == rank ? ys : cl.map_shared_rank(ys, ow)) + (y + 1 - ow * RB) * nx;
+                            if (r < nr - 1) rowh = rowm + nx;
+                            else { rowh = hl + 3 * nx; csh = nx; }
                         }
                         const int xo[4] = {ok[0] ? x - 1 : x, ok[1] ? x + 1 : x, x, x};
                         const S* rp[4] = {rowm, rowm, rowl, rowh};
+                        const int cst[4] = {cs, cs, csl, csh};
                         S j0[4], j1[4], j2[4];
 #pragma unroll
                         for (int nb = 0; nb < 4; ++nb) {
                             j0[nb] = rp[nb][xo[nb]];
-                            j1[nb] = rp[nb][cs + xo[nb]];
-                            j2[nb] = rp[nb][2 * cs + xo[nb]];
+                            j1[nb] = rp[nb][cst[nb] + xo[nb]];
+                            j2[nb] = rp[nb][2 * cst[nb] + xo[nb]];
                         }
                         if (msarr) {
                             const long long cc = (long long)y * nx + x;
@@ -490,43 +533,57 @@ __global__ void __launch_bounds__(kSmallThreads, 1) k_small_rk(SmallParams<C> p)
                 const unsigned long long rr = block_max_u64(vmax, red_u);
                 if (threadIdx.x == 0) {
                     const double v = obits_to_double<S>(rr);
-                    slot[si] = (unsigned long long)__double_as_longlong(si ? fabs(h * v) : v);
+                    const unsigned long long vb = (unsigned long long)__double_as_longlong(si ? fabs(h * v) : v);
+                    for (int b = 0; b < nc; ++b) cl.map_shared_rank(&slots[si][0], b)[rank] = vb;
                 }
-                cl.sync();                      // every CTA's maximum published
-                unsigned long long g = 0ull;
-                for (int b = 0; b < nc; ++b) g = umax64(g, *cl.map_shared_rank(&slot[si], b));
-                if (st == 1) {
-                    // k_after_stage1: max|dm/dt|, relaxation stop, initial step
-                    const double mkv = sqrt(bits_to_double(g));
-                    maxk = mkv;
-                    err_bits = 0ull;
-                    if (!(mkv == mkv) || isinf(mkv)) status = -4;
-                    else if (max_dmdt > 0.0 && mkv < max_dmdt) status = 2;
-                    else if (h <= 0.0) {
-                        double h0 = mkv > 0.0 ? fmin(1e-12, 0.01 / mkv) : 1e-12;
-                        if (t_end > 0.0) h0 = fmin(h0, t_end - t);
-                        h = h0;
-                    }
-                    if (status != 0) { stop = true; accepted = 0; }
-                } else {
-                    // k_controller: accept when err <= 1, h <- h clamp(0.9 err^-1/5, 0.2, 5)
-                    err_bits = g;
-                    err = bits_to_double(g) / rtol;
-                    if (!(err == err) || isinf(err)) {
-                        status = -4;
-                        accepted = 0;
-                    } else {
-                        const int acc = err <= 1.0;
-                        if (acc) { t += h; n_acc += 1; } else { n_rej += 1; }
-                        accepted = acc;
-                        const double f = err == 0.0 ? 5.0 : fmin(5.0, fmax(0.2, 0.9 * pow(err, -0.2)));
-                        h *= f;
-                        if (t_end > 0.0) {
-                            h = fmin(h, t_end - t);
-                            if (t_end - t <= 1e-12 * t_end) status = 1;
+                cl.sync();                      // every CTA's maximum in every CTA
+                // one thread takes the step decision (its FP64 arithmetic, pow included, would
+                // otherwise run in every warp on the FP64 pipe) and broadcasts it
+                if (threadIdx.x == 0) {
+                    unsigned long long g = 0ull;
+                    for (int b = 0; b < nc; ++b) g = umax64(g, slots[si][b]);
+                    if (st == 1) {
+                        // k_after_stage1: max|dm/dt|, relaxation stop, initial step
+                        const double mkv = sqrt(bits_to_double(g));
+                        maxk = mkv;
+                        err_bits = 0ull;
+                        if (!(mkv == mkv) || isinf(mkv)) status = -4;
+                        else if (max_dmdt > 0.0 && mkv < max_dmdt) status = 2;
+                        else if (h <= 0.0) {
+                            double h0 = mkv > 0.0 ? fmin(1e-12, 0.01 / mkv) : 1e-12;
+                            if (t_end > 0.0) h0 = fmin(h0, t_end - t);
+                            h = h0;
                         }
-                        if (status == 0 && !(h > 1e-24)) status = -5;
+                        if (status != 0) accepted = 0;
+                    } else {
+                        // k_controller: accept when err <= 1, h <- h clamp(0.9 err^-1/5, 0.2, 5)
+                        err_bits = g;
+                        err = bits_to_double(g) / rtol;
+                        if (!(err == err) || isinf(err)) {
+                            status = -4;
+                            accepted = 0;
+                        } else {
+                            const int acc = err <= 1.0;
+                            if (acc) { t += h; n_acc += 1; } else { n_rej += 1; }
+                            accepted = acc;
+                            const double f = step_factor(err);
+                            h *= f;
+                            if (t_end > 0.0) {
+                                h = fmin(h, t_end - t);
+                                if (t_end - t <= 1e-12 * t_end) status = 1;
+                            }
+                            if (status == 0 && !(h > 1e-24)) status = -5;
+                        }
                     }
+                    dec.t = t; dec.h = h; dec.err = err; dec.maxk = maxk; dec.err_bits = err_bits;
+                    dec.n_acc = n_acc; dec.n_rej = n_rej; dec.status = status; dec.accepted = accepted;
+                }
+                __syncthreads();
+                t = dec.t; h = dec.h; err = dec.err; maxk = dec.maxk; err_bits = dec.err_bits;
+                n_acc = dec.n_acc; n_rej = dec.n_rej; status = dec.status; accepted = dec.accepted;
+                if (st == 1) {
+                    if (status != 0) stop = true;
+                } else {
                     if (accepted) {
                         // projection m = y5 / |y5| (y5 is the stage-7 state)
                         for (int i = threadIdx.x; i < ncell; i += blockDim.x) {
@@ -540,8 +597,8 @@ __global__ void __launch_bounds__(kSmallThreads, 1) k_small_rk(SmallParams<C> p)
             }
         }
     }
-    // no CTA leaves while a peer may still read its shared memory (the maxima read after
-    // the last reduction barrier)
+    // no CTA leaves before every peer is past its last access to the cluster's shared
+    // memory
     cl.sync();
     if (ran) {
         for (int i = threadIdx.x; i < ncell; i += blockDim.x) {

@@ -20,39 +20,46 @@ inline bool small_eligible(const SimDesc& d) {
            d.group_begin < 0;
 }
 
-// Rows and kx columns of one CTA for a cluster of nc CTAs: CTA b owns rows
-// [b rb, min(ny, (b + 1) rb)) and kx columns [b cb, min(Kx, (b + 1) cb)).
+// Rows and column units of one CTA for a cluster of nc CTAs.  A column unit is
+// one kx column (Py <= 32) or one half of it (Py = 64: the even and the odd ky
+// bins, each a 32-point transform): unit u = kx H + hf, H = 1 or 2.  CTA b owns
+// rows [b rb, min(ny, (b + 1) rb)) and units [b cu, min(Kx H, (b + 1) cu)).
+__host__ __device__ inline int small_halves(const SimDesc& d) { return d.Py == 64 ? 2 : 1; }
 __host__ __device__ inline int small_rows_per_cta(const SimDesc& d, int nc) { return (d.ny + nc - 1) / nc; }
-__host__ __device__ inline int small_cols_per_cta(const SimDesc& d, int nc) { return (d.Kx + nc - 1) / nc; }
+__host__ __device__ inline int small_units_per_cta(const SimDesc& d, int nc) {
+    return (d.Kx * small_halves(d) + nc - 1) / nc;
+}
 
-// Shared-memory layout of one CTA of a cluster of nc CTAs (element sizes of the
-// storage and of the compute type), identical in every CTA of the cluster: 14
-// state slices [3][rb nx] of the storage type (y_n, k_1..k_7, two stage states,
-// the stage-7 error sum, the demagnetising field), then (complex) the
-// x-transformed rows [3 rb][Kx], the y-inverse-transformed columns [3 cb][ny],
-// the y spectra of the CTA's columns [3 cb][Py], the two half-length inverses
-// of 64-point columns [3 cb][2][32], the table W_64^q, and (real) the tensor of
-// the CTA's kx columns [4][cb][Py/2 + 1].
+// Shared-memory layout of one CTA (element sizes of the storage and of the
+// compute type), identical in every CTA of the cluster: 14 state slices
+// [3][rb nx] of the storage type (y_n, k_1..k_7, two stage states, the stage-7
+// error sum, the demagnetising field) and the halo rows [2][2][3][nx] (the rows
+// below and above the CTA's block, by stage-state parity), then (complex) the
+// rows pushed to the CTA's column units [3 cu][ny], the units' spectra
+// [3 cu][Py / H], the column results pushed to the CTA's rows [3 rb][Kx][H],
+// the table W_64^q, and (real) the tensor at the units' bins [4][cu][Py / H].
 struct SmallLayout {
-    size_t rows, cols, spec, half, w64, tens, total;    // byte offsets and the total
+    size_t halo, colin, spec, rowin, w64, tens, total;    // byte offsets and the total
 };
 __host__ __device__ inline SmallLayout small_layout(const SimDesc& d, int nc, size_t ssz, size_t csz) {
-    const int rb = small_rows_per_cta(d, nc), cb = small_cols_per_cta(d, nc);
+    const int rb = small_rows_per_cta(d, nc), cu = small_units_per_cta(d, nc), H = small_halves(d);
+    const int lyh = d.Py / H;
     const size_t z = 2 * csz;
     SmallLayout L;
-    size_t b = ((14 * 3 * (size_t)rb * d.nx * ssz) + 15) & ~(size_t)15;
-    L.rows = b;
-    b += 3 * (size_t)rb * d.Kx * z;
-    L.cols = b;
-    b += 3 * (size_t)cb * d.ny * z;
+    size_t b = 14 * 3 * (size_t)rb * d.nx * ssz;
+    L.halo = b;
+    b += 2 * 2 * 3 * (size_t)d.nx * ssz;
+    b = (b + 15) & ~(size_t)15;
+    L.colin = b;
+    b += 3 * (size_t)cu * d.ny * z;
     L.spec = b;
-    b += 3 * (size_t)cb * d.Py * z;
-    L.half = b;
-    b += (d.Py == 64 ? 3 * (size_t)cb * 64 : 0) * z;
+    b += 3 * (size_t)cu * lyh * z;
+    L.rowin = b;
+    b += 3 * (size_t)rb * d.Kx * H * z;
     L.w64 = b;
     b += 64 * z;
     L.tens = b;
-    b += 4 * (size_t)cb * (d.Py / 2 + 1) * csz;
+    b += 4 * (size_t)cu * lyh * csz;
     L.total = (b + 15) & ~(size_t)15;
     return L;
 }
