@@ -886,6 +886,7 @@ int mm_set_field(mm_ctx* C, int sim, const double H[3]) {
         s.d.H[i] = H[i];
     }
     replan(s);
+    C->small_nc = -1;           // term flags may change: resolve the attempt path again
     if (C->finalized) {
         CK(cudaMemcpyAsync(&C->desc_d[sim], &s.d, sizeof(SimDesc), cudaMemcpyHostToDevice, C->stream));
         CK(cudaStreamSynchronize(C->stream));
@@ -934,6 +935,7 @@ int mm_set_spin_torque(mm_ctx* C, int sim, const double u[3], double beta, doubl
     s.d.aJ = a_J;
     s.d.bJ = b_J;
     replan(s);
+    C->small_nc = -1;           // the torques decide whether the single-launch attempts apply
     if (C->finalized) {
         if (batch_ext(C) != before) drop_graphs(C);
         CK(cudaMemcpyAsync(&C->desc_d[sim], &s.d, sizeof(SimDesc), cudaMemcpyHostToDevice, C->stream));

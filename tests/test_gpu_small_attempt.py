@@ -176,3 +176,17 @@ def test_single_launch_t_end_clip_and_step():
             assert max_rel(ctx.get_m(0), mref) < 1e-10
         else:
             ref, mref = g, ctx.get_m(0)
+
+
+def test_spin_torques_set_later_leave_the_single_launch():
+    """Spin torques switched on after the single launch ran move the context to the pass
+    kernels (the single launch has no torque terms); switched off, it returns."""
+    sim = _sim(1, *CASES[1])
+    ctx = _ctx("f64", [sim])
+    ctx.rk45_setup(1e-6)
+    ctx.rk45_attempts(1)
+    assert ctx.attempt_kernel()[0]
+    ctx.set_spin_torque(0, (50.0, 0.0, 0.0), 0.1, 0.0, 0.0, (0.0, 0.0, 1.0))
+    assert ctx.attempt_kernel() == (False, 0)
+    ctx.set_spin_torque(0, (0.0, 0.0, 0.0), 0.0, 0.0, 0.0, (0.0, 0.0, 1.0))
+    assert ctx.attempt_kernel()[0]
