@@ -120,16 +120,20 @@ __device__ __forceinline__ V2<C> w64_get(const V2<C>* w64, int q) {
 // Decimation in frequency: natural order in, bit-reversed order out, NV
 // independent sequences per lane advanced stage by stage (their shuffles and
 // products overlap).
+// Each lane forms its own output with one complex addition and one product: the
+// lower lane of a pair v + u (times 1), the upper (u - v) w, so no lane computes
+// both results (the product by 1 is exact in every compute type).
 template <typename C, bool INV, int NV>
 __device__ __forceinline__ void warp_dif(V2<C> (&v)[NV], int l, int j, const V2<C>* w64) {
     for (int t = l - 1; t >= 0; --t) {
         const int s = 1 << t;
         const bool up = (j & s) != 0;
-        const V2<C> w = w64_get<C, INV>(w64, (j & (s - 1)) << (5 - t));
+        const V2<C> w = up ? w64_get<C, INV>(w64, (j & (s - 1)) << (5 - t)) : mk<C>((C)1, (C)0);
 #pragma unroll
         for (int i = 0; i < NV; ++i) {
             const V2<C> u = mk<C>(shfl_xor_v(v[i].x, s), shfl_xor_v(v[i].y, s));
-            v[i] = up ? cmul(u - v[i], w) : v[i] + u;
+            const V2<C> sv = up ? mk<C>(-v[i].x, -v[i].y) : v[i];
+            v[i] = cmul(u + sv, w);
         }
     }
 }
@@ -146,7 +150,7 @@ __device__ __forceinline__ void warp_dit(V2<C> (&v)[NV], int l, int j, const V2<
             const V2<C> u = mk<C>(shfl_xor_v(v[i].x, s), shfl_xor_v(v[i].y, s));
             const V2<C> b = cmul(up ? v[i] : u, w);
             const V2<C> a = up ? u : v[i];
-            v[i] = up ? a - b : a + b;
+            v[i] = a + (up ? mk<C>(-b.x, -b.y) : b);
         }
     }
 }
@@ -259,7 +263,9 @@ __global__ void __launch_bounds__(kSmallThreads, 1) k_small_rk(SmallParams<C> p)
     const int nseqR = 3 * nr;
     const int GY = 32 >> lY, gy = lane >> lY, jy = lane & (LYh - 1);
     const int nit = 3 * nu, nslot = (nit + GY - 1) / GY;
+    const int LYp = small_spec_row(LYh);        // padded row of a unit's spectrum (bank spread)
     const int kyb = bitrev(jy, lY);             // the bin (within its unit) lane jy holds
+    const int kyp = kyb + (kyb >> 3);           // ... at its padded position
     bool ran = false;
     int q = 0;                                  // right-hand sides evaluated: stage-state parity
 
@@ -364,18 +370,18 @@ __global__ void __launch_bounds__(kSmallThreads, 1) k_small_rk(SmallParams<C> p)
                     warp_dif<C, false, kNV>(v, lY, jy, w64);
 #pragma unroll
                     for (int uu = 0; uu < kNV; ++uu)
-                        if (it[uu] < nit) colS[it[uu] * LYh + kyb] = v[uu];
+                        if (it[uu] < nit) colS[it[uu] * LYp + kyp] = v[uu];
                 }
                 __syncthreads();
                 for (int b = threadIdx.x; b < nu * LYh; b += blockDim.x) {
                     const int j = b / LYh, kk = b - j * LYh;
-                    C2* s0 = colS + 3 * j * LYh + kk;
+                    C2* s0 = colS + 3 * j * LYp + kk + (kk >> 3);
                     const C xx = ts[(0 * CU + j) * LYh + kk], yy = ts[(1 * CU + j) * LYh + kk];
                     const C zz = ts[(2 * CU + j) * LYh + kk], xy = ts[(3 * CU + j) * LYh + kk];
-                    const C2 mx = s0[0], my = s0[LYh], mz = s0[2 * LYh];
+                    const C2 mx = s0[0], my = s0[LYp], mz = s0[2 * LYp];
                     s0[0] = mk<C>(xx * mx.x + xy * my.x, xx * mx.y + xy * my.y);
-                    s0[LYh] = mk<C>(xy * mx.x + yy * my.x, xy * mx.y + yy * my.y);
-                    s0[2 * LYh] = mk<C>(zz * mz.x, zz * mz.y);
+                    s0[LYp] = mk<C>(xy * mx.x + yy * my.x, xy * mx.y + yy * my.y);
+                    s0[2 * LYp] = mk<C>(zz * mz.x, zz * mz.y);
                 }
                 __syncthreads();
                 for (int b0 = warp * kNV; b0 < nslot; b0 += nwarp * kNV) {
@@ -384,7 +390,7 @@ __global__ void __launch_bounds__(kSmallThreads, 1) k_small_rk(SmallParams<C> p)
 #pragma unroll
                     for (int uu = 0; uu < kNV; ++uu) {
                         it[uu] = (b0 + uu) * GY + gy;
-                        v[uu] = it[uu] < nit ? colS[it[uu] * LYh + kyb] : mk<C>((C)0, (C)0);   // bit-reversed in
+                        v[uu] = it[uu] < nit ? colS[it[uu] * LYp + kyp] : mk<C>((C)0, (C)0);   // bit-reversed in
                     }
                     warp_dit<C, true, kNV>(v, lY, jy, w64);                 // natural order out
 #pragma unroll
@@ -509,9 +515,15 @@ __global__ void __launch_bounds__(kSmallThreads, 1) k_small_rk(SmallParams<C> p)
                         const S f = -cC * inv;
                         cu0 = f * m0 * m0 * m0; cu1 = f * m1 * m1 * m1; cu2 = f * m2 * m2 * m2;
                     }
-                    const S H0 = hd0 + ex0 + dm0 + un0 + cu0 + Hx0;
-                    const S H1 = hd1 + ex1 + dm1 + un1 + cu1 + Hy0;
-                    const S H2 = hd2 + ex2 + dm2 + un2 + cu2 + Hz0;
+                    // the field in the order hd + ex + dm + un + cu + H_ext, terms that are
+                    // switched off left out (adding their zeros changes no bit; FP64
+                    // additions are what the FP64 epilogue spends its pipe on)
+                    S H0 = hd0, H1 = hd1, H2 = hd2;
+                    if (do_ex) { H0 += ex0; H1 += ex1; H2 += ex2; }
+                    if (dmi) { H0 += dm0; H1 += dm1; H2 += dm2; }
+                    if (do_uni) { H0 += un0; H1 += un1; H2 += un2; }
+                    if (do_cub) { H0 += cu0; H1 += cu1; H2 += cu2; }
+                    H0 += Hx0; H1 += Hy0; H2 += Hz0;
                     // LL form: dm/dt = -g~ m x H - alpha g~ m x (m x H)
                     const S c0 = m1 * H2 - m2 * H1, c1 = m2 * H0 - m0 * H2, c2 = m0 * H1 - m1 * H0;
                     const S dd0 = m1 * c2 - m2 * c1, dd1 = m2 * c0 - m0 * c2, dd2 = m0 * c1 - m1 * c0;

@@ -30,13 +30,17 @@ __host__ __device__ inline int small_units_per_cta(const SimDesc& d, int nc) {
     return (d.Kx * small_halves(d) + nc - 1) / nc;
 }
 
+// Row of a column unit's spectrum in shared memory: bin k at k + k/8, so the
+// bit-reversed stores of a warp spread over the banks.
+__host__ __device__ inline int small_spec_row(int lyh) { return lyh + lyh / 8 + 1; }
+
 // Shared-memory layout of one CTA (element sizes of the storage and of the
 // compute type), identical in every CTA of the cluster: 14 state slices
 // [3][rb nx] of the storage type (y_n, k_1..k_7, two stage states, the stage-7
 // error sum, the demagnetising field) and the halo rows [2][2][3][nx] (the rows
 // below and above the CTA's block, by stage-state parity), then (complex) the
 // rows pushed to the CTA's column units [3 cu][ny], the units' spectra
-// [3 cu][Py / H], the column results pushed to the CTA's rows [3 rb][Kx][H],
+// [3 cu][small_spec_row(Py / H)], the column results pushed to the CTA's rows [3 rb][Kx][H],
 // the table W_64^q, and (real) the tensor at the units' bins [4][cu][Py / H].
 struct SmallLayout {
     size_t halo, colin, spec, rowin, w64, tens, total;    // byte offsets and the total
@@ -53,7 +57,7 @@ __host__ __device__ inline SmallLayout small_layout(const SimDesc& d, int nc, si
     L.colin = b;
     b += 3 * (size_t)cu * d.ny * z;
     L.spec = b;
-    b += 3 * (size_t)cu * lyh * z;
+    b += 3 * (size_t)cu * small_spec_row(lyh) * z;
     L.rowin = b;
     b += 3 * (size_t)rb * d.Kx * H * z;
     L.w64 = b;

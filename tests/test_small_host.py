@@ -64,7 +64,8 @@ def test_layout_fits_one_cta_and_keeps_the_buffers_apart(rows):
                 assert halo == 14 * 3 * rb * nx * e
                 assert colin >= halo + 12 * nx * e and colin % 16 == 0
                 assert spec == colin + 3 * cu * ny * z
-                assert rowin == spec + 3 * cu * (r["Py"] // H) * z
+                lyh = r["Py"] // H
+                assert rowin == spec + 3 * cu * (lyh + lyh // 8 + 1) * z    # padded rows
                 assert w64 == rowin + 3 * rb * r["Kx"] * H * z
                 assert tens == w64 + 64 * z
                 assert total >= tens + 4 * cu * (r["Py"] // H) * e and total % 16 == 0
