@@ -548,10 +548,12 @@ def run_gpu(args, rank, world, dist):
         # one launch runs every timed attempt (k_small_rk, one cluster per simulation):
         # its algorithmic bytes are the whole-step figure, kept in shared memory
         dom = "attempt_single_launch"
-        rows[dom] = {"ms_per_attempt": step_ms, "launches": 1, "attempts_per_launch": args.steps,
+        per = min(args.steps, 1024)                 # the library issues at most 1024 attempts a launch
+        nl = -(-args.steps // per)
+        rows[dom] = {"ms_per_attempt": step_ms, "launches": nl, "attempts_per_launch": per,
                      "cluster_ctas_per_simulation": ncl}
-        avg_launch_ms = ms_max
-        alg_per_launch = step_bytes * args.steps
+        avg_launch_ms = ms_max / nl
+        alg_per_launch = step_bytes * args.steps / nl
         spectrum_per_launch = 0.0
     else:
         dom = max((k for k in rows if kb.get(k)), key=lambda k: rows[k]["ms_per_attempt"])

@@ -176,7 +176,8 @@ int mm_autotune(mm_ctx *ctx, int sim_id, int reps, mm_tuning *best, double *best
  * counterpart).  MM_ATTEMPT_AUTO (the default): when every simulation of the
  * context has one plane and padded FFT lengths Px, Py <= 64 (at most 32 x 32
  * cells), no extended terms (bulk / D_2d DMI, per-cell A or D, spin torques)
- * and no NEB chain, the attempts run in ONE launch per call: one thread-block
+ * and no NEB chain, the attempts run in ONE launch per call (per 1024 attempts
+ * of a call): one thread-block
  * cluster per simulation keeps y_n, the stage vectors and both transform
  * stages in shared memory and runs all n attempts of the call, with the same
  * stage, error-norm, controller and projection arithmetic as the pass kernels

@@ -465,8 +465,9 @@ int launch_attempts(mm_ctx* C, long long n) {
         S.kind = C->precision == MM_F32 ? 0 : (C->dd ? 2 : 1);
         S.cluster = C->small_nc;
         S.smem = C->small_smem;
+        // at most 1024 attempts a launch, so no single kernel runs for long
         for (long long done = 0; done < n;) {
-            const long long chunk = std::min<long long>(n - done, 1 << 30);
+            const long long chunk = std::min<long long>(n - done, 1024);
             S.n_attempts = (int)chunk;
             CK(small_attempts(S));
             C->launches += 1;

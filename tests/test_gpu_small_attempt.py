@@ -69,6 +69,9 @@ def test_single_launch_is_selected_only_where_it_applies():
     ctx.rk45_setup(1e-6)
     ctx.rk45_attempts(5)
     assert ctx.launches() - before == 1          # five attempts, one launch
+    before = ctx.launches()
+    ctx.rk45_attempts(2500)
+    assert ctx.launches() - before == 3          # at most 1024 attempts a launch
     assert _ctx("f64", [s32], passes=True).attempt_kernel() == (False, 0)
     for shape in ((33, 8, 1), (8, 33, 1), (8, 8, 2)):
         s = synth.Sim(synth.Mesh(*shape, 2e-9, 2e-9, 2e-9), synth.Material(Ms=8e5, A=1e-11),
