@@ -193,3 +193,41 @@ def test_spin_torques_set_later_leave_the_single_launch():
     assert ctx.attempt_kernel() == (False, 0)
     ctx.set_spin_torque(0, (0.0, 0.0, 0.0), 0.0, 0.0, 0.0, (0.0, 0.0, 1.0))
     assert ctx.attempt_kernel()[0]
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_single_launch_random_films_equal_the_pass_kernels(seed):
+    """Seeded random films of 1..32 x 1..32 cells, random cell sizes, materials and term
+    sets (DMI, anisotropies, field, precession, masked cells): five FP64 attempts on the
+    single launch and on the pass kernels take the same steps and states (1e-10)."""
+    rng = np.random.default_rng(1000 + seed)
+    nx, ny = (int(v) for v in rng.integers(1, 33, size=2))
+    mesh = synth.Mesh(nx, ny, 1, *(float(v) for v in rng.uniform(1e-9, 4e-9, size=3)))
+    kw = dict(Ms=float(rng.uniform(4e5, 1.2e6)), A=float(rng.uniform(0.5e-11, 2e-11)) * (rng.random() < 0.9),
+              alpha=float(rng.uniform(0.05, 0.6)), precession=int(rng.random() < 0.8),
+              demag=int(rng.random() < 0.9))
+    if rng.random() < 0.5:
+        kw.update(D=float(rng.uniform(-4e-3, 4e-3)), dmi=1)
+    if rng.random() < 0.5:
+        u = rng.normal(size=3)
+        kw.update(Ku=float(rng.uniform(-5e5, 1e6)), u=tuple(u / np.linalg.norm(u)))
+    if rng.random() < 0.3:
+        kw.update(Kc=float(rng.uniform(-5e4, 5e4)))
+    if rng.random() < 0.6:
+        kw.update(H=tuple(float(v) for v in rng.uniform(-1e5, 1e5, size=3)))
+    mat = synth.Material(**kw)
+    Ms_cells = None
+    if rng.random() < 0.3:
+        Ms_cells = np.where(rng.random((1, ny, nx)) < 0.8, mat.Ms, 0.0)
+    sim = synth.Sim(mesh, mat, synth.random_state(2000 + seed, mesh), Ms_cells)
+    out = []
+    for passes in (False, True):
+        ctx = _ctx("f64", [sim], passes=passes)
+        assert ctx.attempt_kernel()[0] == (not passes)
+        ctx.rk45_setup(1e-6)
+        ctx.rk45_attempts(5)
+        out.append((ctx.get_m(0), ctx.status(0)))
+    (ma, sa), (mb, sb) = out
+    assert sa["n_accepted"] == sb["n_accepted"] and sa["n_rejected"] == sb["n_rejected"], (nx, ny)
+    assert abs(sa["t"] - sb["t"]) <= 1e-9 * max(sb["t"], 1e-30)
+    assert max_rel(ma, mb) < 1e-10, (nx, ny)
