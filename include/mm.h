@@ -235,7 +235,11 @@ int mm_precompute_demag(mm_ctx *ctx);
  * [c][k+nz-1][j+ny-1][i+nx-1], c in (xx, yy, zz, xy, xz, yz). */
 int mm_newell_tensor(mm_ctx *ctx, int sim_id, double *out_host);
 
-/* Integration state m (sim_id = -1: the whole batch in batch layout). */
+/* Integration state m (sim_id = -1: the whole batch in batch layout).  Host
+ * buffers are double in every context; in an FP32 context a page-locked host
+ * buffer (cudaMallocHost or registered) moves its FP64 values by DMA and is
+ * converted on the device, any other host buffer is converted on the host
+ * through a pinned staging buffer (the same rounding either way). */
 int mm_set_m(mm_ctx *ctx, int sim_id, const void *m, int where);
 int mm_get_m(mm_ctx *ctx, int sim_id, void *m, int where);
 

@@ -97,6 +97,9 @@ struct mm_ctx {
     // pinned host staging buffer for the host-side state transfers of FP32 contexts
     void* host_stage = nullptr;
     size_t host_stage_bytes = 0;
+    // device FP64 staging of FP32 contexts' transfers from and to pinned host buffers
+    void* dev_stage = nullptr;
+    size_t dev_stage_bytes = 0;
     long long graph_kernels = 0;
     long long launches = 0;
     bool neb = false;
@@ -367,6 +370,39 @@ void convert_host(const A* src, B* dst, long long n) {
     for (auto& x : th) x.join();
 }
 
+// FP64 <-> FP32 conversion of a state on the device (transfers of FP32 contexts
+// from and to pinned host buffers: the FP64 values cross the link by DMA and the
+// rounding to FP32 is the same (T)x as on the host)
+template <typename A, typename B>
+__global__ void k_convert(const A* __restrict__ src, B* __restrict__ dst, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        dst[i] = (B)src[i];
+}
+
+// Whether a host pointer is page-locked (cudaMallocHost or registered): then the
+// FP64 values go by DMA and are converted on the device.
+bool host_pinned(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost;
+}
+
+int ensure_dev_stage(mm_ctx* C, size_t bytes) {
+    if (C->dev_stage_bytes >= bytes) return MM_OK;
+    if (C->dev_stage) cudaFree(C->dev_stage);
+    C->dev_stage = nullptr;
+    C->dev_stage_bytes = 0;
+    int rc = dalloc(C, &C->dev_stage, bytes);
+    if (rc) return rc;
+    C->dev_stage_bytes = bytes;
+    return MM_OK;
+}
+
+static unsigned convert_blocks(long long n) { return (unsigned)std::min<long long>((n + 255) / 256, 4096); }
+
 // The pinned staging buffer, grown to at least `bytes` (reused by every host transfer).
 int ensure_host_stage(mm_ctx* C, size_t bytes) {
     if (C->host_stage_bytes >= bytes) return MM_OK;
@@ -618,6 +654,7 @@ int mm_destroy(mm_ctx* C) {
         for (void* p : pb) if (p) cudaFree(p);
     }
     if (C->host_stage) cudaFreeHost(C->host_stage);
+    if (C->dev_stage) cudaFree(C->dev_stage);
     for (int j = 0; j < 7; ++j) if (C->k[j]) cudaFree(C->k[j]);
     for (int li = 0; li < kYzcListCount; ++li) if (C->yzci[li]) cudaFree(C->yzci[li]);
     if (C->own_stream) cudaStreamDestroy(C->stream);
@@ -1134,6 +1171,12 @@ int mm_set_m(mm_ctx* C, int sim, const void* m, int where) {
     char* dst = (char*)C->m + off * C->esz;
     if (where == MM_DEVICE) {
         CK(cudaMemcpyAsync(dst, m, n * C->esz, cudaMemcpyDeviceToDevice, C->stream));
+    } else if (C->precision == MM_F32 && host_pinned(m)) {
+        if ((rc = ensure_dev_stage(C, (size_t)n * 8))) return rc;
+        CK(cudaMemcpyAsync(C->dev_stage, m, n * 8, cudaMemcpyHostToDevice, C->stream));
+        k_convert<double, float><<<convert_blocks(n), 256, 0, C->stream>>>((const double*)C->dev_stage, (float*)dst, n);
+        C->launches += 1;
+        CK(cudaGetLastError());
     } else if (C->precision == MM_F32) {
         if ((rc = ensure_host_stage(C, (size_t)n * 4))) return rc;
         float* f = (float*)C->host_stage;
@@ -1155,6 +1198,12 @@ int mm_get_m(mm_ctx* C, int sim, void* m, int where) {
     const char* src = (const char*)C->m + off * C->esz;
     if (where == MM_DEVICE) {
         CK(cudaMemcpyAsync(m, src, n * C->esz, cudaMemcpyDeviceToDevice, C->stream));
+    } else if (C->precision == MM_F32 && host_pinned(m)) {
+        if ((rc = ensure_dev_stage(C, (size_t)n * 8))) return rc;
+        k_convert<float, double><<<convert_blocks(n), 256, 0, C->stream>>>((const float*)src, (double*)C->dev_stage, n);
+        C->launches += 1;
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(m, C->dev_stage, n * 8, cudaMemcpyDeviceToHost, C->stream));
     } else if (C->precision == MM_F32) {
         if ((rc = ensure_host_stage(C, (size_t)n * 4))) return rc;
         float* f = (float*)C->host_stage;

@@ -254,8 +254,12 @@ class Context:
             assert a.size == self._count(sim)
             self._check(self.L.mm_set_m(self.h, sim, a.ctypes.data_as(_P), MM_HOST))
 
-    def get_m(self, sim=-1):
-        out = np.empty(self._count(sim))
+    def get_m(self, sim=-1, out=None):
+        """The state as host doubles: into `out` (a contiguous float64 array of the right
+        size, for example a page-locked one) or a new array."""
+        if out is None:
+            out = np.empty(self._count(sim))
+        assert out.dtype == np.float64 and out.flags["C_CONTIGUOUS"] and out.size == self._count(sim)
         self._check(self.L.mm_get_m(self.h, sim, out.ctypes.data_as(_P), MM_HOST))
         return out
 
