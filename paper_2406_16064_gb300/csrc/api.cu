@@ -74,12 +74,12 @@ struct mm_ctx {
     double* oct = nullptr;
     SimDesc* desc_d = nullptr;
     SimState* state_d = nullptr;
-    WorkItem *xi = nullptr, *y13i = nullptr, *zi = nullptr, *y2i = nullptr;
+    WorkItem *xi = nullptr, *y13i = nullptr, *zi = nullptr, *y2i = nullptr, *celli = nullptr;
     WorkItem* yzci[kYzcListCount] = {};
     PlanItems plan;
     // per simulation: first item and item count in each list (the yzc list is the
     // one of its plane count and group width, yzcl)
-    std::vector<int> xb, xc, y13b, y13c, zb, zc, y2b, y2c, yzcb, yzcc, yzcl;
+    std::vector<int> xb, xc, y13b, y13c, zb, zc, y2b, y2c, yzcb, yzcc, yzcl, cellb, cellc;
     int *flag_d = nullptr, *status_d = nullptr;
     unsigned long long* diag_d = nullptr;
     cudaGraphExec_t rk_exec = nullptr;
@@ -159,6 +159,7 @@ Launch make_launch(mm_ctx* C, int sim) {
     set(L.y13, C->y13i, C->y13b, C->y13c, P.y13);
     set(L.z, C->zi, C->zb, C->zc, P.z);
     set(L.y2, C->y2i, C->y2b, C->y2c, P.y2);
+    set(L.cell, C->celli, C->cellb, C->cellc, P.cell);
     for (int li = 0; li < kYzcListCount; ++li) {
         if (sim < 0) L.yzc[li] = {C->yzci[li], (int)P.yzc[li].size()};
         else if (C->yzcl[sim] == li) L.yzc[li] = {C->yzci[li] + C->yzcb[sim], C->yzcc[sim]};
@@ -249,6 +250,11 @@ int validate_items(mm_ctx* C) {
         if ((w.a % d.ny) + w.b > d.ny) return fail(C, MM_EBOUNDS, "x item crosses a plane");
         if (plan_spec_elems(d) >= (1LL << 31) || 3LL * d.ncells >= (1LL << 31))
             return fail(C, MM_EINVAL, "simulation too large for 32-bit per-simulation offsets");
+    }
+    for (const WorkItem& w : P.cell) {
+        const SimDesc& d = C->sims[w.sim].d;
+        if (w.a < 0 || w.b < 1 || w.a + w.b > d.ny * d.nz || (w.a % d.ny) + w.b > d.ny)
+            return fail(C, MM_EBOUNDS, "cell tile rows");
     }
     for (const WorkItem& w : P.y13) {
         const SimDesc& d = C->sims[w.sim].d;
@@ -646,7 +652,7 @@ int mm_destroy(mm_ctx* C) {
     void* ptrs[] = {C->m, C->ybuf, C->errp, C->spec, C->Msd, C->cellp, C->tens, C->twd, C->twf, C->twdd, C->sc_in,
                     C->sc_out,
                     C->sc_h, C->heff, C->tau, C->kvec_dev, C->oct, C->desc_d, C->state_d, C->xi, C->y13i,
-                    C->zi, C->y2i, C->flag_d, C->status_d, C->diag_d, C->sd_H, C->sd_mprev, C->sd_g,
+                    C->zi, C->y2i, C->celli, C->flag_d, C->status_d, C->diag_d, C->sd_H, C->sd_mprev, C->sd_g,
                     C->sd_d};
     for (void* p : ptrs) if (p) cudaFree(p);
     for (auto& pp : C->pot) {
@@ -1042,7 +1048,9 @@ int mm_precompute_demag(mm_ctx* C) {
         C->zb.push_back((int)P.z.size());
         C->y2b.push_back((int)P.y2.size());
         C->yzcb.push_back((int)P.yzc[g].size());
+        C->cellb.push_back((int)P.cell.size());
         plan_items(d, (int)i, vsz, P);
+        C->cellc.push_back((int)P.cell.size() - C->cellb.back());
         C->xc.push_back((int)P.x.size() - C->xb.back());
         C->y13c.push_back((int)P.y13.size() - C->y13b.back());
         C->zc.push_back((int)P.z.size() - C->zb.back());
@@ -1083,6 +1091,7 @@ int mm_precompute_demag(mm_ctx* C) {
     if ((rc = up_items(&C->y13i, P.y13))) return rc;
     if ((rc = up_items(&C->zi, P.z))) return rc;
     if ((rc = up_items(&C->y2i, P.y2))) return rc;
+    if ((rc = up_items(&C->celli, P.cell))) return rc;
     for (int li = 0; li < kYzcListCount; ++li)
         if ((rc = up_items(&C->yzci[li], P.yzc[li]))) return rc;
     CK(cudaMemcpyAsync(C->kvec_dev, C->k, 7 * sizeof(void*), cudaMemcpyHostToDevice, C->stream));

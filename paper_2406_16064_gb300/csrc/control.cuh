@@ -204,9 +204,33 @@ __device__ __forceinline__ double block_csum(CSum<T> v, double* red) {
     return r;
 }
 
+// Three block sums at once (one pair of barriers): results in r[0..2] of thread 0.
+template <typename T>
+__device__ __forceinline__ void block_csum3(CSum<T> a, CSum<T> b, CSum<T> c, double* red, double (&r)[3]) {
+    a.warp_reduce();
+    b.warp_reduce();
+    c.warp_reduce();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
+    __syncthreads();
+    if (lane == 0) {
+        red[wid] = a.value();
+        red[nw + wid] = b.value();
+        red[2 * nw + wid] = c.value();
+    }
+    __syncthreads();
+    r[0] = r[1] = r[2] = 0.0;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < nw; ++i) {
+            r[0] += red[i];
+            r[1] += red[nw + i];
+            r[2] += red[2 * nw + i];
+        }
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(MM_THREADS) k_neb_tangent(NebParams<T> p) {
-    __shared__ double red[MM_THREADS / 32];
+    __shared__ double red[3 * MM_THREADS / 32];
     __shared__ T wsh[2];
     const WorkItem w = p.items[blockIdx.x];
     SimState* st = p.state;
@@ -279,12 +303,13 @@ __global__ void __launch_bounds__(MM_THREADS) k_neb_tangent(NebParams<T> p) {
             ht.add(htc);
         }
     }
-    const double s0 = block_csum(t2, red);
-    if (threadIdx.x == 0) atomicAdd(&st[w.sim].neb[0], s0);
-    const double s1 = block_csum(ht, red);
-    if (threadIdx.x == 0) atomicAdd(&st[w.sim].neb[1], s1);
-    const double s2 = block_csum(th2, red);
-    if (threadIdx.x == 0) atomicAdd(&st[w.sim].neb[2], s2);
+    double sums[3];
+    block_csum3(t2, ht, th2, red, sums);
+    if (threadIdx.x == 0) {
+        atomicAdd(&st[w.sim].neb[0], sums[0]);
+        atomicAdd(&st[w.sim].neb[1], sums[1]);
+        atomicAdd(&st[w.sim].neb[2], sums[2]);
+    }
 }
 
 template <typename T>

@@ -40,6 +40,7 @@ struct Launch {
     SimState* state = nullptr;
     int nsims = 0;
     ItemSet x, y13, z, y2;        // x rows, y fwd/inv (nz > 8), z fused, y fused (films)
+    ItemSet cell;                 // per-cell tiles of ~kCellTile cells (NEB tangent and force)
     ItemSet yzc[kYzcListCount];   // cluster-fused y/z, one list per plane count, groups, CTAs per SM
     size_t smem_x = 0, smem_xi = 0, smem_y13 = 0, smem_z = 0, smem_y2 = 0, smem_yzc = 0;
     int x_threads = 0, col_threads = 0;   // tuned CTA widths of the x and column passes (0: rule)

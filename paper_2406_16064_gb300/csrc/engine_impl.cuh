@@ -211,7 +211,7 @@ void engine_neb_attempt_c(const Launch& L, const RkBuffers& B) {
         NebParams<S> q;
         q.desc = L.desc;
         q.state = L.state;
-        q.items = L.x.dev;
+        q.items = L.cell.dev;
         q.ys = ys;
         q.heff = reinterpret_cast<const S*>(B.heff);
         q.tau = reinterpret_cast<S*>(B.tau);
@@ -220,8 +220,8 @@ void engine_neb_attempt_c(const Launch& L, const RkBuffers& B) {
         q.Ms = reinterpret_cast<const S*>(L.Ms);
         q.stage = st;
         q.e7 = dp_e(6);
-        k_neb_tangent<S><<<L.x.count, MM_THREADS, 0, s>>>(q);
-        k_neb_force<S><<<L.x.count, MM_THREADS, 0, s>>>(q);
+        k_neb_tangent<S><<<L.cell.count, MM_THREADS, 0, s>>>(q);
+        k_neb_force<S><<<L.cell.count, MM_THREADS, 0, s>>>(q);
         if (L.hook) L.hook->mark(KIND_NEB);
         if (L.launches) *L.launches += 3;
         if (st == 1) {

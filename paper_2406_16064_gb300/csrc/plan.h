@@ -193,8 +193,12 @@ inline size_t plan_xinv_smem(const SimDesc& d, size_t vsz) {
     return b;
 }
 
+// Cells per tile of the per-cell NEB kernels (rows of one plane, at least one row).
+constexpr int kCellTile = 1024;
+
 struct PlanItems {
     std::vector<WorkItem> x, y13, z, y2, yzc[kYzcListCount];
+    std::vector<WorkItem> cell;   // per-cell tiles of ~kCellTile cells: rows of one plane
     size_t smem_x = 0, smem_xi = 0, smem_y13 = 0, smem_z = 0, smem_y2 = 0, smem_yzc = 0;
 };
 
@@ -205,6 +209,9 @@ inline void plan_items(const SimDesc& d, int sid, size_t vsz, PlanItems& P) {
         for (int y0 = 0; y0 < d.ny; y0 += d.Rx) P.x.push_back({sid, z * d.ny + y0, std::min(d.Rx, d.ny - y0), 0});
     P.smem_x = std::max(P.smem_x, 2 * 3 * (size_t)d.Rx * padded_len(d.Kx) * vsz);
     P.smem_xi = std::max(P.smem_xi, plan_xinv_smem(d, vsz));
+    const int rc = std::max(1, kCellTile / d.nx);
+    for (int z = 0; z < d.nz; ++z)
+        for (int y0 = 0; y0 < d.ny; y0 += rc) P.cell.push_back({sid, z * d.ny + y0, std::min(rc, d.ny - y0), 0});
     if (!(d.flags & F_DEMAG)) return;
     if (plan_uses_yzc(d)) {
         const int li = plan_yzc_list(d, vsz == 2 * sizeof(float));
