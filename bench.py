@@ -11,7 +11,7 @@ perpendicular anisotropy, ~200 reversed disks (FP32 path; the FP64 path is
 measured on the same workload and reported beside it).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                  [--workload film|film_relax_32|cube|neb|batch|sweep] [--driver rk45|sd|rk4-cayley|rk4-proj|...]
+                  [--workload film|film_relax_32|cube|cube128|neb|batch|sweep] [--driver rk45|sd|rk4-cayley|rk4-proj|...]
 
 `--driver sd` times steepest-descent steps (one effective-field evaluation and
 the Barzilai-Borwein update each) instead of RK45 attempts; `--driver
@@ -82,6 +82,9 @@ def workload(name, world=1):
         return synth.film_relax_32()
     if name == "cube":
         return synth.bulk_cube()
+    if name == "cube128":
+        # the cube's recipe at 128^3 (spectrum 0.2 GB, above L2): a small case of its kernels for ncu
+        return synth.bulk_cube(n=128)
     if name == "neb":
         return synth.neb_chain()
     if name == "batch":

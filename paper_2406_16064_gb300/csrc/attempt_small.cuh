@@ -119,10 +119,10 @@ __device__ __forceinline__ V2<C> w64_get(const V2<C>* w64, int q) {
 
 // Decimation in frequency: natural order in, bit-reversed order out, NV
 // independent sequences per lane advanced stage by stage (their shuffles and
-// products overlap).
-// Each lane forms its own output with one complex addition and one product: the
-// lower lane of a pair v + u (times 1), the upper (u - v) w, so no lane computes
-// both results (the product by 1 is exact in every compute type).
+// products overlap).  Each lane forms its own output with one complex addition
+// and one product: the lower lane of a pair v + u (times 1), the upper
+// (u - v) w, so no lane computes both results (the product by 1 is exact in
+// every compute type).
 template <typename C, bool INV, int NV>
 __device__ __forceinline__ void warp_dif(V2<C> (&v)[NV], int l, int j, const V2<C>* w64) {
     for (int t = l - 1; t >= 0; --t) {
