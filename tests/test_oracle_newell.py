@@ -132,3 +132,54 @@ def test_wide_thin_film_limit():
     # sum over all offsets = field factor at the centre of a 127 x 127 x 1 film
     tz = Nt[2].sum()
     assert 0.99 < tz < 1.0
+
+
+def _clenshaw_curtis(n):
+    """Clenshaw-Curtis nodes and weights on [0, 1] (n + 1 Chebyshev points, n even): a
+    quadrature family independent of the oracle's Gauss-Legendre tent rule."""
+    k = np.arange(n + 1)
+    theta = np.pi * k / n
+    x = 0.5 * (1.0 - np.cos(theta))
+    w = np.zeros(n + 1)
+    for i in range(n + 1):
+        s = 0.0
+        for j in range(1, n // 2 + 1):
+            b = 1.0 if 2 * j == n else 2.0
+            s += b * np.cos(2 * j * theta[i]) / (4 * j * j - 1)
+        c = 1.0 if i in (0, n) else 2.0
+        w[i] = c / n * (1.0 - s)
+    return x, 0.5 * w
+
+
+def _far_reference(R, d, n=32):
+    """Tent average of the point-dipole kernel, each half-tent by Clenshaw-Curtis."""
+    x, w = _clenshaw_curtis(n)
+    axes = []
+    for dc in d:
+        t = np.concatenate([dc * x, -dc * x])
+        wt = np.concatenate([w * (1.0 - x), w * (1.0 - x)])   # density (1 - |t|/d)/d, dt = d du
+        axes.append((t, wt))
+    TX, TY, TZ = np.meshgrid(axes[0][0], axes[1][0], axes[2][0], indexing="ij")
+    W = np.einsum("i,j,k->ijk", axes[0][1], axes[1][1], axes[2][1])
+    rx, ry, rz = R[0] + TX, R[1] + TY, R[2] + TZ
+    r2 = rx * rx + ry * ry + rz * rz
+    inv5 = W / (r2 * r2 * np.sqrt(r2))
+    out = np.array([(inv5 * (r2 - 3 * rx * rx)).sum(), (inv5 * (r2 - 3 * ry * ry)).sum(),
+                    (inv5 * (r2 - 3 * rz * rz)).sum(), (inv5 * (-3 * rx * ry)).sum(),
+                    (inv5 * (-3 * rx * rz)).sum(), (inv5 * (-3 * ry * rz)).sum()])
+    return out * (d[0] * d[1] * d[2] / (4.0 * math.pi))
+
+
+@pytest.mark.parametrize("cell", [(1.0, 1.0, 1.0), (2.0, 2.0, 1.0), (1.0, 1.0, 0.25)])
+def test_far_bands_against_an_independent_quadrature(cell):
+    """The oracle's tensor beyond the switch (its band table of Gauss-Legendre orders)
+    against the same cell-pair average integrated by Clenshaw-Curtis on each half-tent,
+    at radii inside every band."""
+    rng = np.random.default_rng(11)
+    dm = max(cell)
+    for r in (3.5, 5.0, 9.0, 20.0, 60.0, 200.0):
+        dirv = rng.normal(size=3)
+        R = dirv / np.linalg.norm(dirv) * r * dm
+        got = nw.tensor(*R, *cell)
+        ref = _far_reference(R, cell)
+        assert np.abs(got - ref).max() <= 1e-11 * np.abs(ref).max(), (r, got, ref)
