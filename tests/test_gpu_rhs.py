@@ -226,3 +226,17 @@ def test_bulk_cube_full_size_properties_f32():
         ref = F.h_eff(sm, mat_nod, sub, F.ms_array(sm, mat_nod))[:, z - z0, y - y0, x - x0]
         # the block's own boundary hides neighbours only where the mesh has none either
         np.testing.assert_allclose(h2[:, z, y, x], ref, rtol=0, atol=1e-5 * np.abs(ref).max() + 1e-3)
+
+
+def test_newell_far_field_against_an_independent_quadrature():
+    """The GPU's FP64 tensor at far offsets (its own Gauss-Legendre bands) against the
+    cell-pair average integrated by Clenshaw-Curtis on each half-tent (1e-11)."""
+    from tests.test_oracle_newell import _far_reference
+    mesh = synth.Mesh(70, 9, 3, 2e-9, 2.5e-9, 1.5e-9)
+    ctx = make_ctx("f64", [synth.Sim(mesh, synth.Material(Ms=8e5), synth.uniform_state(mesh))])
+    t = ctx.newell_tensor(0, mesh)                     # [6][2nz-1][2ny-1][2nx-1]
+    d = (mesh.dx, mesh.dy, mesh.dz)
+    for (i, j, k) in ((8, 1, 0), (15, -4, 2), (33, 8, -2), (-69, 3, 1), (50, 0, 0)):
+        got = t[:, k + mesh.nz - 1, j + mesh.ny - 1, i + mesh.nx - 1]
+        ref = _far_reference(np.array([i * d[0], j * d[1], k * d[2]]), d)
+        assert np.abs(got - ref).max() <= 1e-11 * np.abs(ref).max(), (i, j, k)
