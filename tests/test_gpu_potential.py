@@ -83,3 +83,16 @@ def test_potential_rejects_too_long_axes():
     with pytest.raises(mm.MMError) as e:
         _field("f32", synth.Sim(mesh, synth.Material(Ms=8e5), synth.random_state(1, mesh)))
     assert e.value.code == mm.MM_EINVAL
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_potential_random_meshes_match_oracle(seed):
+    """Seeded random meshes of 1..24 cells per axis, random cell sizes, FP64 against
+    the oracle's FFT potential (1e-10)."""
+    rng = np.random.default_rng(300 + seed)
+    shape = tuple(int(v) for v in rng.integers(1, 25, size=3))
+    cells = tuple(float(v) for v in rng.uniform(1e-9, 4e-9, size=3))
+    mesh = synth.Mesh(*shape, *cells)
+    sim = synth.Sim(mesh, synth.Material(Ms=float(rng.uniform(4e5, 1.2e6))), synth.random_state(400 + seed, mesh))
+    H, _ = _field("f64", sim)
+    assert max_rel(H, _oracle(sim, "fft")) < 1e-10, shape
